@@ -1,0 +1,448 @@
+"""Plain FP64 CPU oracle for the Levenberg-Marquardt + PCGNR bundle-adjustment path.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this module.  The product path (the CUDA
+library and its Python binding) never imports, calls or links it, and it shares no
+code with that path: no kernels, headers, helpers or constants.
+
+It is slow and obviously correct on purpose.  Every function follows one passage of
+the paper (arXiv 2605.30583, "Caspar"):
+
+* residual        -- Sec. VI-A, the Snavely reprojection factor (``d_safe``, ``p``,
+                     radial scale, ``pixel - px_m``).  Rotation vectors map to
+                     matrices by Rodrigues' formula (reading of Sec. V / VI-A: a
+                     9-parameter angle-axis camera updated additively).
+* Jacobian        -- Sec. V: derivatives of each factor with respect to its
+                     tunable nodes.  Forward-mode dual numbers carried through the
+                     residual, so no derivative is written by hand here.
+* LM              -- Sec. V: Levenberg-Marquardt with the quality-based damping
+                     update of Madsen et al. (cited there).
+* normal eqs.     -- Sec. V: no Schur complement; the full damped normal equations
+                     are solved by PCGNR (Sec. V-A) with a block-Jacobi
+                     preconditioner, one block per node (Sec. V).
+* settings        -- Sec. VI: initial trust region 100, CG tolerance 0.001.
+
+Readings where the paper is silent (all listed in the design notes): damping
+matrix D = diag(J^T J) clamped to [min_diag, max_diag]; mu_0 = 1 / trust region;
+gain ratio denominator -g^T h - |J h|^2 / 2; CG tolerance is relative to the
+unpreconditioned residual 2-norm with h_0 = 0; a step is accepted iff rho > 0.
+
+Parity pins (tests/test_oracle_pins.py): hand-computed projections, central finite
+differences of the residual, scipy's rotation-vector routine, dense Cholesky
+solves of the damped normal equations, exact zero residual at noise-free ground
+truth, monotone accepted cost, the chi-square level of the optimum and the
+Rosenbrock least-squares minimum.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+import scipy.sparse as sp
+
+# --------------------------------------------------------------------------------------
+# Forward-mode dual numbers: value v (shape [N]) and tangent d (shape [N, K]).
+# --------------------------------------------------------------------------------------
+
+
+class Dual:
+    __array_priority__ = 1000
+
+    def __init__(self, v, d):
+        self.v = np.asarray(v, dtype=np.float64)
+        self.d = np.asarray(d, dtype=np.float64)
+
+    @staticmethod
+    def _split(o):
+        if isinstance(o, Dual):
+            return o.v, o.d
+        return np.asarray(o, dtype=np.float64), None
+
+    def __add__(self, o):
+        v, d = Dual._split(o)
+        return Dual(self.v + v, self.d if d is None else self.d + d)
+
+    __radd__ = __add__
+
+    def __neg__(self):
+        return Dual(-self.v, -self.d)
+
+    def __sub__(self, o):
+        return self + (-o)
+
+    def __rsub__(self, o):
+        return (-self) + o
+
+    def __mul__(self, o):
+        v, d = Dual._split(o)
+        if d is None:
+            return Dual(self.v * v, self.d * np.asarray(v)[..., None])
+        return Dual(self.v * v, self.d * v[..., None] + d * self.v[..., None])
+
+    __rmul__ = __mul__
+
+    def __truediv__(self, o):
+        v, d = Dual._split(o)
+        q = self.v / v
+        if d is None:
+            return Dual(q, self.d / np.asarray(v)[..., None])
+        return Dual(q, (self.d - d * q[..., None]) / v[..., None])
+
+    def __rtruediv__(self, o):
+        return Dual(np.broadcast_to(np.asarray(o, dtype=np.float64), self.v.shape),
+                    np.zeros_like(self.d)) / self
+
+
+def _sqrt(x):
+    if isinstance(x, Dual):
+        s = np.sqrt(x.v)
+        return Dual(s, x.d / (2.0 * s)[..., None])
+    return np.sqrt(x)
+
+
+def _sin(x):
+    if isinstance(x, Dual):
+        return Dual(np.sin(x.v), x.d * np.cos(x.v)[..., None])
+    return np.sin(x)
+
+
+def _cos(x):
+    if isinstance(x, Dual):
+        return Dual(np.cos(x.v), -x.d * np.sin(x.v)[..., None])
+    return np.cos(x)
+
+
+def _where(mask, a, b):
+    if isinstance(a, Dual) or isinstance(b, Dual):
+        av, ad = (a.v, a.d) if isinstance(a, Dual) else (a, 0.0 * b.d)
+        bv, bd = (b.v, b.d) if isinstance(b, Dual) else (b, 0.0 * a.d)
+        return Dual(np.where(mask, av, bv), np.where(mask[..., None], ad, bd))
+    return np.where(mask, a, b)
+
+
+def _value(x):
+    return x.v if isinstance(x, Dual) else np.asarray(x)
+
+
+# --------------------------------------------------------------------------------------
+# Residual (Sec. VI-A)
+# --------------------------------------------------------------------------------------
+
+SMALL_ANGLE_SQ = 1e-8   # theta < 1e-4: Taylor series of the Rodrigues coefficients
+
+
+def rotate(w, X):
+    """R(w) X by Rodrigues' formula R = I + a [w]x + b [w]x^2 with
+    a = sin(theta)/theta and b = (1 - cos(theta))/theta^2 = 2 sin^2(theta/2)/theta^2.
+    For theta^2 < 1e-8 the series a = 1 - theta^2/6 + theta^4/120 and
+    b = 1/2 - theta^2/24 + theta^4/720 are used instead (no 0/0)."""
+    w0, w1, w2 = w
+    x0, x1, x2 = X
+    th2 = w0 * w0 + w1 * w1 + w2 * w2
+    small = _value(th2) < SMALL_ANGLE_SQ
+    th2_safe = _where(small, 1.0, th2)
+    th = _sqrt(th2_safe)
+    half = _sin(th * 0.5)
+    a_big = _sin(th) / th
+    b_big = 2.0 * half * half / th2_safe
+    a_small = 1.0 - th2 / 6.0 + th2 * th2 / 120.0
+    b_small = 0.5 - th2 / 24.0 + th2 * th2 / 720.0
+    a = _where(small, a_small, a_big)
+    b = _where(small, b_small, b_big)
+    # c = w x X, e = w x (w x X)
+    c0 = w1 * x2 - w2 * x1
+    c1 = w2 * x0 - w0 * x2
+    c2 = w0 * x1 - w1 * x0
+    e0 = w1 * c2 - w2 * c1
+    e1 = w2 * c0 - w0 * c2
+    e2 = w0 * c1 - w1 * c0
+    return (x0 + a * c0 + b * e0, x1 + a * c1 + b * e1, x2 + a * c2 + b * e2)
+
+
+def _sign_no_zero(x):
+    return np.where(_value(x) >= 0.0, 1.0, -1.0)
+
+
+def project(cam, X, eps_depth=0.0):
+    """Pixel predicted for a camera cam = (w0,w1,w2,t0,t1,t2,f,k1,k2) and point X."""
+    w = cam[0:3]
+    t = cam[3:6]
+    f, k1, k2 = cam[6], cam[7], cam[8]
+    RX = rotate(w, X)
+    P0, P1, P2 = RX[0] + t[0], RX[1] + t[1], RX[2] + t[2]
+    d_safe = P2 + eps_depth * _sign_no_zero(P2)
+    p0 = -P0 / d_safe
+    p1 = -P1 / d_safe
+    n2 = p0 * p0 + p1 * p1
+    n4 = n2 * n2
+    s = 1.0 + k1 * n2 + k2 * n4
+    return f * s * p0, f * s * p1
+
+
+def residuals(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0):
+    """r_o = pixel(cam_{c_o}, X_{p_o}) - u_o for every observation, shape [n_obs, 2]."""
+    cams = np.asarray(cams, np.float64)
+    pts = np.asarray(pts, np.float64)
+    c = cams[np.asarray(cam_idx, np.int64)].T
+    X = pts[np.asarray(pt_idx, np.int64)].T
+    u0, u1 = project(list(c), list(X), eps_depth)
+    return np.stack([u0 - pixels[:, 0], u1 - pixels[:, 1]], axis=1)
+
+
+def cost(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0):
+    """F = 1/2 sum_o |r_o|^2."""
+    r = residuals(cams, pts, cam_idx, pt_idx, pixels, eps_depth)
+    return 0.5 * float(np.sum(r * r))
+
+
+def jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, chunk=200_000):
+    """Residuals r [n_obs,2] and Jacobian blocks J_c [n_obs,2,9], J_p [n_obs,2,3], by
+    forward-mode dual numbers seeded with the 12 tangent directions of (camera, point)."""
+    cams = np.asarray(cams, np.float64)
+    pts = np.asarray(pts, np.float64)
+    ci = np.asarray(cam_idx, np.int64)
+    pi = np.asarray(pt_idx, np.int64)
+    n = ci.shape[0]
+    r = np.empty((n, 2))
+    Jc = np.empty((n, 2, 9))
+    Jp = np.empty((n, 2, 3))
+    eye = np.eye(12)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        m = e - s
+        c = cams[ci[s:e]]
+        X = pts[pi[s:e]]
+        cd = [Dual(c[:, k], np.broadcast_to(eye[k], (m, 12))) for k in range(9)]
+        Xd = [Dual(X[:, k], np.broadcast_to(eye[9 + k], (m, 12))) for k in range(3)]
+        u0, u1 = project(cd, Xd, eps_depth)
+        r[s:e, 0] = u0.v - pixels[s:e, 0]
+        r[s:e, 1] = u1.v - pixels[s:e, 1]
+        Jc[s:e, 0] = u0.d[:, :9]
+        Jc[s:e, 1] = u1.d[:, :9]
+        Jp[s:e, 0] = u0.d[:, 9:]
+        Jp[s:e, 1] = u1.d[:, 9:]
+    return r, Jc, Jp
+
+
+# --------------------------------------------------------------------------------------
+# Problem layout: x = [cams (9 per camera) | points (3 per point)], n = 9 Nc + 3 Np
+# --------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Linearization:
+    F: float                 # 1/2 |r|^2
+    r: np.ndarray            # [m]
+    J: sp.csr_matrix         # [m, n]
+    g: np.ndarray            # J^T r, [n]
+    Hc: np.ndarray           # camera diagonal blocks of J^T J, [Nc, 9, 9]
+    Hp: np.ndarray           # point diagonal blocks of J^T J, [Np, 3, 3]
+
+
+def assemble_jacobian(Jc, Jp, cam_idx, pt_idx, n_cams, n_pts):
+    """Sparse J with rows (2o, 2o+1) and columns 9c..9c+8 and 9Nc + 3p..+2."""
+    n_obs = Jc.shape[0]
+    ci = np.asarray(cam_idx, np.int64)
+    pi = np.asarray(pt_idx, np.int64)
+    rows = np.repeat(np.arange(2 * n_obs), 12)
+    cols_c = 9 * ci[:, None] + np.arange(9)[None, :]
+    cols_p = 9 * n_cams + 3 * pi[:, None] + np.arange(3)[None, :]
+    cols = np.concatenate([cols_c, cols_p], axis=1)                 # [n_obs, 12]
+    cols = np.repeat(cols, 2, axis=0).reshape(-1)                    # rows 2o and 2o+1 share columns
+    vals = np.concatenate([Jc, Jp], axis=2).reshape(-1)             # [n_obs, 2, 12]
+    n = 9 * n_cams + 3 * n_pts
+    return sp.csr_matrix((vals, (rows, cols)), shape=(2 * n_obs, n))
+
+
+def linearize(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0) -> Linearization:
+    n_cams, n_pts = cams.shape[0], pts.shape[0]
+    r, Jc, Jp = jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth)
+    J = assemble_jacobian(Jc, Jp, cam_idx, pt_idx, n_cams, n_pts)
+    rf = r.reshape(-1)
+    g = J.T @ rf
+    Hc = np.zeros((n_cams, 9, 9))
+    Hp = np.zeros((n_pts, 3, 3))
+    np.add.at(Hc, np.asarray(cam_idx, np.int64), np.einsum("oki,okj->oij", Jc, Jc))
+    np.add.at(Hp, np.asarray(pt_idx, np.int64), np.einsum("oki,okj->oij", Jp, Jp))
+    return Linearization(F=0.5 * float(rf @ rf), r=rf, J=J, g=g, Hc=Hc, Hp=Hp)
+
+
+# --------------------------------------------------------------------------------------
+# Block-Jacobi preconditioner and PCGNR (Sec. V, V-A)
+# --------------------------------------------------------------------------------------
+
+
+def damping_diag(J, min_diag=1e-6, max_diag=1e32):
+    """D = diag(J^T J) (column sums of J squared), clamped to [min_diag, max_diag]."""
+    d = np.asarray(J.multiply(J).sum(axis=0)).ravel()
+    return np.clip(d, min_diag, max_diag)
+
+
+def block_jacobi(lin: Linearization, D, mu):
+    """Inverses of the diagonal blocks of J^T J + mu D, one block per node, by Cholesky."""
+    nc = lin.Hc.shape[0]
+    Dc = D[: 9 * nc].reshape(nc, 9)
+    Dp = D[9 * nc:].reshape(-1, 3)
+    Ac = lin.Hc + mu * np.einsum("ci,ij->cij", Dc, np.eye(9))
+    Ap = lin.Hp + mu * np.einsum("pi,ij->pij", Dp, np.eye(3))
+    Lc = np.linalg.cholesky(Ac)
+    Lp = np.linalg.cholesky(Ap)
+    inv = lambda L: np.linalg.inv(L).transpose(0, 2, 1) @ np.linalg.inv(L)
+    return inv(Lc), inv(Lp)
+
+
+def apply_block_jacobi(Mc, Mp, v):
+    nc = Mc.shape[0]
+    zc = np.einsum("cij,cj->ci", Mc, v[: 9 * nc].reshape(nc, 9)).reshape(-1)
+    zp = np.einsum("pij,pj->pi", Mp, v[9 * nc:].reshape(-1, 3)).reshape(-1)
+    return np.concatenate([zc, zp])
+
+
+@dataclasses.dataclass
+class PCGResult:
+    h: np.ndarray
+    iters: int
+    r0_norm: float
+    r_norm: float
+
+
+def pcgnr(J, D, mu, b, precond, tol=1e-3, max_iters=50):
+    """Solve (J^T J + mu D) h = b with preconditioned CG on the normal equations.
+
+    Matrix-free: each iteration forms w = J p and then J^T w + mu D p.  Starts from
+    h = 0 and stops when |r_k|_2 <= tol |r_0|_2 or after max_iters iterations."""
+    h = np.zeros_like(b)
+    r = b.copy()
+    z = precond(r)
+    p = z.copy()
+    rz = float(r @ z)
+    r0 = float(np.sqrt(r @ r))
+    rn = r0
+    k = 0
+    while k < max_iters and rn > tol * r0:
+        w = J @ p
+        q = J.T @ w + mu * D * p
+        alpha = rz / float(w @ w + mu * (p @ (D * p)))
+        h = h + alpha * p
+        r = r - alpha * q
+        k += 1
+        rn = float(np.sqrt(r @ r))
+        if rn <= tol * r0:
+            break
+        z = precond(r)
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+    return PCGResult(h=h, iters=k, r0_norm=r0, r_norm=rn)
+
+
+# --------------------------------------------------------------------------------------
+# Levenberg-Marquardt with Madsen's quality-based damping (Sec. V)
+# --------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class LMOptions:
+    max_lm_iters: int = 20
+    max_pcg_iters: int = 50
+    pcg_rel_tol: float = 1e-3
+    initial_trust_region: float = 100.0
+    min_diag: float = 1e-6
+    max_diag: float = 1e32
+    eps_depth: float = 0.0
+    max_mu: float = 1e32
+
+
+@dataclasses.dataclass
+class LMResult:
+    x: np.ndarray
+    initial_cost: float
+    final_cost: float
+    history: list
+    lm_iters: int
+    accepted: int
+    pcg_iters_total: int
+
+
+def lm_solve(x0, linearize_fn, cost_fn, make_precond, opts: LMOptions = LMOptions()) -> LMResult:
+    """Generic LM over x.  linearize_fn(x) -> object with F, J (sparse) and g = J^T r;
+    cost_fn(x) -> F; make_precond(lin, D, mu) -> callable applying the preconditioner.
+
+    One iteration: solve (J^T J + mu D) h = -g by PCGNR; x' = x + h;
+    rho = (F - F') / (-g^T h - 1/2 |J h|^2).  If rho > 0 the step is accepted,
+    mu <- mu * max(1/3, 1 - (2 rho - 1)^3), nu <- 2; otherwise mu <- mu nu, nu <- 2 nu.
+    Stops after max_lm_iters iterations, when mu exceeds max_mu, or when F = 0."""
+    x = np.array(x0, dtype=np.float64)
+    lin = linearize_fn(x)
+    mu = 1.0 / opts.initial_trust_region
+    nu = 2.0
+    F0 = lin.F
+    hist = []
+    accepted = 0
+    pcg_total = 0
+    it = 0
+    while it < opts.max_lm_iters and lin.F > 0.0 and mu <= opts.max_mu:
+        D = damping_diag(lin.J, opts.min_diag, opts.max_diag)
+        precond = make_precond(lin, D, mu)
+        res = pcgnr(lin.J, D, mu, -lin.g, precond, opts.pcg_rel_tol, opts.max_pcg_iters)
+        h = res.h
+        pcg_total += res.iters
+        Jh = lin.J @ h
+        L = float(-(lin.g @ h) - 0.5 * (Jh @ Jh))
+        x_new = x + h
+        F_new = cost_fn(x_new)
+        rho = (lin.F - F_new) / L if L > 0 else -np.inf
+        ok = bool(np.isfinite(F_new) and L > 0 and rho > 0)
+        hist.append(dict(cost=lin.F, cost_new=F_new, mu=mu, rho=rho, pcg_iters=res.iters,
+                         accepted=ok, model_decrease=L))
+        it += 1
+        if ok:
+            x = x_new
+            mu = mu * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)
+            nu = 2.0
+            accepted += 1
+            lin = linearize_fn(x)
+        else:
+            mu = mu * nu
+            nu = 2.0 * nu
+    return LMResult(x=x, initial_cost=F0, final_cost=lin.F, history=hist, lm_iters=it,
+                    accepted=accepted, pcg_iters_total=pcg_total)
+
+
+def _ba_precond(lin, D, mu):
+    Mc, Mp = block_jacobi(lin, D, mu)
+    return lambda v: apply_block_jacobi(Mc, Mp, v)
+
+
+# --------------------------------------------------------------------------------------
+# Bundle adjustment entry points
+# --------------------------------------------------------------------------------------
+
+
+def pack(cams, pts):
+    return np.concatenate([np.asarray(cams, np.float64).reshape(-1),
+                           np.asarray(pts, np.float64).reshape(-1)])
+
+
+def unpack(x, n_cams):
+    return x[: 9 * n_cams].reshape(n_cams, 9), x[9 * n_cams:].reshape(-1, 3)
+
+
+def ba_solve(cams0, pts0, cam_idx, pt_idx, pixels, opts: LMOptions = LMOptions()) -> LMResult:
+    """Bundle adjustment by LM + PCGNR over all camera and point parameters."""
+    n_cams = cams0.shape[0]
+
+    def lin_fn(x):
+        c, p = unpack(x, n_cams)
+        return linearize(c, p, cam_idx, pt_idx, pixels, opts.eps_depth)
+
+    def cost_fn(x):
+        c, p = unpack(x, n_cams)
+        return cost(c, p, cam_idx, pt_idx, pixels, opts.eps_depth)
+
+    return lm_solve(pack(cams0, pts0), lin_fn, cost_fn, _ba_precond, opts)
+
+
+def normal_matvec(lin: Linearization, D, mu, v):
+    """(J^T J + mu D) v, the operator PCGNR applies."""
+    return lin.J.T @ (lin.J @ v) + mu * D * v

@@ -1,0 +1,315 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test is chosen so that a plausible mistake in the oracle (a dropped term, a
+wrong sign or index, a transposed operand, a wrong damping or gain-ratio formula)
+fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.spatial.transform import Rotation
+
+from oracle import ba_oracle as O
+from paper_2605_30583_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small_problem(seed=7, n_cams=3, n_pts=20, noise=1.0):
+    return synth.make_problem(n_cams, n_pts, ("poisson", 1.0), "uniform", seed=seed, noise_px=noise)
+
+
+# ---------------------------------------------------------------- projection -----
+
+
+def test_hand_projection_cases():
+    """Hand-worked pixels of the Sec. VI-A residual (tests/golden/hand_projection.json)."""
+    data = json.load(open(os.path.join(GOLDEN, "hand_projection.json")))
+    for case in data["cases"]:
+        cam = np.array(case["cam"], dtype=np.float64)
+        X = np.array(case["point"], dtype=np.float64)
+        RX = O.rotate(list(cam[:3]), list(X))
+        P = np.array(RX) + cam[3:6]
+        np.testing.assert_allclose(P, case["P"], atol=1e-14)
+        u = O.project(list(cam), list(X))
+        np.testing.assert_allclose(u, case["pixel"], rtol=0, atol=1e-12)
+        # residual against the predicted pixel is exactly zero
+        r = O.residuals(cam[None], X[None], [0], [0], np.array([case["pixel"]]))
+        assert np.all(np.abs(r) <= 1e-12)
+
+
+def test_first_hand_case_is_exact():
+    """With w = 0 every step is exact in binary, so the pixel is bit-exact."""
+    u = O.project([0.0, 0.0, 0.0, 0.0, 0.0, -4.0, 500.0, 0.1, 0.01], [1.0, 2.0, 0.0])
+    assert u == (129.0283203125, 258.056640625)
+
+
+def test_rotation_matches_scipy_rotvec():
+    rng = np.random.default_rng(0)
+    w = rng.standard_normal((500, 3))
+    w[:100] *= 1e-6                                   # small-angle series branch
+    w[100:200] *= np.pi / np.linalg.norm(w[100:200], axis=1, keepdims=True)  # |w| = pi
+    X = rng.standard_normal((500, 3))
+    ours = np.stack(O.rotate(list(w.T), list(X.T)), axis=1)
+    ref = Rotation.from_rotvec(w).apply(X)
+    np.testing.assert_allclose(ours, ref, rtol=0, atol=1e-13)
+
+
+def test_eps_depth_shifts_depth_away_from_zero():
+    """d_safe = d + eps * sign_no_zero(d): for d < 0 the shift is -eps (Sec. VI-A)."""
+    cam = [0, 0, 0, 0, 0, -4, 500, 0, 0]
+    u0 = O.project(cam, [1.0, 2.0, 0.0], eps_depth=0.0)
+    u1 = O.project(cam, [1.0, 2.0, 0.0], eps_depth=1.0)     # d_safe = -5
+    np.testing.assert_allclose(u1, (100.0, 200.0), atol=1e-12)
+    assert u0 != u1
+    # sign_no_zero(0) = +1
+    u2 = O.project([0, 0, 0, 0, 0, 0, 1, 0, 0], [1.0, 2.0, 0.0], eps_depth=0.5)
+    np.testing.assert_allclose(u2, (-2.0, -4.0), atol=1e-12)
+
+
+# ---------------------------------------------------------------- Jacobian -------
+
+
+def _fd_jacobian(cams, pts, ci, pi, px, h=1e-6):
+    n = ci.shape[0]
+    Jc = np.zeros((n, 2, 9))
+    Jp = np.zeros((n, 2, 3))
+    for k in range(9):
+        cp, cm = cams.copy(), cams.copy()
+        cp[:, k] += h
+        cm[:, k] -= h
+        Jc[:, :, k] = (O.residuals(cp, pts, ci, pi, px) - O.residuals(cm, pts, ci, pi, px)) / (2 * h)
+    for k in range(3):
+        pp, pm = pts.copy(), pts.copy()
+        pp[:, k] += h
+        pm[:, k] -= h
+        Jp[:, :, k] = (O.residuals(cams, pp, ci, pi, px) - O.residuals(cams, pm, ci, pi, px)) / (2 * h)
+    return Jc, Jp
+
+
+def test_dual_jacobian_matches_central_differences():
+    p = synth.make_config("tiny")
+    sel = np.arange(0, p.n_obs, 7)
+    ci, pi, px = p.cam_idx[sel], p.pt_idx[sel], p.pixels[sel]
+    # one observation per (camera, point) row so each FD column touches one observation
+    cams = p.cams_init[ci]
+    pts = p.pts_init[pi]
+    idx = np.arange(sel.shape[0])
+    r, Jc, Jp = O.jacobian_blocks(cams, pts, idx, idx, px)
+    fJc, fJp = _fd_jacobian(cams, pts, idx, idx, px)
+    for A, B in ((Jc, fJc), (Jp, fJp)):
+        err = np.linalg.norm(A - B, axis=(1, 2)) / np.linalg.norm(B, axis=(1, 2))
+        assert err.max() < 1e-6, err.max()
+
+
+def test_dual_jacobian_small_angle_and_pi():
+    rng = np.random.default_rng(3)
+    cams = np.tile(np.array([0, 0, 0, 0.1, -0.2, -5.0, 700.0, 0.01, -0.005]), (6, 1))
+    cams[0, :3] = 0.0
+    cams[1, :3] = [3e-5, -2e-5, 1e-5]          # series branch
+    cams[2, :3] = [2e-4, 1e-4, -1e-4]          # just above the branch threshold
+    cams[3, :3] = [0, 0, np.pi]                # 180 degrees
+    cams[4, :3] = rng.standard_normal(3)
+    cams[5, :3] = [1.0, 2.0, 0.5]
+    pts = rng.standard_normal((6, 3)) * 0.5
+    idx = np.arange(6)
+    px = np.zeros((6, 2))
+    r, Jc, Jp = O.jacobian_blocks(cams, pts, idx, idx, px)
+    fJc, fJp = _fd_jacobian(cams, pts, idx, idx, px)
+    np.testing.assert_allclose(Jc, fJc, rtol=1e-6, atol=1e-5)
+    np.testing.assert_allclose(Jp, fJp, rtol=1e-6, atol=1e-5)
+
+
+def test_sparse_assembly_matches_dense_fd_jacobian():
+    """Column layout [9 per camera | 3 per point] and row pairs (2o, 2o+1)."""
+    p = _small_problem()
+    x0 = O.pack(p.cams_init, p.pts_init)
+    lin = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+
+    def rfun(x):
+        c, q = O.unpack(x, p.n_cams)
+        return O.residuals(c, q, p.cam_idx, p.pt_idx, p.pixels).reshape(-1)
+
+    h = 1e-6
+    Jd = np.zeros((2 * p.n_obs, x0.shape[0]))
+    for k in range(x0.shape[0]):
+        e = np.zeros_like(x0)
+        e[k] = h
+        Jd[:, k] = (rfun(x0 + e) - rfun(x0 - e)) / (2 * h)
+    J = lin.J.toarray()
+    assert np.abs(J - Jd).max() <= 1e-5 * np.abs(Jd).max()
+    np.testing.assert_allclose(lin.r, rfun(x0), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(lin.g, Jd.T @ lin.r, rtol=1e-6, atol=1e-6 * np.abs(Jd.T @ lin.r).max())
+    JtJ = J.T @ J
+    for c in range(p.n_cams):
+        np.testing.assert_allclose(lin.Hc[c], JtJ[9 * c:9 * c + 9, 9 * c:9 * c + 9], rtol=1e-12, atol=1e-9)
+    base = 9 * p.n_cams
+    for q in range(p.n_pts):
+        s = base + 3 * q
+        np.testing.assert_allclose(lin.Hp[q], JtJ[s:s + 3, s:s + 3], rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------- PCG ------------
+
+
+def test_pcgnr_matches_dense_cholesky_solve():
+    p = _small_problem()
+    lin = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+    mu = 0.01
+    D = O.damping_diag(lin.J)
+    J = lin.J.toarray()
+    A = J.T @ J + mu * np.diag(D)
+    h_dense = np.linalg.solve(A, -lin.g)
+    Mc, Mp = O.block_jacobi(lin, D, mu)
+    res = O.pcgnr(lin.J, D, mu, -lin.g, lambda v: O.apply_block_jacobi(Mc, Mp, v),
+                  tol=1e-14, max_iters=10 * A.shape[0])
+    assert np.linalg.norm(res.h - h_dense) <= 1e-9 * np.linalg.norm(h_dense)
+    # the preconditioner blocks are the inverses of the dense diagonal blocks
+    for c in range(p.n_cams):
+        blk = A[9 * c:9 * c + 9, 9 * c:9 * c + 9]
+        np.testing.assert_allclose(Mc[c] @ blk, np.eye(9), atol=1e-8)
+    np.testing.assert_allclose(O.normal_matvec(lin, D, mu, h_dense), -lin.g, rtol=1e-8,
+                               atol=1e-8 * np.abs(lin.g).max())
+
+
+def test_damping_diag_is_clamped_column_norm():
+    J = sp.csr_matrix(np.array([[1.0, 0.0, 2.0], [3.0, 0.0, 0.0]]))
+    np.testing.assert_array_equal(O.damping_diag(J, 1e-6, 5.0), [5.0, 1e-6, 4.0])
+
+
+def test_pcg_exact_preconditioner_converges_in_one_iteration():
+    """A block-diagonal J^T J with the exact block inverse as preconditioner: one step."""
+    rng = np.random.default_rng(1)
+    B1, B2 = rng.standard_normal((4, 2)), rng.standard_normal((4, 3))
+    J = sp.block_diag([sp.csr_matrix(B1), B2]).tocsr()
+    D = np.ones(5)
+    mu = 0.5
+    A = (J.T @ J).toarray() + mu * np.eye(5)
+    b = rng.standard_normal(5)
+    Ainv = np.linalg.inv(A)
+    res = O.pcgnr(J, D, mu, b, lambda v: Ainv @ v, tol=1e-12, max_iters=5)
+    assert res.iters == 1
+    np.testing.assert_allclose(res.h, Ainv @ b, rtol=1e-12)
+
+
+def test_pcg_iteration_cap_and_tolerance():
+    p = _small_problem()
+    lin = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+    D = O.damping_diag(lin.J)
+    Mc, Mp = O.block_jacobi(lin, D, 0.01)
+    pre = lambda v: O.apply_block_jacobi(Mc, Mp, v)
+    capped = O.pcgnr(lin.J, D, 0.01, -lin.g, pre, tol=1e-14, max_iters=3)
+    assert capped.iters == 3
+    tol = O.pcgnr(lin.J, D, 0.01, -lin.g, pre, tol=1e-3, max_iters=1000)
+    assert tol.r_norm <= 1e-3 * tol.r0_norm
+    assert tol.iters < 1000
+
+
+# ---------------------------------------------------------------- LM -------------
+
+
+def _linear_problem(seed=5):
+    rng = np.random.default_rng(seed)
+    A = sp.csr_matrix(rng.standard_normal((30, 6)))
+    b = rng.standard_normal(30)
+
+    class Lin:
+        def __init__(self, x):
+            self.r = A @ x - b
+            self.F = 0.5 * float(self.r @ self.r)
+            self.J = A
+            self.g = A.T @ self.r
+
+    def pre(lin, D, mu):
+        M = np.linalg.inv((A.T @ A).toarray() + mu * np.diag(D))
+        return lambda v: M @ v
+
+    return A, b, Lin, (lambda x: 0.5 * float(np.sum((A @ x - b) ** 2))), pre
+
+
+def test_lm_gain_ratio_is_one_on_linear_least_squares():
+    """The quadratic model is exact for linear residuals, so rho = 1 and Madsen's rule
+    gives mu <- mu * max(1/3, 1 - (2*1 - 1)^3) = mu / 3 on every accepted step."""
+    A, b, Lin, cost, pre = _linear_problem()
+    opts = O.LMOptions(max_lm_iters=4, pcg_rel_tol=1e-14, max_pcg_iters=50)
+    res = O.lm_solve(np.zeros(6), Lin, cost, pre, opts)
+    for k, h in enumerate(res.history):
+        if h["model_decrease"] > 1e-9 * res.initial_cost:
+            assert h["accepted"]
+            assert abs(h["rho"] - 1.0) < 1e-8
+    np.testing.assert_allclose([h["mu"] for h in res.history[:2]], [0.01, 0.01 / 3], rtol=1e-12)
+    x_ls = np.linalg.lstsq(A.toarray(), b, rcond=None)[0]
+    np.testing.assert_allclose(res.x, x_ls, rtol=1e-6, atol=1e-8)
+
+
+def test_lm_rosenbrock_reaches_minimum():
+    """Rosenbrock as least squares, r = (10 (x1 - x0^2), 1 - x0); minimum F = 0 at (1, 1)."""
+
+    class Lin:
+        def __init__(self, x):
+            self.r = np.array([10 * (x[1] - x[0] ** 2), 1 - x[0]])
+            self.F = 0.5 * float(self.r @ self.r)
+            self.J = sp.csr_matrix(np.array([[-20 * x[0], 10.0], [-1.0, 0.0]]))
+            self.g = self.J.T @ self.r
+
+    def pre(lin, D, mu):
+        M = np.linalg.inv((lin.J.T @ lin.J).toarray() + mu * np.diag(D))
+        return lambda v: M @ v
+
+    cost = lambda x: 0.5 * (100 * (x[1] - x[0] ** 2) ** 2 + (1 - x[0]) ** 2)
+    res = O.lm_solve(np.array([-1.2, 1.0]), Lin, cost, pre,
+                     O.LMOptions(max_lm_iters=200, pcg_rel_tol=1e-12, max_pcg_iters=10))
+    np.testing.assert_allclose(res.x, [1.0, 1.0], atol=1e-6)
+    assert res.final_cost < 1e-12
+
+
+def test_lm_rejected_step_leaves_x_and_increases_mu():
+    A, b, Lin, cost, pre = _linear_problem()
+    # A cost function that always reports a higher cost forces every step to be rejected.
+    res = O.lm_solve(np.zeros(6), Lin, lambda x: 1e30, pre, O.LMOptions(max_lm_iters=4))
+    assert res.accepted == 0
+    np.testing.assert_array_equal(res.x, np.zeros(6))
+    mus = [h["mu"] for h in res.history]
+    np.testing.assert_allclose(mus, [0.01, 0.02, 0.08, 0.64], rtol=1e-12)   # nu = 2, 4, 8
+
+
+# ---------------------------------------------------------------- BA invariants --
+
+
+def test_zero_residual_at_noise_free_ground_truth():
+    """The generator's look-at projection and the oracle's Rodrigues projection agree."""
+    p = synth.make_problem(16, 300, ("poisson", 3.0), "uniform", seed=11, noise_px=0.0)
+    r = O.residuals(p.cams_gt, p.pts_gt, p.cam_idx, p.pt_idx, p.pixels)
+    assert np.abs(r).max() < 1e-9
+    res = O.ba_solve(p.cams_gt, p.pts_gt, p.cam_idx, p.pt_idx, p.pixels, O.LMOptions(max_lm_iters=3))
+    assert res.final_cost <= res.initial_cost < 1e-15
+
+
+def test_lm_monotone_cost_and_chi_square_level():
+    """Accepted steps strictly decrease F; at the optimum 2F / sigma^2 follows a
+    chi-square law with m - n + 7 degrees of freedom (7-DoF similarity gauge)."""
+    p = synth.make_config("tiny")
+    res = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+    costs = [h["cost"] for h in res.history] + [res.final_cost]
+    for a, b_ in zip(costs[:-1], costs[1:]):
+        assert b_ <= a
+    for h in res.history:
+        if h["accepted"]:
+            assert h["cost_new"] < h["cost"]
+    m = 2 * p.n_obs
+    n = 9 * p.n_cams + 3 * p.n_pts
+    dof = m - n + 7
+    assert abs(2 * res.final_cost - dof) < 4 * np.sqrt(2 * dof)
+    assert res.final_cost < 0.01 * res.initial_cost
+
+
+def test_gradient_vanishes_at_solution():
+    p = synth.make_config("tiny")
+    res = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+    c, q = O.unpack(res.x, p.n_cams)
+    g0 = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels).g
+    g1 = O.linearize(c, q, p.cam_idx, p.pt_idx, p.pixels).g
+    assert np.linalg.norm(g1) < 1e-6 * np.linalg.norm(g0)
