@@ -1,0 +1,393 @@
+"""Benchmark of the LM + PCGNR bundle-adjustment hot path on one or more GB300s.
+
+One step = one complete LM solve (20 LM iterations, at most 50 PCG iterations each,
+initial trust region 100, CG tolerance 1e-3) of the medium synthetic workload
+(1,000 cameras, 200,000 points, ~1.2M observations), restarted from the same
+initial parameters, with every input already resident in HBM.  The metric is PCG
+iterations per second of whole-solve wall time (device events); the time to reach
+the FP64 oracle's final cost within 1e-4 is reported beside it.
+
+Multi-GPU: problems are independent, so ranks run replicas on their own seeds with
+no collective on the data path (weak scaling); timing is max over ranks.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "BA time-to-cost and PCG iters/s (HBM GB/s) vs plain FP64 GPU form"
+UNIT = "PCG iters/s"
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="medium")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks ----------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, name in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers ---------
+
+def golden_cost(config: str):
+    path = os.path.join(GOLDEN, f"oracle_lm_{config}.json")
+    if not os.path.exists(path):
+        return None
+    return json.load(open(path))["fp64"]["final_cost"]
+
+
+def time_to_cost(history, target):
+    if target is None:
+        return None
+    for h in history:
+        if h["accepted"] and h["cost_new"] <= target:
+            return h["t_ns"] / 1e6
+    return None
+
+
+def matvec_model(prob):
+    """Algorithmic bytes and FP32 flops of one normal-operator launch (recomputed J).
+
+    Bytes: per observation its 4-byte key; per point X, p, D read and q written
+    (4 x 12 B); per camera its 64-byte record, 48-byte direction record and a
+    48-byte accumulator read-modify-write.  Flops: per observation the projection
+    and A = d(pixel)/dP (~40), J d (~36), J^T t (~44): 120 FP32 flops."""
+    nb = 4 * prob.n_obs + 48 * prob.n_pts + (64 + 48 + 96) * prob.n_cams
+    nf = 120 * prob.n_obs
+    return nb, nf
+
+
+# ---------------------------------------------------------------- reference arm ---
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on a bounded sample: one linearisation and PCG iterations."""
+    if rank != 0:
+        return
+    from oracle import ba_oracle as O
+    from paper_2605_30583_gb300 import synth
+    prob = synth.make_config(args.config)
+    lin = O.linearize(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
+    D = O.damping_diag(lin.J)
+    Mc, Mp = O.block_jacobi(lin, D, 0.01)
+    pre = lambda v: O.apply_block_jacobi(Mc, Mp, v)
+    iters_per_step = 5
+
+    def step():
+        t0 = time.perf_counter()
+        res = O.pcgnr(lin.J, D, 0.01, -lin.g, pre, tol=0.0, max_iters=iters_per_step)
+        return res.iters, time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    it = 0
+    dt = 0.0
+    for _ in range(args.steps):
+        a, b = step()
+        it += a
+        dt += b
+    v = it / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: {prob.n_cams} cameras, {prob.n_pts} points, {prob.n_obs} observations",
+                   "sample": f"{iters_per_step} PCGNR iterations per step after one linearisation"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{iters_per_step} PCG iterations per step, {args.steps} steps"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(prob, seconds=12.0):
+    """The oracle as it stands, timed on the host: PCG iterations per second over a
+    bounded sample (one linearisation, then PCG iterations until ~`seconds`)."""
+    from oracle import ba_oracle as O
+    lin = O.linearize(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
+    D = O.damping_diag(lin.J)
+    Mc, Mp = O.block_jacobi(lin, D, 0.01)
+    pre = lambda v: O.apply_block_jacobi(Mc, Mp, v)
+    t0 = time.perf_counter()
+    it = 0
+    while time.perf_counter() - t0 < seconds:
+        res = O.pcgnr(lin.J, D, 0.01, -lin.g, pre, tol=0.0, max_iters=5)
+        it += res.iters
+    dt = time.perf_counter() - t0
+    return {"value": it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{it} PCGNR iterations of the FP64 oracle on the same workload after one linearisation"}
+
+
+# ---------------------------------------------------------------- our arm ---------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2605_30583_gb300 import binding, build, synth
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    base_seed = synth.CONFIGS[args.config]["seed"]
+    prob = synth.make_config(args.config, seed=base_seed + 7919 * rank)
+    target = golden_cost(args.config) if rank == 0 else None
+    opts = binding.default_options()
+
+    p = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels)
+    cams0 = torch.tensor(prob.cams_init, dtype=torch.float64, device=dev)
+    pts0 = torch.tensor(prob.pts_init, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one_solve():
+        p.set_params(cams0, pts0)
+        p.solve(opts, wait=False)
+
+    for _ in range(max(3, args.warmup)):
+        one_solve()
+    torch.cuda.synchronize()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    step_ms = []
+    pcg = 0
+    lm = 0
+    last = None
+    for _ in range(args.steps):
+        flush.fill_(1)                                   # L2 flush between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_solve()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        last = p.stats()
+        pcg += last.pcg_iters_total
+        lm += last.lm_iters
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms, float(pcg)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
+        pc = t[1:].clone()
+        dist.all_reduce(pc, op=dist.ReduceOp.SUM)
+        t[1] = pc[0]
+    total_ms_max, pcg_all = float(t[0]), float(t[1])
+    value = pcg_all / (total_ms_max / 1e3)
+
+    # ---- normal-operator kernel: live timing with CUDA events on the launching stream
+    p.set_params(cams0, pts0)
+    p.evaluate()
+    n = 9 * prob.n_cams + 3 * prob.n_pts
+    v = torch.randn(n, dtype=torch.float32, device=dev)
+    p.apply_normal(0.01, v)
+    reps = 200
+    p.repeat_normal(10)
+    flush.fill_(2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    p.repeat_normal(reps)
+    e1.record(stream)
+    e1.synchronize()
+    mv_ms = e0.elapsed_time(e1) / reps
+    nb, nf = matvec_model(prob)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_mhz = clocks.get("sm_mhz") or 1920.0
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    gbs = nb / (mv_ms / 1e3) / 1e9
+    tfl = nf / (mv_ms / 1e3) / 1e12
+    roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    roof_alu = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
+                "traffic": None,
+                "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
+    roofline = roof_alu if roof_alu["frac"] >= roof_hbm["frac"] else roof_hbm
+    roofline = dict(roofline, kernel="k_matvec (damped normal operator, recomputed Jacobian)",
+                    ms_per_launch=mv_ms, algorithmic_bytes=nb, algorithmic_flops=nf)
+    other = roof_hbm if roofline["bound"] == "alu" else roof_alu
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        import ctypes
+        L = binding.lib()
+        ws = p.workspace
+        ci = np.ascontiguousarray(prob.cam_idx, np.uint32)
+        pi = np.ascontiguousarray(prob.pt_idx, np.uint32)
+        px = np.ascontiguousarray(prob.pixels, np.float64)
+        c0 = np.ascontiguousarray(prob.cams_init)
+        q0 = np.ascontiguousarray(prob.pts_init)
+        c1 = np.empty_like(c0)
+        q1 = np.empty_like(q0)
+        e2e_s = []
+        e2e_pcg = 0
+        for _ in range(max(1, min(3, args.steps))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = ctypes.c_void_p()
+            binding.check(L.ba_problem_create(prob.n_cams, prob.n_pts, prob.n_obs, ci.ctypes.data, pi.ctypes.data,
+                                              px.ctypes.data, 0, ctypes.byref(h)))
+            binding.check(L.ba_bind_workspace(h, ws.data_ptr(), p.workspace_bytes, stream.cuda_stream))
+            binding.check(L.ba_set_params(h, c0.ctypes.data, q0.ctypes.data))
+            st = binding.Stats()
+            binding.check(L.ba_solve(h, ctypes.byref(opts), ctypes.byref(st), None, 0))
+            binding.check(L.ba_get_params(h, c1.ctypes.data, q1.ctypes.data))
+            e2e_s.append(time.perf_counter() - t0)
+            e2e_pcg += st.pcg_iters_total
+            L.ba_problem_destroy(h)
+        h2d = prob.n_obs * (4 + 4 + 16) + 8 * (9 * prob.n_cams + 3 * prob.n_pts)
+        d2h = 8 * (9 * prob.n_cams + 3 * prob.n_pts) + 64
+        e2e = {"value": e2e_pcg / sum(e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "s_per_step": sum(e2e_s) / len(e2e_s),
+               "path": "ba_problem_create + ba_bind_workspace (upload + ordering) + ba_set_params + ba_solve "
+                       "+ ba_get_params, host FP64 arrays"}
+
+    # ---- plain all-FP64 GPU form on the same problem
+    fp64 = None
+    if not args.no_fp64:
+        try:
+            q = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels, precision="fp64")
+            q.set_params(cams0, pts0)
+            q.solve(opts, wait=False)
+            torch.cuda.synchronize()
+            ms = []
+            pc = 0
+            for _ in range(max(1, min(3, args.steps))):
+                flush.fill_(3)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                q.set_params(cams0, pts0)
+                q.solve(opts, wait=False)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                st64 = q.stats()
+                pc += st64.pcg_iters_total
+            fp64 = {"value": pc / (sum(ms) / 1e3), "unit": UNIT, "ms_per_solve": sum(ms) / len(ms),
+                    "final_cost": st64.final_cost, "time_to_cost_ms": time_to_cost(st64.history, target * (1 + 1e-4)
+                                                                                   if target else None)}
+            q.close()
+        except binding.BAError as e:
+            fp64 = {"unavailable": str(e)}
+
+    launches_per_step = 1 + 3 + 5 * last.lm_iters + 3 * last.pcg_iters_total + 1
+    ttc = time_to_cost(last.history, target * (1 + 1e-4) if target else None)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: {prob.n_cams} cameras, {prob.n_pts} points, {prob.n_obs} observations,"
+                               f" 20 LM x <=50 PCG, TR0=100, CG tol 1e-3",
+                   "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "final_cost": last.final_cost, "oracle_final_cost": target,
+        "time_to_cost_ms": ttc, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
+        "step_ms": step_ms,
+        "roofline": roofline, "roofline_other": other,
+        "e2e": e2e, "fp64_plain": fp64, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * gbba.h -- C ABI of the GB300 bundle-adjustment hot path (libgbba.so).
+ *
+ * Levenberg-Marquardt with a matrix-free, block-Jacobi-preconditioned conjugate
+ * gradient on the damped normal equations (PCGNR), for the Snavely reprojection
+ * factor of arXiv 2605.30583 (Caspar), Sec. V and Sec. VI-A.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns a ba_status; BA_OK is 0.  On failure ba_last_error()
+ *    returns a message for the calling thread.  No call aborts the process.
+ *  - Cameras are 9 doubles each, in this order: rotation vector w (3),
+ *    translation t (3), focal length f, radial terms k1, k2.  Points are 3
+ *    doubles.  Both are row-major arrays ("user layout"): cams[n_cams][9],
+ *    pts[n_pts][3].  Pixels are pixels[n_obs][2].
+ *  - The camera model is P = R(w) X + t, p = -P.xy / d_safe with
+ *    d_safe = P.z + eps_depth * sign_no_zero(P.z), pixel = f (1 + k1|p|^2 +
+ *    k2|p|^4) p, residual = pixel - measured (Sec. VI-A).
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *    memory of the current device.  Pointers are borrowed: the library never
+ *    frees caller memory and keeps no caller pointer beyond the call, except the
+ *    workspace and stream given to ba_bind_workspace.
+ *  - All device memory the library uses lives in ONE caller-allocated workspace
+ *    (Sec. V-A: a single allocation for the whole optimisation, arrays are views
+ *    into it).  The library itself calls no cudaMalloc.
+ *  - Device work is enqueued on the stream given to ba_bind_workspace.  Calls
+ *    that return host data synchronise that stream.
+ *  - One problem may be used by one host thread at a time.
+ */
+#ifndef GBBA_H
+#define GBBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BA_OK = 0,
+    BA_ERR_INVALID_ARG = 1,          /* bad size, index, pointer or option          */
+    BA_ERR_CUDA = 2,                 /* a CUDA runtime call failed                  */
+    BA_ERR_WORKSPACE_TOO_SMALL = 3,  /* bound workspace smaller than ba_workspace_size */
+    BA_ERR_NUMERIC = 4,              /* NaN/Inf, or a preconditioner block not SPD  */
+    BA_ERR_TIMEOUT = 5,              /* a bounded device wait ran out               */
+    BA_ERR_NOT_IMPLEMENTED = 6,
+    BA_ERR_STATE = 7                 /* call made in the wrong order (e.g. no workspace) */
+} ba_status;
+
+typedef enum {
+    BA_PREC_MIXED = 0,   /* FP32 residuals, Jacobians, parameters and PCG vectors;
+                            FP64 cost sums, PCG dot products and block inversions */
+    BA_PREC_FP64 = 1     /* plain all-FP64 form: stored FP64 Jacobian, FP64 vectors,
+                            per-observation atomics (the comparison baseline)      */
+} ba_precision;
+
+typedef struct ba_problem ba_problem;
+
+/* Solver options.  Defaults (ba_options_default) follow Sec. VI of the paper:
+ * initial trust region 100 (mu_0 = 1/100) and CG tolerance 1e-3. */
+typedef struct {
+    int32_t max_lm_iters;         /* LM iterations (accepted or rejected), default 20   */
+    int32_t max_pcg_iters;        /* PCG iterations per LM iteration, default 50        */
+    double pcg_rel_tol;           /* stop when |r_k|_2 <= tol |r_0|_2, default 1e-3     */
+    double initial_trust_region;  /* mu_0 = 1 / initial_trust_region, default 100       */
+    double min_diag;              /* D = clamp(diag(J^T J), min_diag, max_diag)         */
+    double max_diag;
+    double max_mu;                /* stop when mu exceeds this, default 1e32            */
+    double eps_depth;             /* epsilon of d_safe (Sec. VI-A), default 0           */
+    int32_t use_graph;            /* 1: one CUDA graph with device-side loops (default) */
+    int32_t reserved;
+} ba_options;
+
+/* One LM iteration (Sec. V): cost before the step, candidate cost, damping used,
+ * gain ratio, PCG iterations spent, whether the step was accepted, and the device
+ * time (ns since the start of the solve) at which the decision was taken. */
+typedef struct {
+    double cost;
+    double cost_new;
+    double mu;
+    double rho;
+    double model_decrease;
+    int32_t pcg_iters;
+    int32_t accepted;
+    int64_t t_ns;
+} ba_iter_stat;
+
+typedef struct {
+    double initial_cost;
+    double final_cost;
+    int32_t lm_iters;
+    int32_t accepted;
+    int32_t pcg_iters_total;
+    int32_t status;               /* ba_status of the device-side solve            */
+    int64_t solve_ns;             /* device time of the whole solve                */
+} ba_stats;
+
+const char* ba_last_error(void);
+const char* ba_status_string(int32_t status);
+int32_t ba_abi_version(void);
+
+/* Fills *opts with the defaults listed at ba_options. */
+ba_status ba_options_default(ba_options* opts);
+
+/* Creates a problem from host index arrays (Sec. VI-A: cameras and points are the
+ * tunable nodes, observations are constant and read sequentially).
+ *   cam_idx[n_obs], pt_idx[n_obs]: host, camera / point of each observation.
+ *   pixels[n_obs][2]: host, measured pixels.
+ * Copied; the caller keeps ownership.  Requirements (else BA_ERR_INVALID_ARG):
+ * 1 <= n_cams < 2^24, 1 <= n_pts, 1 <= n_obs < 2^32, every index in range, and
+ * every point observed at least twice.  No device memory is touched until
+ * ba_bind_workspace. */
+ba_status ba_problem_create(int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                            const uint32_t* cam_idx, const uint32_t* pt_idx,
+                            const double* pixels, int32_t precision, ba_problem** out);
+
+/* Frees the problem's host memory, streams and graphs (never the workspace). */
+void ba_problem_destroy(ba_problem* problem);
+
+/* Bytes of device workspace the problem needs (any options). */
+ba_status ba_workspace_size(const ba_problem* problem, size_t* bytes);
+
+/* Binds caller-owned device memory (>= ba_workspace_size bytes, 256-byte aligned)
+ * and a CUDA stream (cudaStream_t, may be 0 for the legacy stream).  Uploads the
+ * observations and builds the locality ordering on the device: points sorted by
+ * their first camera, tiles of consecutive points, observations of a tile sorted
+ * by camera (our counterpart of the Shared Read/Add index build of Sec. IV-A).
+ * Must precede every call below.  Rebinding rebuilds everything. */
+ba_status ba_bind_workspace(ba_problem* problem, void* workspace, size_t bytes, void* stream);
+
+/* Parameters from / to host FP64 arrays in user layout. */
+ba_status ba_set_params(ba_problem* problem, const double* cams, const double* pts);
+ba_status ba_get_params(ba_problem* problem, double* cams, double* pts);
+
+/* Parameters from / to device arrays in user layout; dtype 0 = float32, 1 = float64.
+ * Enqueued on the bound stream, no synchronisation. */
+ba_status ba_set_params_device(ba_problem* problem, const void* cams, const void* pts, int32_t dtype);
+ba_status ba_get_params_device(ba_problem* problem, void* cams, void* pts, int32_t dtype);
+
+/* Evaluates the problem at the current parameters (Sec. VI-A residual, Sec. V
+ * Jacobian).  cost_out (host, may be NULL) receives 1/2 sum |r|^2 in FP64.
+ * residuals (device, may be NULL): [n_obs][2] in the caller's observation order.
+ * jacobian (device, may be NULL): [n_obs][2][12], columns = 9 camera parameters
+ * then 3 point coordinates.  Element type float for BA_PREC_MIXED, double for
+ * BA_PREC_FP64.  Synchronises when cost_out is given. */
+ba_status ba_evaluate(ba_problem* problem, double* cost_out, void* residuals, void* jacobian);
+
+/* Runs LM + PCGNR from the current parameters (Sec. V).  If stats is NULL the call
+ * only enqueues the solve and returns; read results later with ba_get_stats.
+ * Otherwise it synchronises and fills *stats and up to history_cap entries of
+ * history (may be NULL). */
+ba_status ba_solve(ba_problem* problem, const ba_options* opts, ba_stats* stats,
+                   ba_iter_stat* history, int32_t history_cap);
+
+/* Results of the last ba_solve (synchronises). */
+ba_status ba_get_stats(ba_problem* problem, ba_stats* stats, ba_iter_stat* history,
+                       int32_t history_cap);
+
+/* Applies the damped normal operator once, out = (J^T J + mu D) v at the current
+ * linearisation (Sec. V-A PCGNR step), for testing and kernel timing.  v and out are
+ * device vectors in user layout (n_cams*9 then n_pts*3 entries, float for MIXED,
+ * double for FP64).  Requires a prior ba_evaluate or ba_solve that linearised.
+ * jp2_out (host, may be NULL) receives |J v|^2 + mu v^T D v in FP64 (synchronises). */
+ba_status ba_apply_normal(ba_problem* problem, double mu, const void* v, void* out,
+                          double* vAv_out);
+
+/* Launches the normal-operator kernel `launches` times back to back on the bound
+ * stream with the launch configuration the solver uses (timing aid). */
+ba_status ba_repeat_normal(ba_problem* problem, int32_t launches);
+
+/* Total reprojection cost F = 1/2 sum |r|^2 (FP64) at caller parameters, and its
+ * adjoint.  cams/pts are device arrays in user layout of dtype (0 float32,
+ * 1 float64).  Forward writes F to *cost_dev (device double).  Backward writes
+ * grad_cams = grad_out * J_c^T r and grad_pts = grad_out * J_p^T r (device, same
+ * dtype, user layout), where grad_out is a device double.  Neither call
+ * synchronises.  Used by the torch.autograd.Function of the Python binding. */
+ba_status ba_cost_forward(ba_problem* problem, const void* cams, const void* pts, int32_t dtype,
+                          double* cost_dev);
+ba_status ba_cost_backward(ba_problem* problem, const void* cams, const void* pts, int32_t dtype,
+                           const double* grad_out_dev, void* grad_cams, void* grad_pts);
+
+/* Batched mode: many independent small problems solved by one persistent kernel.
+ * Offsets are host prefix arrays of length n_problems + 1 into the concatenated
+ * camera, point and observation arrays; cam_idx / pt_idx are LOCAL to each
+ * problem.  Problems must each satisfy the ba_problem_create requirements. */
+typedef struct ba_batch ba_batch;
+ba_status ba_batch_create(int32_t n_problems, const int32_t* cam_off, const int32_t* pt_off,
+                          const int64_t* obs_off, const uint32_t* cam_idx, const uint32_t* pt_idx,
+                          const double* pixels, ba_batch** out);
+void ba_batch_destroy(ba_batch* batch);
+ba_status ba_batch_workspace_size(const ba_batch* batch, size_t* bytes);
+ba_status ba_batch_bind_workspace(ba_batch* batch, void* workspace, size_t bytes, void* stream);
+ba_status ba_batch_set_params(ba_batch* batch, const double* cams, const double* pts);
+ba_status ba_batch_get_params(ba_batch* batch, double* cams, double* pts);
+/* Solves every problem with the same options; NULL stats = asynchronous. */
+ba_status ba_batch_solve(ba_batch* batch, const ba_options* opts, ba_stats* stats_per_problem);
+ba_status ba_batch_get_costs(ba_batch* batch, double* initial_costs, double* final_costs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBBA_H */

@@ -1,0 +1,719 @@
+// C ABI of libgbba (include/gbba.h): validation, the single workspace, the
+// locality ordering, parameter transfer, evaluation and the LM + PCGNR solve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "gbba.h"
+#include "kernels.h"
+#include "problem.h"
+
+namespace gbba {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+ba_status cuda_status(cudaError_t e, const char* what) {
+    set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    return BA_ERR_CUDA;
+}
+
+namespace {
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Bump {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        off = align_up(off, 256);
+        size_t o = off;
+        off += bytes;
+        return o;
+    }
+};
+
+inline size_t pow2_at_least(size_t n) {
+    size_t p = 2;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t precision) {
+    Layout l{};
+    const size_t T = precision == BA_PREC_FP64 ? 8 : 4;
+    const size_t nc = (size_t)n_cams, np = (size_t)n_pts, no = (size_t)n_obs;
+    const size_t n_tiles = (np + TILE_PTS - 1) / TILE_PTS;
+    const size_t pt_off = align_up(9 * nc, 4);
+    const size_t n_vec = pt_off + align_up(3 * np, 4);
+    Bump b;
+    l.state = b.take(sizeof(DevState));
+    l.partials = b.take(sizeof(double) * MAX_GRID * NPART);
+    l.obs_key = b.take(4 * no);
+    l.obs_uv = b.take(T * 2 * no);
+    l.obs_user = b.take(4 * no);
+    l.tile_off = b.take(4 * (n_tiles + 1));
+    l.pt_user = b.take(4 * np);
+    l.pt_internal = b.take(4 * np);
+    l.staging = b.take(8 * (9 * nc + 3 * np));
+    const size_t union_base = align_up(b.off, 256);
+    // solver arrays
+    Bump s;
+    s.off = union_base;
+    for (int i = 0; i < 9; ++i) l.vec[i] = s.take(T * n_vec);
+    l.cam_pre = s.take(4 * CP_STRIDE * nc);
+    l.cam_pre_new = s.take(4 * CP_STRIDE * nc);
+    l.cam_dir = s.take(4 * CD_STRIDE * nc);
+    l.cam_acc = s.take(4 * CA_STRIDE * nc);
+    l.cam_lin = s.take(8 * CL_STRIDE * nc);
+    l.pt_H = s.take(T * PH_STRIDE * np);
+    l.Minv_c = s.take(T * MC_STRIDE * nc);
+    l.Minv_p = s.take(T * MP_STRIDE * np);
+    if (precision == BA_PREC_FP64) {
+        l.jac = s.take(T * 24 * no);
+        l.res = s.take(T * 2 * no);
+    } else {
+        l.jac = l.res = 0;
+    }
+    // ordering scratch (only live during ba_bind_workspace), overlaps the solver arrays
+    Bump o;
+    o.off = union_base;
+    l.sort_cap = pow2_at_least(std::max(no, np));
+    l.s_cam_idx = o.take(4 * no);
+    l.s_pt_idx = o.take(4 * no);
+    l.s_pixels = o.take(8 * 2 * no);
+    l.s_pt_key = o.take(4 * np);
+    l.s_tile_cnt = o.take(4 * (n_tiles + 1));
+    l.s_keys = o.take(8 * l.sort_cap);
+    l.s_vals = o.take(4 * l.sort_cap);
+    l.total = align_up(std::max(s.off, o.off), 256);
+    return l;
+}
+
+template <typename T>
+Views<T> make_views(ba_problem* p) {
+    Views<T> v{};
+    const Layout& l = p->lay;
+    char* w = p->ws;
+    v.n_cams = p->n_cams;
+    v.n_pts = p->n_pts;
+    v.n_tiles = p->n_tiles;
+    v.n_obs = p->n_obs;
+    v.pt_off = p->pt_off;
+    v.n_vec = p->n_vec;
+    v.obs_key = (const uint32_t*)(w + l.obs_key);
+    v.obs_uv = (const T*)(w + l.obs_uv);
+    v.obs_user = (const uint32_t*)(w + l.obs_user);
+    v.tile_off = (const uint32_t*)(w + l.tile_off);
+    v.pt_user = (const uint32_t*)(w + l.pt_user);
+    v.pt_internal = (const uint32_t*)(w + l.pt_internal);
+    T** vecs[9] = {&v.x, &v.x_new, &v.h, &v.r, &v.z, &v.p, &v.q, &v.g, &v.D};
+    for (int i = 0; i < 9; ++i) *vecs[i] = (T*)(w + l.vec[i]);
+    v.cam_pre = (float*)(w + l.cam_pre);
+    v.cam_pre_new = (float*)(w + l.cam_pre_new);
+    v.cam_dir = (float*)(w + l.cam_dir);
+    v.cam_acc = (float*)(w + l.cam_acc);
+    v.cam_lin = (double*)(w + l.cam_lin);
+    v.pt_H = (T*)(w + l.pt_H);
+    v.Minv_c = (T*)(w + l.Minv_c);
+    v.Minv_p = (T*)(w + l.Minv_p);
+    v.jac = l.jac ? (T*)(w + l.jac) : nullptr;
+    v.res = l.res ? (T*)(w + l.res) : nullptr;
+    v.st = (DevState*)(w + l.state);
+    v.partials = (double*)(w + l.partials);
+    v.staging = w + l.staging;
+    return v;
+}
+
+template Views<float> make_views<float>(ba_problem*);
+template Views<double> make_views<double>(ba_problem*);
+
+// ------------------------------------------------------------------ solve ------
+
+static void enqueue_lm_body_mixed(ba_problem* p, cudaStream_t s, CondHandle lm_c, CondHandle pcg_c, int use_cond,
+                                  cudaStream_t pcg_stream, bool inline_pcg, int max_pcg);
+
+static void enqueue_pcg_iteration_mixed(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int use_cond) {
+    const Views<float>& v = p->vf;
+    launch_direction(v, p->L, s);
+    launch_matvec(v, p->L, s, &v.st->pcg_active);
+    launch_update(v, p->L, s, pcg_c, use_cond);
+}
+
+static void enqueue_lm_body_mixed(ba_problem* p, cudaStream_t s, CondHandle lm_c, CondHandle pcg_c, int use_cond,
+                                  cudaStream_t, bool inline_pcg, int max_pcg) {
+    const Views<float>& v = p->vf;
+    launch_precond(v, p->L, s, pcg_c, use_cond);
+    if (inline_pcg)
+        for (int k = 0; k < max_pcg; ++k) enqueue_pcg_iteration_mixed(p, s, pcg_c, use_cond);
+    (void)lm_c;
+}
+
+static void enqueue_lm_tail_mixed(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use_cond) {
+    const Views<float>& v = p->vf;
+    launch_candidate(v, p->L, s);
+    launch_eval_candidate(v, p->L, s, lm_c, use_cond);
+    launch_commit(v, p->L, s);
+    launch_linearize(v, p->L, s, 1, nullptr, nullptr, lm_c, 0);
+}
+
+// Adds a WHILE conditional node at the current capture position of `s`; returns its
+// body graph.  The handle must already exist on the capturing graph.
+static cudaError_t add_while_node(cudaStream_t s, CondHandle h, cudaGraph_t* body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = (cudaGraphConditionalHandle)h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np);
+    if (e != cudaSuccess) return e;
+    *body = np.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// One CUDA graph for a whole solve: init, then WHILE(lm) { precond; WHILE(pcg)
+// { direction; matvec; update }; candidate; evaluate; commit; relinearise }, finish.
+// Loop flags are set on the device by the kernels that decide them; both loops are
+// bounded by the iteration caps held in the device state.
+static ba_status build_graph_mixed(ba_problem* p) {
+    cudaStream_t s0 = p->cap[0], s1 = p->cap[1], s2 = p->cap[2];
+    const Views<float>& v = p->vf;
+    cudaGraph_t top;
+    GBBA_CUDA(cudaGraphCreate(&top, 0));
+    cudaGraphConditionalHandle lm_h, pcg_h;
+    GBBA_CUDA(cudaGraphConditionalHandleCreate(&lm_h, top, 0, cudaGraphCondAssignDefault));
+    GBBA_CUDA(cudaStreamBeginCaptureToGraph(s0, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    launch_init_state(v.st, s0);
+    launch_camera_precompute(v, p->L, s0);
+    launch_linearize(v, p->L, s0, 0, nullptr, nullptr, (CondHandle)lm_h, 1);
+    cudaGraph_t lm_body;
+    cudaError_t e = add_while_node(s0, (CondHandle)lm_h, &lm_body);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&pcg_h, lm_body, 0, 0);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s1, lm_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        enqueue_lm_body_mixed(p, s1, (CondHandle)lm_h, (CondHandle)pcg_h, 1, s2, false, 0);
+        cudaGraph_t pcg_body;
+        e = add_while_node(s1, (CondHandle)pcg_h, &pcg_body);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s2, pcg_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            enqueue_pcg_iteration_mixed(p, s2, (CondHandle)pcg_h, 1);
+            cudaGraph_t tmp;
+            e = cudaStreamEndCapture(s2, &tmp);
+        }
+        if (e == cudaSuccess) enqueue_lm_tail_mixed(p, s1, (CondHandle)lm_h, 1);
+        cudaGraph_t tmp1;
+        cudaError_t e1 = cudaStreamEndCapture(s1, &tmp1);
+        if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) launch_finish_state(v.st, s0);
+    cudaGraph_t tmp0;
+    cudaError_t e0 = cudaStreamEndCapture(s0, &tmp0);
+    if (e == cudaSuccess) e = e0;
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(top);
+        return cuda_status(e, "building the solve graph");
+    }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, top, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(top);
+        return cuda_status(e, "cudaGraphInstantiate");
+    }
+    p->graph.graph = top;
+    p->graph.exec = exec;
+    return BA_OK;
+}
+
+static void enqueue_solve_predicated_mixed(ba_problem* p, const ba_options& o) {
+    cudaStream_t s = p->stream;
+    const Views<float>& v = p->vf;
+    launch_init_state(v.st, s);
+    launch_camera_precompute(v, p->L, s);
+    launch_linearize(v, p->L, s, 0, nullptr, nullptr, 0, 0);
+    for (int it = 0; it < o.max_lm_iters; ++it) {
+        enqueue_lm_body_mixed(p, s, 0, 0, 0, s, true, o.max_pcg_iters);
+        enqueue_lm_tail_mixed(p, s, 0, 0);
+    }
+    launch_finish_state(v.st, s);
+}
+
+}  // namespace gbba
+
+using namespace gbba;
+
+// ------------------------------------------------------------------ C ABI ------
+
+extern "C" {
+
+const char* ba_last_error(void) { return g_err; }
+
+const char* ba_status_string(int32_t s) {
+    switch (s) {
+        case BA_OK: return "ok";
+        case BA_ERR_INVALID_ARG: return "invalid argument";
+        case BA_ERR_CUDA: return "CUDA error";
+        case BA_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+        case BA_ERR_NUMERIC: return "numeric failure (NaN/Inf or non-SPD block)";
+        case BA_ERR_TIMEOUT: return "device wait timed out";
+        case BA_ERR_NOT_IMPLEMENTED: return "not implemented";
+        case BA_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+int32_t ba_abi_version(void) { return 1; }
+
+ba_status ba_options_default(ba_options* o) {
+    if (!o) {
+        set_error("ba_options_default: null pointer");
+        return BA_ERR_INVALID_ARG;
+    }
+    o->max_lm_iters = 20;
+    o->max_pcg_iters = 50;
+    o->pcg_rel_tol = 1e-3;
+    o->initial_trust_region = 100.0;
+    o->min_diag = 1e-6;
+    o->max_diag = 1e32;
+    o->max_mu = 1e32;
+    o->eps_depth = 0.0;
+    o->use_graph = 1;
+    o->reserved = 0;
+    return BA_OK;
+}
+
+ba_status ba_problem_create(int32_t n_cams, int32_t n_pts, int64_t n_obs, const uint32_t* cam_idx,
+                            const uint32_t* pt_idx, const double* pixels, int32_t precision, ba_problem** out) {
+    if (!out) {
+        set_error("ba_problem_create: out is null");
+        return BA_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (n_cams < 1 || n_cams >= (1 << 24) || n_pts < 1 || n_obs < 1 || n_obs >= (int64_t)0xffffffffLL) {
+        set_error("ba_problem_create: sizes out of range (n_cams=%d n_pts=%d n_obs=%lld)", n_cams, n_pts,
+                  (long long)n_obs);
+        return BA_ERR_INVALID_ARG;
+    }
+    if (!cam_idx || !pt_idx || !pixels) {
+        set_error("ba_problem_create: null input array");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (precision != BA_PREC_MIXED && precision != BA_PREC_FP64) {
+        set_error("ba_problem_create: unknown precision %d", precision);
+        return BA_ERR_INVALID_ARG;
+    }
+    std::vector<uint32_t> deg((size_t)n_pts, 0);
+    for (int64_t o = 0; o < n_obs; ++o) {
+        if (cam_idx[o] >= (uint32_t)n_cams || pt_idx[o] >= (uint32_t)n_pts) {
+            set_error("ba_problem_create: observation %lld has camera %u / point %u out of range", (long long)o,
+                      cam_idx[o], pt_idx[o]);
+            return BA_ERR_INVALID_ARG;
+        }
+        deg[pt_idx[o]] += 1;
+    }
+    for (int32_t i = 0; i < n_pts; ++i)
+        if (deg[i] < 2) {
+            set_error("ba_problem_create: point %d is observed %u time(s); at least 2 are required", i, deg[i]);
+            return BA_ERR_INVALID_ARG;
+        }
+    ba_problem* p = new (std::nothrow) ba_problem();
+    if (!p) {
+        set_error("ba_problem_create: out of host memory");
+        return BA_ERR_INVALID_ARG;
+    }
+    p->n_cams = n_cams;
+    p->n_pts = n_pts;
+    p->n_obs = n_obs;
+    p->n_tiles = (n_pts + TILE_PTS - 1) / TILE_PTS;
+    p->precision = precision;
+    p->cam_idx.assign(cam_idx, cam_idx + n_obs);
+    p->pt_idx.assign(pt_idx, pt_idx + n_obs);
+    p->pixels.assign(pixels, pixels + 2 * n_obs);
+    p->pt_off = (int64_t)((9 * (size_t)n_cams + 3) / 4 * 4);
+    p->n_vec = p->pt_off + (int64_t)((3 * (size_t)n_pts + 3) / 4 * 4);
+    p->lay = compute_layout(n_cams, n_pts, n_obs, precision);
+    *out = p;
+    return BA_OK;
+}
+
+static void release_graph(ba_problem* p) {
+    if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
+    if (p->graph.graph) cudaGraphDestroy(p->graph.graph);
+    p->graph = GraphCache{};
+}
+
+void ba_problem_destroy(ba_problem* p) {
+    if (!p) return;
+    release_graph(p);
+    for (auto& s : p->cap)
+        if (s) cudaStreamDestroy(s);
+    delete p;
+}
+
+ba_status ba_workspace_size(const ba_problem* p, size_t* bytes) {
+    if (!p || !bytes) {
+        set_error("ba_workspace_size: null pointer");
+        return BA_ERR_INVALID_ARG;
+    }
+    *bytes = p->lay.total;
+    return BA_OK;
+}
+
+static ba_status check_bound(const ba_problem* p, const char* who) {
+    if (!p) {
+        set_error("%s: null problem", who);
+        return BA_ERR_INVALID_ARG;
+    }
+    if (!p->bound) {
+        set_error("%s: no workspace bound (call ba_bind_workspace first)", who);
+        return BA_ERR_STATE;
+    }
+    return BA_OK;
+}
+
+ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream) {
+    if (!p || !ws) {
+        set_error("ba_bind_workspace: null pointer");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)ws & 255u) != 0) {
+        set_error("ba_bind_workspace: workspace must be 256-byte aligned");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (bytes < p->lay.total) {
+        set_error("ba_bind_workspace: workspace has %zu bytes, needs %zu", bytes, p->lay.total);
+        return BA_ERR_WORKSPACE_TOO_SMALL;
+    }
+    release_graph(p);
+    p->bound = false;
+    p->linearized = false;
+    p->ws = (char*)ws;
+    p->ws_bytes = bytes;
+    p->stream = (cudaStream_t)stream;
+    GBBA_CUDA(cudaGetDevice(&p->device));
+    for (auto& s : p->cap)
+        if (!s) GBBA_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int sms = 0;
+    GBBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    p->L.item_block = 256;
+    p->L.item_grid = std::min(MAX_GRID, sms * 8);
+    if (p->precision == BA_PREC_MIXED) {
+        p->L.lin_grid = std::min(MAX_GRID, sms * std::max(1, occupancy_blocks_linearize()));
+        p->L.mv_grid = std::min(MAX_GRID, sms * std::max(1, occupancy_blocks_matvec()));
+        p->L.ev_grid = std::min(MAX_GRID, sms * std::max(1, occupancy_blocks_eval()));
+    }
+    const Layout& l = p->lay;
+    char* w = p->ws;
+    cudaStream_t s = p->stream;
+    GBBA_CUDA(cudaMemsetAsync(w + l.state, 0, sizeof(DevState), s));
+    GBBA_CUDA(cudaMemsetAsync(w + l.partials, 0, sizeof(double) * MAX_GRID * NPART, s));
+    GBBA_CUDA(cudaMemcpyAsync(w + l.s_cam_idx, p->cam_idx.data(), 4 * (size_t)p->n_obs, cudaMemcpyHostToDevice, s));
+    GBBA_CUDA(cudaMemcpyAsync(w + l.s_pt_idx, p->pt_idx.data(), 4 * (size_t)p->n_obs, cudaMemcpyHostToDevice, s));
+    GBBA_CUDA(cudaMemcpyAsync(w + l.s_pixels, p->pixels.data(), 16 * (size_t)p->n_obs, cudaMemcpyHostToDevice, s));
+    OrderBuffers b{};
+    b.cam_idx = (const uint32_t*)(w + l.s_cam_idx);
+    b.pt_idx = (const uint32_t*)(w + l.s_pt_idx);
+    b.pixels = (const double*)(w + l.s_pixels);
+    b.pt_key = (uint32_t*)(w + l.s_pt_key);
+    b.tile_cnt = (uint32_t*)(w + l.s_tile_cnt);
+    b.keys = (uint64_t*)(w + l.s_keys);
+    b.vals = (uint32_t*)(w + l.s_vals);
+    b.sort_cap = l.sort_cap;
+    p->vf = make_views<float>(p);
+    p->vd = make_views<double>(p);
+    if (p->precision == BA_PREC_MIXED) build_order<float>(p->vf, b, s);
+    else build_order<double>(p->vd, b, s);
+    GBBA_CUDA(cudaGetLastError());
+    // the scratch overlapped the solver arrays: clear them before first use
+    const size_t ub = l.vec[0];
+    GBBA_CUDA(cudaMemsetAsync(w + ub, 0, l.total - ub, s));
+    GBBA_CUDA(cudaStreamSynchronize(s));
+    p->bound = true;
+    return BA_OK;
+}
+
+ba_status ba_set_params(ba_problem* p, const double* cams, const double* pts) {
+    ba_status st = check_bound(p, "ba_set_params");
+    if (st) return st;
+    if (!cams || !pts) {
+        set_error("ba_set_params: null pointer");
+        return BA_ERR_INVALID_ARG;
+    }
+    double* stg = (double*)(p->ws + p->lay.staging);
+    GBBA_CUDA(cudaMemcpyAsync(stg, cams, 72 * (size_t)p->n_cams, cudaMemcpyHostToDevice, p->stream));
+    GBBA_CUDA(cudaMemcpyAsync(stg + 9 * (size_t)p->n_cams, pts, 24 * (size_t)p->n_pts, cudaMemcpyHostToDevice, p->stream));
+    return ba_set_params_device(p, stg, stg + 9 * (size_t)p->n_cams, 1);
+}
+
+ba_status ba_get_params(ba_problem* p, double* cams, double* pts) {
+    ba_status st = check_bound(p, "ba_get_params");
+    if (st) return st;
+    if (!cams || !pts) {
+        set_error("ba_get_params: null pointer");
+        return BA_ERR_INVALID_ARG;
+    }
+    double* stg = (double*)(p->ws + p->lay.staging);
+    st = ba_get_params_device(p, stg, stg + 9 * (size_t)p->n_cams, 1);
+    if (st) return st;
+    GBBA_CUDA(cudaMemcpyAsync(cams, stg, 72 * (size_t)p->n_cams, cudaMemcpyDeviceToHost, p->stream));
+    GBBA_CUDA(cudaMemcpyAsync(pts, stg + 9 * (size_t)p->n_cams, 24 * (size_t)p->n_pts, cudaMemcpyDeviceToHost, p->stream));
+    GBBA_CUDA(cudaStreamSynchronize(p->stream));
+    return BA_OK;
+}
+
+ba_status ba_set_params_device(ba_problem* p, const void* cams, const void* pts, int32_t dtype) {
+    ba_status st = check_bound(p, "ba_set_params_device");
+    if (st) return st;
+    if (!cams || !pts || (dtype != 0 && dtype != 1)) {
+        set_error("ba_set_params_device: null pointer or bad dtype %d", dtype);
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->precision != BA_PREC_MIXED) {
+        set_error("ba_set_params_device: FP64 form not built yet");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    launch_pack(p->vf, p->L, p->stream, cams, pts, dtype);
+    GBBA_CUDA(cudaGetLastError());
+    p->linearized = false;
+    return BA_OK;
+}
+
+ba_status ba_get_params_device(ba_problem* p, void* cams, void* pts, int32_t dtype) {
+    ba_status st = check_bound(p, "ba_get_params_device");
+    if (st) return st;
+    if (!cams || !pts || (dtype != 0 && dtype != 1)) {
+        set_error("ba_get_params_device: null pointer or bad dtype %d", dtype);
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->precision != BA_PREC_MIXED) {
+        set_error("ba_get_params_device: FP64 form not built yet");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    launch_unpack(p->vf, p->L, p->stream, p->vf.x, cams, pts, dtype);
+    GBBA_CUDA(cudaGetLastError());
+    return BA_OK;
+}
+
+static ba_status read_state(ba_problem* p, DevState* host) {
+    GBBA_CUDA(cudaMemcpyAsync(host, p->ws + p->lay.state, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
+    GBBA_CUDA(cudaStreamSynchronize(p->stream));
+    return BA_OK;
+}
+
+ba_status ba_evaluate(ba_problem* p, double* cost_out, void* residuals, void* jacobian) {
+    ba_status st = check_bound(p, "ba_evaluate");
+    if (st) return st;
+    if (p->precision != BA_PREC_MIXED) {
+        set_error("ba_evaluate: FP64 form not built yet");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    const Views<float>& v = p->vf;
+    launch_camera_precompute(v, p->L, p->stream);
+    launch_linearize(v, p->L, p->stream, 2, (float*)residuals, (float*)jacobian, 0, 0);
+    GBBA_CUDA(cudaGetLastError());
+    p->linearized = true;
+    if (cost_out) {
+        double c = 0;
+        GBBA_CUDA(cudaMemcpyAsync(&c, &v.st->cost_out, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        GBBA_CUDA(cudaStreamSynchronize(p->stream));
+        *cost_out = c;
+    }
+    return BA_OK;
+}
+
+static ba_status check_options(const ba_options* o) {
+    if (!o) {
+        set_error("null options");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (o->max_lm_iters < 0 || o->max_pcg_iters < 0 || !(o->pcg_rel_tol >= 0) || !(o->initial_trust_region > 0) ||
+        !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0)) {
+        set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive)");
+        return BA_ERR_INVALID_ARG;
+    }
+    return BA_OK;
+}
+
+static ba_status write_options(ba_problem* p, const ba_options* o) {
+    DevOptions d{};
+    d.max_lm = o->max_lm_iters;
+    d.max_pcg = o->max_pcg_iters;
+    d.tol = o->pcg_rel_tol;
+    d.mu0 = 1.0 / o->initial_trust_region;
+    d.min_diag = o->min_diag;
+    d.max_diag = o->max_diag;
+    d.max_mu = o->max_mu;
+    d.eps = o->eps_depth;
+    static_assert(offsetof(DevState, opt) == 0, "options first");
+    GBBA_CUDA(cudaMemcpyAsync(p->ws + p->lay.state, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
+    return BA_OK;
+}
+
+ba_status ba_get_stats(ba_problem* p, ba_stats* stats, ba_iter_stat* hist, int32_t cap) {
+    ba_status st = check_bound(p, "ba_get_stats");
+    if (st) return st;
+    if (!stats) {
+        set_error("ba_get_stats: null stats");
+        return BA_ERR_INVALID_ARG;
+    }
+    DevState* h = new DevState;
+    st = read_state(p, h);
+    if (st) {
+        delete h;
+        return st;
+    }
+    stats->initial_cost = h->F0;
+    stats->final_cost = h->F;
+    stats->lm_iters = h->lm_iter;
+    stats->accepted = h->n_accepted;
+    stats->pcg_iters_total = h->pcg_total;
+    stats->status = h->status;
+    stats->solve_ns = h->t_end - h->t_start;
+    if (hist && cap > 0) {
+        const int n = std::min(std::min(cap, h->lm_iter), HIST_CAP);
+        static_assert(sizeof(IterRec) == sizeof(ba_iter_stat), "history record layout");
+        memcpy(hist, h->hist, sizeof(IterRec) * (size_t)n);
+    }
+    delete h;
+    return BA_OK;
+}
+
+ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_stat* hist, int32_t cap) {
+    ba_status st = check_bound(p, "ba_solve");
+    if (st) return st;
+    if ((st = check_options(o))) return st;
+    if (p->precision != BA_PREC_MIXED) {
+        set_error("ba_solve: FP64 form not built yet");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    if ((st = write_options(p, o))) return st;
+    if (o->use_graph) {
+        if (!p->graph.exec && (st = build_graph_mixed(p))) return st;
+        GBBA_CUDA(cudaGraphLaunch(p->graph.exec, p->stream));
+    } else {
+        enqueue_solve_predicated_mixed(p, *o);
+        GBBA_CUDA(cudaGetLastError());
+    }
+    p->linearized = true;
+    if (!stats) return BA_OK;
+    return ba_get_stats(p, stats, hist, cap);
+}
+
+ba_status ba_apply_normal(ba_problem* p, double mu, const void* vin, void* out, double* vAv) {
+    ba_status st = check_bound(p, "ba_apply_normal");
+    if (st) return st;
+    if (!vin || !out || !(mu >= 0)) {
+        set_error("ba_apply_normal: null vector or negative mu");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->precision != BA_PREC_MIXED) {
+        set_error("ba_apply_normal: FP64 form not built yet");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    if (!p->linearized) {
+        set_error("ba_apply_normal: call ba_evaluate first");
+        return BA_ERR_STATE;
+    }
+    const Views<float>& v = p->vf;
+    cudaStream_t s = p->stream;
+    // state: mu, an active LM iteration so the preconditioner kernel runs
+    DevState* dst = v.st;
+    GBBA_CUDA(cudaMemcpyAsync(&dst->mu, &mu, sizeof(double), cudaMemcpyHostToDevice, s));
+    int32_t one = 1;
+    GBBA_CUDA(cudaMemcpyAsync(&dst->lm_active, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    launch_precond(v, p->L, s, 0, 0);
+    launch_set_direction(v, p->L, s, (const float*)vin);
+    launch_matvec(v, p->L, s, nullptr);
+    launch_normal_out(v, p->L, s, (float*)out);
+    GBBA_CUDA(cudaGetLastError());
+    if (vAv) {
+        double jp2 = 0, pdp = 0;
+        GBBA_CUDA(cudaMemcpyAsync(&jp2, &dst->jp2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GBBA_CUDA(cudaMemcpyAsync(&pdp, &dst->pDp, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GBBA_CUDA(cudaStreamSynchronize(s));
+        *vAv = jp2 + mu * pdp;
+    }
+    return BA_OK;
+}
+
+ba_status ba_repeat_normal(ba_problem* p, int32_t launches) {
+    ba_status st = check_bound(p, "ba_repeat_normal");
+    if (st) return st;
+    if (launches < 0) {
+        set_error("ba_repeat_normal: negative count");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->precision != BA_PREC_MIXED) {
+        set_error("ba_repeat_normal: FP64 form not built yet");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    if (!p->linearized) {
+        set_error("ba_repeat_normal: call ba_apply_normal first");
+        return BA_ERR_STATE;
+    }
+    for (int i = 0; i < launches; ++i) launch_matvec(p->vf, p->L, p->stream, nullptr);
+    GBBA_CUDA(cudaGetLastError());
+    return BA_OK;
+}
+
+// ---- not yet available in this build --------------------------------------------
+
+ba_status ba_cost_forward(ba_problem*, const void*, const void*, int32_t, double*) {
+    set_error("ba_cost_forward: not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+ba_status ba_cost_backward(ba_problem*, const void*, const void*, int32_t, const double*, void*, void*) {
+    set_error("ba_cost_backward: not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+ba_status ba_batch_create(int32_t, const int32_t*, const int32_t*, const int64_t*, const uint32_t*,
+                          const uint32_t*, const double*, ba_batch** out) {
+    if (out) *out = nullptr;
+    set_error("ba_batch_create: not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+void ba_batch_destroy(ba_batch*) {}
+ba_status ba_batch_workspace_size(const ba_batch*, size_t*) {
+    set_error("not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+ba_status ba_batch_bind_workspace(ba_batch*, void*, size_t, void*) {
+    set_error("not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+ba_status ba_batch_set_params(ba_batch*, const double*, const double*) {
+    set_error("not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+ba_status ba_batch_get_params(ba_batch*, double*, double*) {
+    set_error("not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+ba_status ba_batch_solve(ba_batch*, const ba_options*, ba_stats*) {
+    set_error("not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+ba_status ba_batch_get_costs(ba_batch*, double*, double*) {
+    set_error("not implemented");
+    return BA_ERR_NOT_IMPLEMENTED;
+}
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// Device-side building blocks shared by the kernels of libgbba.
+//
+// Camera model: Snavely reprojection factor, Sec. VI-A of arXiv 2605.30583.
+// Jacobian: closed form derived by hand (Sec. V asks for the Jacobian of each
+// factor with respect to its tunable nodes); the derivation is in the comments of
+// proj_jacobian below.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "layout.h"
+
+namespace gbba {
+
+// ------------------------------------------------------------------ reductions ---
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the block, in a fixed order; valid in thread 0.  `sh` holds at
+// least blockDim.x / 32 doubles.  Contains __syncthreads.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; ++i) s += sh[i];
+    }
+    return s;
+}
+
+// Grid-wide reduction of NV doubles with a deterministic result: every block writes
+// its partial sums to partials[block * NV + k]; the last block to finish sums the
+// partials in block order and returns true (the totals are then in out[0..NV) of
+// thread 0).  ticket is reset by the last block so the next launch can reuse it.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* partials,
+                                            unsigned int* ticket, double (&out)[NV]) {
+    __shared__ double sh[32];
+    __shared__ bool is_last;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = block_sum(v[k], sh);
+        if (threadIdx.x == 0) partials[blockIdx.x * NV + k] = s;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = 0.0;
+        for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            s += __ldcg(&partials[b * NV + k]);
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) out[k] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+    return true;
+}
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------ camera precompute ---
+
+// Rodrigues coefficients A = sin(th)/th, B = (1 - cos th)/th^2 and the left-Jacobian
+// coefficient C = (th - sin th)/th^3, evaluated in FP64.  For th^2 < 1e-4 the Taylor
+// series to th^6 are used (no cancellation; truncation below 1e-16 there).
+__device__ __forceinline__ void rodrigues_coeffs(double th2, double& A, double& B, double& C) {
+    if (th2 < 1e-4) {
+        A = 1.0 + th2 * (-1.0 / 6.0 + th2 * (1.0 / 120.0 + th2 * (-1.0 / 5040.0)));
+        B = 0.5 + th2 * (-1.0 / 24.0 + th2 * (1.0 / 720.0 + th2 * (-1.0 / 40320.0)));
+        C = 1.0 / 6.0 + th2 * (-1.0 / 120.0 + th2 * (1.0 / 5040.0 + th2 * (-1.0 / 362880.0)));
+    } else {
+        const double th = sqrt(th2);
+        double s, c, sh, ch;
+        sincos(th, &s, &c);
+        sincos(0.5 * th, &sh, &ch);
+        A = s / th;
+        B = 2.0 * sh * sh / th2;
+        C = (th - s) / (th2 * th);
+    }
+}
+
+// Writes one camera record (layout.h, CamPre) from 9 parameters (w, t, f, k1, k2):
+// R(w) = I + A [w]x + B [w]x^2 and J_l(w) = I + B [w]x + C [w]x^2, where J_l is the
+// left Jacobian of the rotation exponential: R(w + d) = Exp(J_l(w) d) R(w) + O(|d|^2),
+// so d(R(w) X)/dw . d = (J_l d) x (R X).
+__device__ __forceinline__ void camera_record(const double* c, float* out) {
+    const double w0 = c[0], w1 = c[1], w2 = c[2];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+    double A, B, C;
+    rodrigues_coeffs(th2, A, B, C);
+    // [w]x and [w]x^2 = w w^T - th2 I
+    const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+    const double K2[9] = {w0 * w0 - th2, w0 * w1, w0 * w2,
+                          w1 * w0, w1 * w1 - th2, w1 * w2,
+                          w2 * w0, w2 * w1, w2 * w2 - th2};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const double I = (i % 4 == 0) ? 1.0 : 0.0;
+        out[CP_R + i] = (float)(I + A * K[i] + B * K2[i]);
+        out[CP_JL + i] = (float)(I + B * K[i] + C * K2[i]);
+    }
+    out[CP_T + 0] = (float)c[3];
+    out[CP_T + 1] = (float)c[4];
+    out[CP_T + 2] = (float)c[5];
+    out[CP_F] = (float)c[6];
+    out[CP_K1] = (float)c[7];
+    out[CP_K2] = (float)c[8];
+    out[CP_PAD] = 0.0f;
+}
+
+// ------------------------------------------------------------- projection core ---
+
+struct Cam {
+    float R[9], t[3], f, k1, k2;
+};
+
+__device__ __forceinline__ Cam load_cam(const float* __restrict__ rec) {
+    const float4* r4 = reinterpret_cast<const float4*>(rec);
+    const float4 a = __ldg(r4 + 0), b = __ldg(r4 + 1), c = __ldg(r4 + 2), d = __ldg(r4 + 3);
+    Cam m;
+    m.R[0] = a.x; m.R[1] = a.y; m.R[2] = a.z; m.R[3] = a.w;
+    m.R[4] = b.x; m.R[5] = b.y; m.R[6] = b.z; m.R[7] = b.w;
+    m.R[8] = c.x; m.t[0] = c.y; m.t[1] = c.z; m.t[2] = c.w;
+    m.f = d.x; m.k1 = d.y; m.k2 = d.z;
+    return m;
+}
+
+// Geometry of one observation: RX = R X, P = RX + t, iz = 1/d_safe, normalised point
+// p, |p|^2, radial scale s = 1 + k1 |p|^2 + k2 |p|^4, and A = d(pixel)/dP (2x3).
+//
+// pixel = f s(n2) p with p = -P.xy / d_safe, n2 = |p|^2.
+//   d(pixel)/dp = f (s I + 2 s' p p^T),  s' = k1 + 2 k2 n2            (2x2, symmetric M)
+//   dp/dP       = -iz [[1, 0, px], [0, 1, py]]   (d_safe shifts P.z by a constant)
+//   A = M dp/dP = -iz [M col0, M col1, px M col0 + py M col1]
+struct Geo {
+    float RX[3];
+    float p[2];
+    float n2, s;
+    float A[6];   // row-major 2x3
+};
+
+__device__ __forceinline__ Geo project_geo(const Cam& c, float X0, float X1, float X2, float eps) {
+    Geo g;
+    g.RX[0] = fmaf(c.R[0], X0, fmaf(c.R[1], X1, c.R[2] * X2));
+    g.RX[1] = fmaf(c.R[3], X0, fmaf(c.R[4], X1, c.R[5] * X2));
+    g.RX[2] = fmaf(c.R[6], X0, fmaf(c.R[7], X1, c.R[8] * X2));
+    const float P0 = g.RX[0] + c.t[0];
+    const float P1 = g.RX[1] + c.t[1];
+    const float P2 = g.RX[2] + c.t[2];
+    const float d = P2 + (P2 >= 0.0f ? eps : -eps);
+    const float iz = __frcp_rn(d);
+    g.p[0] = -P0 * iz;
+    g.p[1] = -P1 * iz;
+    g.n2 = fmaf(g.p[0], g.p[0], g.p[1] * g.p[1]);
+    const float sp = fmaf(2.0f * c.k2, g.n2, c.k1);         // s'
+    g.s = fmaf(g.n2, fmaf(c.k2, g.n2, c.k1), 1.0f);
+    const float a = c.f * g.s;
+    const float b = 2.0f * c.f * sp;
+    const float m00 = fmaf(b * g.p[0], g.p[0], a);
+    const float m01 = b * g.p[0] * g.p[1];
+    const float m11 = fmaf(b * g.p[1], g.p[1], a);
+    const float niz = -iz;
+    g.A[0] = niz * m00;
+    g.A[1] = niz * m01;
+    g.A[2] = niz * fmaf(m00, g.p[0], m01 * g.p[1]);
+    g.A[3] = niz * m01;
+    g.A[4] = niz * m11;
+    g.A[5] = niz * fmaf(m01, g.p[0], m11 * g.p[1]);
+    return g;
+}
+
+// Residual only (no Jacobian): f s p - u.
+__device__ __forceinline__ void project_residual(const Cam& c, float X0, float X1, float X2, float eps,
+                                                 float u0, float u1, float& r0, float& r1) {
+    const float P0 = fmaf(c.R[0], X0, fmaf(c.R[1], X1, c.R[2] * X2)) + c.t[0];
+    const float P1 = fmaf(c.R[3], X0, fmaf(c.R[4], X1, c.R[5] * X2)) + c.t[1];
+    const float P2 = fmaf(c.R[6], X0, fmaf(c.R[7], X1, c.R[8] * X2)) + c.t[2];
+    const float d = P2 + (P2 >= 0.0f ? eps : -eps);
+    const float iz = __frcp_rn(d);
+    const float p0 = -P0 * iz, p1 = -P1 * iz;
+    const float n2 = fmaf(p0, p0, p1 * p1);
+    const float s = fmaf(n2, fmaf(c.k2, n2, c.k1), 1.0f);
+    const float fs = c.f * s;
+    r0 = fmaf(fs, p0, -u0);
+    r1 = fmaf(fs, p1, -u1);
+}
+
+}  // namespace gbba

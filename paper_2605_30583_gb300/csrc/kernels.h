@@ -1,0 +1,62 @@
+// Host-side declarations of libgbba's kernel launchers (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "layout.h"
+
+namespace gbba {
+
+typedef unsigned long long CondHandle;   // cudaGraphConditionalHandle
+
+constexpr int LIN_TB = 128;   // threads per tile CTA, linearisation
+constexpr int MV_TB = 128;    // threads per tile CTA, normal operator
+constexpr int EV_TB = 128;    // threads per tile CTA, candidate evaluation
+
+struct LaunchCfg {
+    int item_block = 256;
+    int item_grid = 1024;   // cap on blocks of per-node kernels
+    int lin_grid = 1024;    // cap on blocks of tile kernels
+    int mv_grid = 1024;
+    int ev_grid = 1024;
+};
+
+// mixed precision (kernels_mixed.cu)
+void launch_camera_precompute(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
+void launch_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode,
+                      float* res_out, float* jac_out, CondHandle lm_cond, int use_cond);
+void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
+void launch_direction(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
+void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate);
+void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
+void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
+void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
+void launch_commit(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
+void launch_init_state(DevState* st, cudaStream_t s);
+void launch_finish_state(DevState* st, cudaStream_t s);
+void launch_pack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const void* cams,
+                 const void* pts, int dtype);
+void launch_unpack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const float* src, void* cams,
+                   void* pts, int dtype);
+void launch_set_direction(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const float* src);
+void launch_normal_out(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, float* out);
+int occupancy_blocks_linearize();
+int occupancy_blocks_matvec();
+int occupancy_blocks_eval();
+
+// ordering (order.cu).  All buffers are device memory inside the workspace.
+struct OrderBuffers {
+    const uint32_t* cam_idx;   // [n_obs] uploaded
+    const uint32_t* pt_idx;    // [n_obs]
+    const double* pixels;      // [n_obs][2]
+    uint32_t* pt_key;          // [n_pts] scratch
+    uint32_t* tile_cnt;        // [n_tiles + 1] scratch
+    uint64_t* keys;            // [pow2(max(n_obs, n_pts))] scratch
+    uint32_t* vals;            // [pow2(...)] scratch
+    size_t sort_cap;
+};
+template <typename T>
+void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s);
+
+}  // namespace gbba

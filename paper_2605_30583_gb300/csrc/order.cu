@@ -1,0 +1,240 @@
+// Locality ordering built once per bound problem (our counterpart of the
+// shared-index build of Sec. IV-A, "Shared Read/Add", of arXiv 2605.30583):
+//
+//  1. each point's key is the smallest camera index observing it; points are
+//     sorted by (key, caller index), giving the internal point order;
+//  2. tiles are TILE_PTS consecutive internal points;
+//  3. observations are sorted by (tile, camera, tile slot, caller index), so a
+//     tile's observations are contiguous and grouped into camera runs.
+//
+// Sorting is a bitonic network on (64-bit key, 32-bit value) pairs: shared-memory
+// passes for distances below 2048 elements and global passes above.  Deterministic
+// (ties broken by the value), so the same input always gives the same order.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace gbba {
+
+namespace {
+
+constexpr int LOCAL_ELEMS = 2048;
+constexpr int LOCAL_THREADS = LOCAL_ELEMS / 2;
+
+__device__ __forceinline__ bool pair_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
+    return ka < kb || (ka == kb && va < vb);
+}
+
+__global__ void k_fill_u32(uint32_t* a, size_t n, uint32_t v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+__global__ void k_point_min_camera(const uint32_t* cam_idx, const uint32_t* pt_idx, int64_t n_obs,
+                                   uint32_t* pt_key) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x)
+        atomicMin(&pt_key[pt_idx[o]], cam_idx[o]);
+}
+
+__global__ void k_point_sort_keys(const uint32_t* pt_key, int n_pts, size_t sort_n, uint64_t* keys,
+                                  uint32_t* vals) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sort_n; i += (size_t)gridDim.x * blockDim.x) {
+        if (i < (size_t)n_pts) {
+            keys[i] = ((uint64_t)pt_key[i] << 32) | (uint64_t)i;
+            vals[i] = (uint32_t)i;
+        } else {
+            keys[i] = ~0ull;
+            vals[i] = 0xffffffffu;
+        }
+    }
+}
+
+__global__ void k_point_perm(const uint32_t* vals, int n_pts, uint32_t* pt_user, uint32_t* pt_internal) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_pts; j += gridDim.x * blockDim.x) {
+        const uint32_t u = vals[j];
+        pt_user[j] = u;
+        pt_internal[u] = (uint32_t)j;
+    }
+}
+
+__global__ void k_tile_count(const uint32_t* pt_idx, const uint32_t* pt_internal, int64_t n_obs,
+                             uint32_t* tile_cnt) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&tile_cnt[pt_internal[pt_idx[o]] / TILE_PTS], 1u);
+}
+
+// Exclusive scan of cnt[0..n) into off[0..n] with one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_single(const uint32_t* cnt, int n, uint32_t* off) {
+    __shared__ uint32_t part[1024];
+    const int per = (n + 1023) / 1024;
+    const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+    uint32_t s = 0;
+    for (int i = lo; i < hi; ++i) s += cnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const uint32_t t = part[i];
+            part[i] = run;
+            run += t;
+        }
+        off[n] = run;
+    }
+    __syncthreads();
+    uint32_t run = part[threadIdx.x];
+    for (int i = lo; i < hi; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+}
+
+__global__ void k_obs_sort_keys(const uint32_t* cam_idx, const uint32_t* pt_idx, const uint32_t* pt_internal,
+                                int64_t n_obs, size_t sort_n, uint64_t* keys, uint32_t* vals) {
+    for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < sort_n; o += (size_t)gridDim.x * blockDim.x) {
+        if (o < (size_t)n_obs) {
+            const uint32_t ip = pt_internal[pt_idx[o]];
+            const uint64_t tile = ip / TILE_PTS, slot = ip % TILE_PTS;
+            keys[o] = (tile << 40) | ((uint64_t)cam_idx[o] << 16) | (slot << 8);
+            vals[o] = (uint32_t)o;
+        } else {
+            keys[o] = ~0ull;
+            vals[o] = 0xffffffffu;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_obs_gather(const uint64_t* keys, const uint32_t* vals, const double* pixels, int64_t n_obs,
+                             uint32_t* obs_key, T* obs_uv, uint32_t* obs_user) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_obs; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[j];
+        const uint32_t o = vals[j];
+        const uint32_t cam = (uint32_t)((k >> 16) & 0xffffffu);
+        const uint32_t slot = (uint32_t)((k >> 8) & 0xffu);
+        obs_key[j] = (cam << 8) | slot;
+        obs_uv[2 * j] = (T)pixels[2 * (size_t)o];
+        obs_uv[2 * j + 1] = (T)pixels[2 * (size_t)o + 1];
+        obs_user[j] = o;
+    }
+}
+
+// --- bitonic network --------------------------------------------------------------
+
+// Compare-exchange of positions i < l = i + j; ascending iff (i & k) == 0.
+__device__ __forceinline__ void cx_global(uint64_t* keys, uint32_t* vals, size_t i, size_t l, size_t k) {
+    const uint64_t ka = keys[i], kb = keys[l];
+    const uint32_t va = vals[i], vb = vals[l];
+    const bool asc = (i & k) == 0;
+    if (pair_less(kb, vb, ka, va) == asc) {
+        keys[i] = kb; keys[l] = ka;
+        vals[i] = vb; vals[l] = va;
+    }
+}
+
+__global__ void k_bitonic_global(uint64_t* keys, uint32_t* vals, size_t n, size_t k, size_t j) {
+    const size_t pairs = n / 2;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < pairs; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = 2 * j * (t / j) + (t % j);
+        cx_global(keys, vals, i, i + j, k);
+    }
+}
+
+// Runs stages (k, j) for j = j0, j0/2, ..., 1 inside blocks of `elems` elements;
+// if full_sort, first runs every k = 2 .. elems (sorting each block bitonically).
+__global__ void __launch_bounds__(LOCAL_THREADS) k_bitonic_local(uint64_t* keys, uint32_t* vals, size_t elems,
+                                                                 size_t k_outer, int full_sort) {
+    __shared__ uint64_t sk[LOCAL_ELEMS];
+    __shared__ uint32_t sv[LOCAL_ELEMS];
+    const size_t base = (size_t)blockIdx.x * elems;
+    for (size_t i = threadIdx.x; i < elems; i += blockDim.x) {
+        sk[i] = keys[base + i];
+        sv[i] = vals[base + i];
+    }
+    __syncthreads();
+    const size_t pairs = elems / 2;
+    auto stage = [&](size_t k, size_t j) {
+        for (size_t t = threadIdx.x; t < pairs; t += blockDim.x) {
+            const size_t i = 2 * j * (t / j) + (t % j), l = i + j;
+            const bool asc = ((base + i) & k) == 0;
+            const uint64_t ka = sk[i], kb = sk[l];
+            const uint32_t va = sv[i], vb = sv[l];
+            if (pair_less(kb, vb, ka, va) == asc) {
+                sk[i] = kb; sk[l] = ka;
+                sv[i] = vb; sv[l] = va;
+            }
+        }
+        __syncthreads();
+    };
+    if (full_sort) {
+        for (size_t k = 2; k <= elems; k <<= 1)
+            for (size_t j = k >> 1; j > 0; j >>= 1) stage(k, j);
+    } else {
+        for (size_t j = elems >> 1; j > 0; j >>= 1) stage(k_outer, j);
+    }
+    for (size_t i = threadIdx.x; i < elems; i += blockDim.x) {
+        keys[base + i] = sk[i];
+        vals[base + i] = sv[i];
+    }
+}
+
+void bitonic_sort(uint64_t* keys, uint32_t* vals, size_t n, cudaStream_t s) {
+    // n is a power of two >= 2
+    const size_t elems = n < (size_t)LOCAL_ELEMS ? n : (size_t)LOCAL_ELEMS;
+    const int lblocks = (int)(n / elems);
+    const int lthreads = (int)(elems / 2 < (size_t)LOCAL_THREADS ? elems / 2 : (size_t)LOCAL_THREADS);
+    k_bitonic_local<<<lblocks, lthreads, 0, s>>>(keys, vals, elems, 0, 1);
+    const int gthreads = 256;
+    const size_t gblocks_need = (n / 2 + gthreads - 1) / gthreads;
+    const int gblocks = (int)(gblocks_need > 65535 ? 65535 : gblocks_need);
+    for (size_t k = 2 * elems; k <= n; k <<= 1) {
+        for (size_t j = k >> 1; j >= elems; j >>= 1) k_bitonic_global<<<gblocks, gthreads, 0, s>>>(keys, vals, n, k, j);
+        k_bitonic_local<<<lblocks, lthreads, 0, s>>>(keys, vals, elems, k, 0);
+    }
+}
+
+inline size_t pow2_at_least(size_t n) {
+    size_t p = 2;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+inline int blocks_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b > 8192 ? 8192 : b);
+}
+
+}  // namespace
+
+template <typename T>
+void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s) {
+    const int TB = 256;
+    uint32_t* pt_user = const_cast<uint32_t*>(v.pt_user);
+    uint32_t* pt_internal = const_cast<uint32_t*>(v.pt_internal);
+    uint32_t* tile_off = const_cast<uint32_t*>(v.tile_off);
+    // 1. point keys and point order
+    k_fill_u32<<<blocks_for(v.n_pts, TB), TB, 0, s>>>(b.pt_key, (size_t)v.n_pts, 0xffffffffu);
+    k_point_min_camera<<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.cam_idx, b.pt_idx, v.n_obs, b.pt_key);
+    const size_t np2 = pow2_at_least((size_t)v.n_pts);
+    k_point_sort_keys<<<blocks_for(np2, TB), TB, 0, s>>>(b.pt_key, v.n_pts, np2, b.keys, b.vals);
+    bitonic_sort(b.keys, b.vals, np2, s);
+    k_point_perm<<<blocks_for(v.n_pts, TB), TB, 0, s>>>(b.vals, v.n_pts, pt_user, pt_internal);
+    // 2. tiles
+    k_fill_u32<<<blocks_for(v.n_tiles, TB), TB, 0, s>>>(b.tile_cnt, (size_t)v.n_tiles, 0u);
+    k_tile_count<<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.pt_idx, pt_internal, v.n_obs, b.tile_cnt);
+    k_scan_single<<<1, 1024, 0, s>>>(b.tile_cnt, v.n_tiles, tile_off);
+    // 3. observation order
+    const size_t no2 = pow2_at_least((size_t)v.n_obs);
+    k_obs_sort_keys<<<blocks_for(no2, TB), TB, 0, s>>>(b.cam_idx, b.pt_idx, pt_internal, v.n_obs, no2, b.keys, b.vals);
+    bitonic_sort(b.keys, b.vals, no2, s);
+    k_obs_gather<T><<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.keys, b.vals, b.pixels, v.n_obs,
+                                                           const_cast<uint32_t*>(v.obs_key),
+                                                           const_cast<T*>(v.obs_uv),
+                                                           const_cast<uint32_t*>(v.obs_user));
+}
+
+template void build_order<float>(const Views<float>&, const OrderBuffers&, cudaStream_t);
+template void build_order<double>(const Views<double>&, const OrderBuffers&, cudaStream_t);
+
+}  // namespace gbba

@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI: the library loads, exports every symbol the public
+header declares, and validates its inputs without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2605_30583_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_30583_gb300 import build
+    build.build()
+    return binding.lib()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "gbba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ba_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(binding.SIGNATURES), set(names) ^ set(binding.SIGNATURES)
+
+
+def test_options_defaults_follow_the_paper(lib):
+    o = binding.default_options()
+    assert o.initial_trust_region == 100.0 and o.pcg_rel_tol == 1e-3      # Sec. VI settings
+    assert o.max_lm_iters == 20 and o.max_pcg_iters == 50 and o.use_graph == 1
+    assert lib.ba_abi_version() == 1
+
+
+def _create(n_cams, n_pts, ci, pi, px, prec=0):
+    h = ctypes.c_void_p()
+    ci = np.ascontiguousarray(ci, np.uint32)
+    pi = np.ascontiguousarray(pi, np.uint32)
+    px = np.ascontiguousarray(px, np.float64)
+    st = binding.lib().ba_problem_create(n_cams, n_pts, len(ci), ci.ctypes.data, pi.ctypes.data,
+                                          px.ctypes.data, prec, ctypes.byref(h))
+    return st, h
+
+
+def test_create_rejects_bad_indices_and_single_views(lib):
+    px = np.zeros((4, 2))
+    st, h = _create(2, 2, [0, 1, 2, 0], [0, 0, 1, 1], px)
+    assert st == 1 and not h.value
+    assert b"out of range" in lib.ba_last_error()
+    st, h = _create(2, 2, [0, 1, 0, 1], [0, 0, 1, 0], px)      # point 1 seen once
+    assert st == 1 and b"at least 2" in lib.ba_last_error()
+    st, h = _create(0, 2, [0, 1, 0, 1], [0, 0, 1, 1], px)
+    assert st == 1
+    st, h = _create(2, 2, [0, 1, 0, 1], [0, 0, 1, 1], px, prec=7)
+    assert st == 1
+
+
+def test_create_and_workspace_size_without_gpu(lib):
+    st, h = _create(3, 2, [0, 1, 2, 0], [0, 0, 1, 1], np.zeros((4, 2)))
+    assert st == 0 and h.value
+    n = ctypes.c_size_t()
+    assert lib.ba_workspace_size(h, ctypes.byref(n)) == 0 and n.value > 0
+    # calls that need a bound workspace report a state error, not a crash
+    c = np.zeros((3, 9))
+    p = np.zeros((2, 3))
+    assert lib.ba_set_params(h, c.ctypes.data, p.ctypes.data) == 7
+    o = binding.default_options()
+    assert lib.ba_solve(h, ctypes.byref(o), None, None, 0) == 7
+    lib.ba_problem_destroy(h)
+
+
+def test_workspace_grows_with_problem_and_fp64_is_larger(lib):
+    sizes = {}
+    for prec in (0, 1):
+        st, h = _create(4, 3, [0, 1, 2, 3, 0, 1], [0, 0, 1, 1, 2, 2], np.zeros((6, 2)), prec)
+        n = ctypes.c_size_t()
+        lib.ba_workspace_size(h, ctypes.byref(n))
+        sizes[prec] = n.value
+        lib.ba_problem_destroy(h)
+    assert sizes[1] > sizes[0]

@@ -1,0 +1,153 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Inputs are rounded to FP32 first, so both sides see bit-identical parameters and
+pixels and only arithmetic differs.  Tolerances (derived from FP32 arithmetic):
+  * residuals: |r_gpu - r_ref|_2 <= 1e-5 |r_ref|_2 at the initial point, and per
+    element |dr| <= 2e-4 px + 1e-5 |r| (a pixel of ~500 px carries an FP32 rounding
+    of ~3e-5 px per operation);
+  * Jacobian blocks, normal operator: relative 2-norm error <= 1e-5 / 1e-4;
+  * final LM cost: relative error <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+from oracle import ba_oracle as O
+from paper_2605_30583_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2605_30583_gb300 import binding, build
+    build.build()
+    binding.lib()
+    return binding
+
+
+def _problem(B, prob, precision="mixed"):
+    p = B.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels, precision=precision)
+    p.set_params(prob.cams_init, prob.pts_init)
+    return p
+
+
+def _ragged(seed=3):
+    # 1000 points = 7 full tiles of 128 plus a ragged tail of 104
+    return synth.round_to_f32(synth.make_config("tiny", seed=seed))
+
+
+def test_residuals_match_oracle(B):
+    prob = _ragged()
+    p = _problem(B, prob)
+    cost, r, _ = p.evaluate(residuals=True)
+    r = r.double().cpu().numpy()
+    ref = O.residuals(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
+    assert np.linalg.norm(r - ref) <= 1e-5 * np.linalg.norm(ref)
+    assert np.all(np.abs(r - ref) <= 2e-4 + 1e-5 * np.abs(ref))
+    ref_cost = 0.5 * float(np.sum(ref * ref))
+    assert abs(cost - ref_cost) <= 1e-5 * ref_cost
+
+
+def test_jacobian_matches_oracle(B):
+    prob = _ragged(5)
+    p = _problem(B, prob)
+    _, _, J = p.evaluate(jacobian=True)
+    J = J.double().cpu().numpy()
+    _, Jc, Jp = O.jacobian_blocks(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
+    err_c = np.linalg.norm(J[:, :, :9] - Jc, axis=(1, 2)) / np.linalg.norm(Jc, axis=(1, 2))
+    err_p = np.linalg.norm(J[:, :, 9:] - Jp, axis=(1, 2)) / np.linalg.norm(Jp, axis=(1, 2))
+    assert err_c.max() < 1e-5, err_c.max()
+    assert err_p.max() < 1e-5, err_p.max()
+
+
+def test_normal_operator_matches_oracle(B):
+    import torch
+    prob = _ragged(9)
+    p = _problem(B, prob)
+    p.evaluate()
+    lin = O.linearize(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
+    D = O.damping_diag(lin.J)
+    rng = np.random.default_rng(0)
+    n = 9 * prob.n_cams + 3 * prob.n_pts
+    for mu in (0.0, 0.01, 3.0):
+        v = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+        out, vav = p.apply_normal(mu, torch.from_numpy(v))
+        ref = O.normal_matvec(lin, D, mu, v)
+        out = out.double().cpu().numpy()
+        assert np.linalg.norm(out - ref) <= 1e-4 * np.linalg.norm(ref)
+        assert abs(vav - v @ ref) <= 1e-4 * abs(v @ ref)
+        # adjointness of the operator: <A v, w> = <v, A w>
+        w = rng.standard_normal(n).astype(np.float32).astype(np.float64)
+        out_w, _ = p.apply_normal(mu, torch.from_numpy(w))
+        a, b = float(out @ w), float(v @ out_w.double().cpu().numpy())
+        assert abs(a - b) <= 1e-4 * (abs(a) + abs(b))
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_lm_solve_matches_oracle(B, use_graph):
+    prob = _ragged(11)
+    p = _problem(B, prob)
+    opts = dict(max_lm_iters=12, max_pcg_iters=50)
+    res = p.solve(use_graph=use_graph, **opts)
+    ref = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels, O.LMOptions(**opts))
+    assert res.status == 0
+    assert res.lm_iters == ref.lm_iters
+    assert abs(res.initial_cost - ref.initial_cost) <= 1e-5 * ref.initial_cost
+    assert abs(res.final_cost - ref.final_cost) <= 1e-4 * ref.final_cost, (res.final_cost, ref.final_cost)
+    # accepted steps strictly decrease the cost
+    for h in res.history:
+        if h["accepted"]:
+            assert h["cost_new"] < h["cost"]
+    # the parameters on the device reproduce the reported cost
+    c, q = p.get_params()
+    assert abs(O.cost(c, q, prob.cam_idx, prob.pt_idx, prob.pixels) - res.final_cost) <= 1e-5 * res.final_cost
+
+
+def test_graph_and_predicated_solves_agree(B):
+    prob = _ragged(13)
+    a = _problem(B, prob).solve(use_graph=1, max_lm_iters=8)
+    b = _problem(B, prob).solve(use_graph=0, max_lm_iters=8)
+    assert a.lm_iters == b.lm_iters
+    assert abs(a.final_cost - b.final_cost) <= 1e-6 * a.final_cost
+
+
+def test_repeated_solves_reuse_the_graph(B):
+    prob = _ragged(17)
+    p = _problem(B, prob)
+    r1 = p.solve(max_lm_iters=5)
+    p.set_params(prob.cams_init, prob.pts_init)
+    r2 = p.solve(max_lm_iters=5)
+    assert abs(r1.final_cost - r2.final_cost) <= 1e-6 * r1.final_cost
+    # zero LM iterations: nothing changes, final cost = initial cost
+    p.set_params(prob.cams_init, prob.pts_init)
+    r0 = p.solve(max_lm_iters=0)
+    assert r0.lm_iters == 0 and r0.final_cost == r0.initial_cost
+
+
+def test_noise_free_ground_truth_has_zero_cost(B):
+    prob = synth.make_problem(16, 300, ("poisson", 3.0), "uniform", seed=21, noise_px=0.0, perturb=False)
+    prob = synth.round_to_f32(prob)
+    p = B.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels)
+    p.set_params(prob.cams_gt.astype(np.float32), prob.pts_gt.astype(np.float32))
+    cost, r, _ = p.evaluate(residuals=True)
+    ref = O.residuals(prob.cams_gt.astype(np.float32).astype(np.float64),
+                      prob.pts_gt.astype(np.float32).astype(np.float64), prob.cam_idx, prob.pt_idx, prob.pixels)
+    # FP32 ulp of a ~500 px pixel is ~3e-5 px; the rounded inputs leave a residual of that order
+    assert np.abs(r.double().cpu().numpy() - ref).max() < 2e-4
+
+
+def test_single_tile_and_heavy_point(B):
+    """One point seen by every camera (a 40-observation run in a tile) and tiny tiles."""
+    prob = synth.make_problem(40, 5, ("poisson", 60.0), "uniform", seed=4)
+    prob = synth.round_to_f32(prob)
+    p = _problem(B, prob)
+    cost, r, J = p.evaluate(residuals=True, jacobian=True)
+    ref = O.residuals(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
+    assert np.linalg.norm(r.double().cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+    res = p.solve(max_lm_iters=5)
+    refs = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels,
+                      O.LMOptions(max_lm_iters=5))
+    assert abs(res.final_cost - refs.final_cost) <= 1e-4 * max(refs.final_cost, 1e-9) + 1e-6
