@@ -389,6 +389,8 @@ static ba_status check_bound(const ba_problem* p, const char* who) {
     return BA_OK;
 }
 
+static ba_status write_options(ba_problem* p, const ba_options* o);
+
 ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream) {
     if (!p || !ws) {
         set_error("ba_bind_workspace: null pointer");
@@ -425,6 +427,13 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
     cudaStream_t s = p->stream;
     GBBA_CUDA(cudaMemsetAsync(w + l.state, 0, sizeof(DevState), s));
     GBBA_CUDA(cudaMemsetAsync(w + l.partials, 0, sizeof(double) * MAX_GRID * NPART, s));
+    {
+        // evaluation and operator calls made before any solve use the default options
+        ba_options d;
+        ba_options_default(&d);
+        ba_status ost = write_options(p, &d);
+        if (ost) return ost;
+    }
     GBBA_CUDA(cudaMemcpyAsync(w + l.s_cam_idx, p->cam_idx.data(), 4 * (size_t)p->n_obs, cudaMemcpyHostToDevice, s));
     GBBA_CUDA(cudaMemcpyAsync(w + l.s_pt_idx, p->pt_idx.data(), 4 * (size_t)p->n_obs, cudaMemcpyHostToDevice, s));
     GBBA_CUDA(cudaMemcpyAsync(w + l.s_pixels, p->pixels.data(), 16 * (size_t)p->n_obs, cudaMemcpyHostToDevice, s));
