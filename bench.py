@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1, 2],
+                    help="1: conditional-loop graph; 2: unrolled predicated graph; 0: host-enqueued sequence")
     return ap.parse_args()
 
 
@@ -195,7 +197,7 @@ def run_ours(args, rank, world, local_rank):
     base_seed = synth.CONFIGS[args.config]["seed"]
     prob = synth.make_config(args.config, seed=base_seed + 7919 * rank)
     target = golden_cost(args.config) if rank == 0 else None
-    opts = binding.default_options()
+    opts = binding.default_options(use_graph=args.graph_mode)
 
     p = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels)
     cams0 = torch.tensor(prob.cams_init, dtype=torch.float64, device=dev)
@@ -283,6 +285,11 @@ def run_ours(args, rank, world, local_rank):
                     ms_per_launch=mv_ms, algorithmic_bytes=nb, algorithmic_flops=nf)
     other = roof_hbm if roofline["bound"] == "alu" else roof_alu
 
+    # ---- per-kernel times in isolation (CUDA events, warm, back-to-back)
+    p.set_params(cams0, pts0)
+    p.evaluate()
+    kernel_us = p.profile_kernels(20)
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -361,7 +368,7 @@ def run_ours(args, rank, world, local_rank):
         "time_to_cost_ms": ttc, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
         "step_ms": step_ms,
         "roofline": roofline, "roofline_other": other,
-        "e2e": e2e, "fp64_plain": fp64, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob)

@@ -68,8 +68,16 @@ typedef struct {
     double max_diag;
     double max_mu;                /* stop when mu exceeds this, default 1e32            */
     double eps_depth;             /* epsilon of d_safe (Sec. VI-A), default 0           */
-    int32_t use_graph;            /* 1: one CUDA graph with device-side loops (default) */
-    int32_t reserved;
+    int32_t use_graph;            /* 1 (default): one CUDA graph; its LM and PCG loops are
+                                     device-driven conditional nodes, except with the
+                                     persistent PCG kernel, where the graph holds the
+                                     fixed LM sequence (as for 2);
+                                     2: one graph of the fixed sequence of max_lm_iters x
+                                     max_pcg_iters slots, idle slots return at once;
+                                     0: the same sequence launched from the host    */
+    int32_t pcg_kernel;           /* 0: one persistent cooperative kernel per PCG solve when
+                                     every CTA's tiles fit in shared memory (default);
+                                     1: separate kernels per PCG iteration           */
 } ba_options;
 
 /* One LM iteration (Sec. V): cost before the step, candidate cost, damping used,
@@ -168,6 +176,14 @@ ba_status ba_apply_normal(ba_problem* problem, double mu, const void* v, void* o
 /* Launches the normal-operator kernel `launches` times back to back on the bound
  * stream with the launch configuration the solver uses (timing aid). */
 ba_status ba_repeat_normal(ba_problem* problem, int32_t launches);
+
+/* Times each kernel of the solver in isolation with CUDA events on the bound stream:
+ * `reps` back-to-back launches each, after a prior ba_evaluate or ba_solve.  Writes
+ * the average microseconds per launch into us_out[0..n) in this order: camera
+ * records, linearisation, preconditioner, normal operator (matvec), PCG update,
+ * candidate step, candidate evaluation, commit.  Leaves the solver state undefined
+ * (the next ba_solve starts afresh).  Synchronises. */
+ba_status ba_profile_kernels(ba_problem* problem, int32_t reps, double* us_out, int32_t n);
 
 /* Total reprojection cost F = 1/2 sum |r|^2 (FP64) at caller parameters, and its
  * adjoint.  cams/pts are device arrays in user layout of dtype (0 float32,

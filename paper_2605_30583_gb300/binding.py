@@ -31,7 +31,7 @@ class Options(ctypes.Structure):
     _fields_ = [("max_lm_iters", ctypes.c_int32), ("max_pcg_iters", ctypes.c_int32),
                 ("pcg_rel_tol", ctypes.c_double), ("initial_trust_region", ctypes.c_double),
                 ("min_diag", ctypes.c_double), ("max_diag", ctypes.c_double), ("max_mu", ctypes.c_double),
-                ("eps_depth", ctypes.c_double), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("eps_depth", ctypes.c_double), ("use_graph", ctypes.c_int32), ("pcg_kernel", ctypes.c_int32)]
 
 
 class IterStat(ctypes.Structure):
@@ -68,6 +68,7 @@ SIGNATURES = {
     "ba_get_stats": (I32, [P, ctypes.POINTER(Stats), ctypes.POINTER(IterStat), I32]),
     "ba_apply_normal": (I32, [P, ctypes.c_double, P, P, ctypes.POINTER(ctypes.c_double)]),
     "ba_repeat_normal": (I32, [P, I32]),
+    "ba_profile_kernels": (I32, [P, I32, P, I32]),
     "ba_cost_forward": (I32, [P, P, P, I32, P]),
     "ba_cost_backward": (I32, [P, P, P, I32, P, P, P]),
     "ba_batch_create": (I32, [I32, P, P, P, P, P, P, ctypes.POINTER(P)]),
@@ -208,6 +209,14 @@ class Problem:
         vav = ctypes.c_double()
         check(lib().ba_apply_normal(self._h, float(mu), v.data_ptr(), out.data_ptr(), ctypes.byref(vav)))
         return out, vav.value
+
+    KERNELS = ("camera_records", "linearize", "precond", "matvec", "update", "candidate", "eval_candidate",
+               "commit")
+
+    def profile_kernels(self, reps=20) -> dict:
+        out = np.zeros(len(self.KERNELS))
+        check(lib().ba_profile_kernels(self._h, int(reps), _ptr(out), len(out)))
+        return dict(zip(self.KERNELS, out.tolist()))
 
     def repeat_normal(self, launches):
         check(lib().ba_repeat_normal(self._h, int(launches)))

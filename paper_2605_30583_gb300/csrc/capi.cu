@@ -25,6 +25,7 @@ void set_error(const char* fmt, ...) {
 
 ba_status cuda_status(cudaError_t e, const char* what) {
     set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+    cudaGetLastError();   // clear a non-sticky error so later calls do not report it again
     return BA_ERR_CUDA;
 }
 
@@ -55,8 +56,10 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     const size_t T = precision == BA_PREC_FP64 ? 8 : 4;
     const size_t nc = (size_t)n_cams, np = (size_t)n_pts, no = (size_t)n_obs;
     const size_t n_tiles = (np + TILE_PTS - 1) / TILE_PTS;
+    const size_t n_quads = (np + 3) / 4;
     const size_t pt_off = align_up(9 * nc, 4);
-    const size_t n_vec = pt_off + align_up(3 * np, 4);
+    const size_t n_vec = pt_off + 12 * n_quads;
+    const size_t pc_stride = align_up(9 * nc, 64);
     Bump b;
     l.state = b.take(sizeof(DevState));
     l.partials = b.take(sizeof(double) * MAX_GRID * NPART);
@@ -66,7 +69,16 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     l.tile_off = b.take(4 * (n_tiles + 1));
     l.pt_user = b.take(4 * np);
     l.pt_internal = b.take(4 * np);
+    l.obs_pm = b.take(4 * no);
+    l.pt_obs_off = b.take(4 * (np + 1));
     l.staging = b.take(8 * (9 * nc + 3 * np));
+    l.blk_tile = b.take(4 * (MAX_PBLOCKS + 1));
+    l.blk_cam_off = b.take(4 * (MAX_PBLOCKS + 1));
+    // per-CTA camera lists of the persistent PCG kernel: each CTA lists at most the
+    // cameras of its observations, so n_obs + MAX_PBLOCKS entries always suffice; the
+    // plan is only used when they fit in shared memory, so cap the region
+    l.blk_cams = b.take(4 * std::min(no + MAX_PBLOCKS, (size_t)(MAX_PBLOCKS * 4096)));
+    l.pslots = b.take(8 * PSLOT_DOUBLES);
     const size_t union_base = align_up(b.off, 256);
     // solver arrays
     Bump s;
@@ -76,10 +88,12 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     l.cam_pre_new = s.take(4 * CP_STRIDE * nc);
     l.cam_dir = s.take(4 * CD_STRIDE * nc);
     l.cam_acc = s.take(4 * CA_STRIDE * nc);
+    l.pc = s.take(4 * 2 * pc_stride);
     l.cam_lin = s.take(8 * CL_STRIDE * nc);
-    l.pt_H = s.take(T * PH_STRIDE * np);
+    l.cam_H = s.take(4 * CH_STRIDE * nc);
+    l.pt_H = s.take(T * PH_STRIDE * 4 * n_quads);
     l.Minv_c = s.take(T * MC_STRIDE * nc);
-    l.Minv_p = s.take(T * MP_STRIDE * np);
+    l.Minv_p = s.take(T * MP_STRIDE * 4 * n_quads);
     if (precision == BA_PREC_FP64) {
         l.jac = s.take(T * 24 * no);
         l.res = s.take(T * 2 * no);
@@ -109,7 +123,9 @@ Views<T> make_views(ba_problem* p) {
     v.n_cams = p->n_cams;
     v.n_pts = p->n_pts;
     v.n_tiles = p->n_tiles;
+    v.n_quads = (p->n_pts + 3) / 4;
     v.n_obs = p->n_obs;
+    v.pc_stride = (int64_t)((9 * (size_t)p->n_cams + 63) / 64 * 64);
     v.pt_off = p->pt_off;
     v.n_vec = p->n_vec;
     v.obs_key = (const uint32_t*)(w + l.obs_key);
@@ -118,13 +134,17 @@ Views<T> make_views(ba_problem* p) {
     v.tile_off = (const uint32_t*)(w + l.tile_off);
     v.pt_user = (const uint32_t*)(w + l.pt_user);
     v.pt_internal = (const uint32_t*)(w + l.pt_internal);
+    v.obs_pm = (const uint32_t*)(w + l.obs_pm);
+    v.pt_obs_off = (const uint32_t*)(w + l.pt_obs_off);
     T** vecs[9] = {&v.x, &v.x_new, &v.h, &v.r, &v.z, &v.p, &v.q, &v.g, &v.D};
     for (int i = 0; i < 9; ++i) *vecs[i] = (T*)(w + l.vec[i]);
     v.cam_pre = (float*)(w + l.cam_pre);
     v.cam_pre_new = (float*)(w + l.cam_pre_new);
     v.cam_dir = (float*)(w + l.cam_dir);
     v.cam_acc = (float*)(w + l.cam_acc);
+    v.pc = (float*)(w + l.pc);
     v.cam_lin = (double*)(w + l.cam_lin);
+    v.cam_H = (float*)(w + l.cam_H);
     v.pt_H = (T*)(w + l.pt_H);
     v.Minv_c = (T*)(w + l.Minv_c);
     v.Minv_p = (T*)(w + l.Minv_p);
@@ -146,17 +166,19 @@ static void enqueue_lm_body_mixed(ba_problem* p, cudaStream_t s, CondHandle lm_c
 
 static void enqueue_pcg_iteration_mixed(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int use_cond) {
     const Views<float>& v = p->vf;
-    launch_direction(v, p->L, s);
-    launch_matvec(v, p->L, s, &v.st->pcg_active);
+    launch_matvec(v, p->L, s, &v.st->pcg_active, v.z, 1);
     launch_update(v, p->L, s, pcg_c, use_cond);
 }
 
 static void enqueue_lm_body_mixed(ba_problem* p, cudaStream_t s, CondHandle lm_c, CondHandle pcg_c, int use_cond,
                                   cudaStream_t, bool inline_pcg, int max_pcg) {
     const Views<float>& v = p->vf;
-    launch_precond(v, p->L, s, pcg_c, use_cond);
-    if (inline_pcg)
+    launch_precond(v, p->L, s, pcg_c, use_cond, p->use_persistent ? p->pslots : nullptr);
+    if (p->use_persistent) {
+        launch_pcg_persistent(v, p->blk_tile, p->blk_cam_off, p->blk_cams, p->pslots, p->p_grid, p->p_smem, s);
+    } else if (inline_pcg) {
         for (int k = 0; k < max_pcg; ++k) enqueue_pcg_iteration_mixed(p, s, pcg_c, use_cond);
+    }
     (void)lm_c;
 }
 
@@ -210,14 +232,17 @@ static ba_status build_graph_mixed(ba_problem* p) {
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&pcg_h, lm_body, 0, 0);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s1, lm_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        enqueue_lm_body_mixed(p, s1, (CondHandle)lm_h, (CondHandle)pcg_h, 1, s2, false, 0);
-        cudaGraph_t pcg_body;
-        e = add_while_node(s1, (CondHandle)pcg_h, &pcg_body);
-        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s2, pcg_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-        if (e == cudaSuccess) {
-            enqueue_pcg_iteration_mixed(p, s2, (CondHandle)pcg_h, 1);
-            cudaGraph_t tmp;
-            e = cudaStreamEndCapture(s2, &tmp);
+        enqueue_lm_body_mixed(p, s1, (CondHandle)lm_h, (CondHandle)pcg_h, p->use_persistent ? 0 : 1, s2, false, 0);
+        if (!p->use_persistent) {
+            cudaGraph_t pcg_body;
+            e = add_while_node(s1, (CondHandle)pcg_h, &pcg_body);
+            if (e == cudaSuccess)
+                e = cudaStreamBeginCaptureToGraph(s2, pcg_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                enqueue_pcg_iteration_mixed(p, s2, (CondHandle)pcg_h, 1);
+                cudaGraph_t tmp;
+                e = cudaStreamEndCapture(s2, &tmp);
+            }
         }
         if (e == cudaSuccess) enqueue_lm_tail_mixed(p, s1, (CondHandle)lm_h, 1);
         cudaGraph_t tmp1;
@@ -243,8 +268,7 @@ static ba_status build_graph_mixed(ba_problem* p) {
     return BA_OK;
 }
 
-static void enqueue_solve_predicated_mixed(ba_problem* p, const ba_options& o) {
-    cudaStream_t s = p->stream;
+static void enqueue_solve_predicated_mixed(ba_problem* p, const ba_options& o, cudaStream_t s) {
     const Views<float>& v = p->vf;
     launch_init_state(v.st, s);
     launch_camera_precompute(v, p->L, s);
@@ -296,7 +320,7 @@ ba_status ba_options_default(ba_options* o) {
     o->max_mu = 1e32;
     o->eps_depth = 0.0;
     o->use_graph = 1;
-    o->reserved = 0;
+    o->pcg_kernel = 0;
     return BA_OK;
 }
 
@@ -348,16 +372,19 @@ ba_status ba_problem_create(int32_t n_cams, int32_t n_pts, int64_t n_obs, const 
     p->pt_idx.assign(pt_idx, pt_idx + n_obs);
     p->pixels.assign(pixels, pixels + 2 * n_obs);
     p->pt_off = (int64_t)((9 * (size_t)n_cams + 3) / 4 * 4);
-    p->n_vec = p->pt_off + (int64_t)((3 * (size_t)n_pts + 3) / 4 * 4);
+    p->n_vec = p->pt_off + 12 * (int64_t)(((size_t)n_pts + 3) / 4);
     p->lay = compute_layout(n_cams, n_pts, n_obs, precision);
     *out = p;
     return BA_OK;
 }
 
 static void release_graph(ba_problem* p) {
-    if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
-    if (p->graph.graph) cudaGraphDestroy(p->graph.graph);
-    p->graph = GraphCache{};
+    for (GraphCache* g : {&p->graph, &p->graph_unrolled}) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        *g = GraphCache{};
+    }
+    p->unrolled_lm = p->unrolled_pcg = -1;
 }
 
 void ba_problem_destroy(ba_problem* p) {
@@ -390,6 +417,66 @@ static ba_status check_bound(const ba_problem* p, const char* who) {
 }
 
 static ba_status write_options(ba_problem* p, const ba_options* o);
+
+// Persistent PCG plan: one CTA per SM, contiguous tile runs balanced by observation
+// count; used only when every CTA's keys and point state fit in its shared memory.
+static ba_status plan_persistent(ba_problem* p, int sms) {
+    const int nt = p->n_tiles;
+    std::vector<uint32_t> off((size_t)nt + 1);
+    GBBA_CUDA(cudaMemcpy(off.data(), p->vf.tile_off, 4 * off.size(), cudaMemcpyDeviceToHost));
+    const int G = std::min(std::min(sms, MAX_PBLOCKS), nt);
+    if (G < 1) return BA_OK;
+    std::vector<uint32_t> bt((size_t)G + 1, 0);
+    const double total = (double)off[nt];
+    int t = 0;
+    for (int b = 1; b < G; ++b) {
+        const double target = total * b / G;
+        while (t < nt && (double)off[t] < target) ++t;
+        bt[b] = (uint32_t)std::max(t, (int)bt[b - 1]);
+    }
+    bt[G] = (uint32_t)nt;
+    const size_t limit = (size_t)std::max(0, persistent_max_smem() - 4096);
+    auto point_bytes = [&](int b) {
+        const size_t no = off[bt[b + 1]] - off[bt[b]];
+        const long pb = (long)bt[b] * TILE_PTS, pe = std::min((long)bt[b + 1] * TILE_PTS, (long)p->n_pts);
+        const size_t np = pe > pb ? (size_t)(pe - pb) : 0;
+        const size_t n3p = (3 * np + 3) & ~(size_t)3;
+        // keys, X and p as float4, D r z h q as 3-float arrays, M^-1 (6 per point)
+        return ((4 * no + 15) & ~(size_t)15) + 32 * np + 4 * (5 * n3p + ((6 * np + 3) & ~(size_t)3));
+    };
+    size_t worst = 0;
+    for (int b = 0; b < G; ++b) worst = std::max(worst, point_bytes(b));
+    if (worst > limit) return BA_OK;   // too large: the multi-kernel PCG path is used
+    // distinct cameras of each CTA's observations (sorted)
+    std::vector<uint32_t> keys((size_t)p->n_obs);
+    GBBA_CUDA(cudaMemcpy(keys.data(), p->vf.obs_key, 4 * keys.size(), cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> coff((size_t)G + 1, 0), cams;
+    for (int b = 0; b < G; ++b) {
+        std::vector<uint32_t> cb;
+        for (uint32_t j = off[bt[b]]; j < off[bt[b + 1]]; ++j) cb.push_back(keys[j] >> 8);
+        std::sort(cb.begin(), cb.end());
+        cb.erase(std::unique(cb.begin(), cb.end()), cb.end());
+        cams.insert(cams.end(), cb.begin(), cb.end());
+        coff[b + 1] = (uint32_t)cams.size();
+        const size_t bytes = point_bytes(b) + 4 * ((cb.size() + 3) & ~(size_t)3) + 4 * 28 * cb.size();
+        worst = std::max(worst, bytes);
+    }
+    if (worst > limit) return BA_OK;
+    const size_t cap = (p->lay.pslots - p->lay.blk_cams) / 4;
+    if (cams.size() > cap) return BA_OK;
+    int bps = 0;
+    if (persistent_prepare((int)worst, &bps) != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        return BA_OK;
+    }
+    GBBA_CUDA(cudaMemcpy(p->blk_tile, bt.data(), 4 * bt.size(), cudaMemcpyHostToDevice));
+    GBBA_CUDA(cudaMemcpy(p->blk_cam_off, coff.data(), 4 * coff.size(), cudaMemcpyHostToDevice));
+    GBBA_CUDA(cudaMemcpy(p->blk_cams, cams.data(), 4 * cams.size(), cudaMemcpyHostToDevice));
+    p->persistent = true;
+    p->p_grid = G;
+    p->p_smem = (int)worst;
+    return BA_OK;
+}
 
 ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream) {
     if (!p || !ws) {
@@ -455,6 +542,15 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
     const size_t ub = l.vec[0];
     GBBA_CUDA(cudaMemsetAsync(w + ub, 0, l.total - ub, s));
     GBBA_CUDA(cudaStreamSynchronize(s));
+    p->blk_tile = (uint32_t*)(w + l.blk_tile);
+    p->blk_cam_off = (uint32_t*)(w + l.blk_cam_off);
+    p->blk_cams = (uint32_t*)(w + l.blk_cams);
+    p->pslots = (double*)(w + l.pslots);
+    p->persistent = false;
+    if (p->precision == BA_PREC_MIXED) {
+        ba_status pst = plan_persistent(p, sms);
+        if (pst) return pst;
+    }
     p->bound = true;
     return BA_OK;
 }
@@ -554,7 +650,8 @@ static ba_status check_options(const ba_options* o) {
         return BA_ERR_INVALID_ARG;
     }
     if (o->max_lm_iters < 0 || o->max_pcg_iters < 0 || !(o->pcg_rel_tol >= 0) || !(o->initial_trust_region > 0) ||
-        !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0)) {
+        !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0) ||
+        (o->pcg_kernel != 0 && o->pcg_kernel != 1) || o->use_graph < 0 || o->use_graph > 2) {
         set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive)");
         return BA_ERR_INVALID_ARG;
     }
@@ -614,11 +711,43 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
         return BA_ERR_NOT_IMPLEMENTED;
     }
     if ((st = write_options(p, o))) return st;
-    if (o->use_graph) {
+    const bool want_persistent = p->persistent && o->pcg_kernel == 0;
+    if (want_persistent != p->use_persistent) {   // cached graphs were built for the other PCG form
+        release_graph(p);
+        p->use_persistent = want_persistent;
+    }
+    // A cooperative kernel cannot sit inside a conditional node, so with the persistent
+    // PCG kernel the default graph is the fixed LM sequence (six kernels per LM step).
+    const int graph_mode = (o->use_graph == 1 && p->use_persistent) ? 2 : o->use_graph;
+    if (graph_mode == 2) {
+        // the predicated sequence (every PCG and LM slot launched, idle ones return
+        // at once) captured into one plain graph; rebuilt when the caps change
+        if (!p->graph_unrolled.exec || p->unrolled_lm != o->max_lm_iters || p->unrolled_pcg != o->max_pcg_iters) {
+            if (p->graph_unrolled.exec) cudaGraphExecDestroy(p->graph_unrolled.exec);
+            if (p->graph_unrolled.graph) cudaGraphDestroy(p->graph_unrolled.graph);
+            p->graph_unrolled = GraphCache{};
+            cudaStream_t cs = p->cap[0];
+            GBBA_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+            enqueue_solve_predicated_mixed(p, *o, cs);
+            cudaGraph_t g;
+            GBBA_CUDA(cudaStreamEndCapture(cs, &g));
+            cudaGraphExec_t ex;
+            cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return cuda_status(e, "cudaGraphInstantiate (unrolled)");
+            }
+            p->graph_unrolled.graph = g;
+            p->graph_unrolled.exec = ex;
+            p->unrolled_lm = o->max_lm_iters;
+            p->unrolled_pcg = o->max_pcg_iters;
+        }
+        GBBA_CUDA(cudaGraphLaunch(p->graph_unrolled.exec, p->stream));
+    } else if (graph_mode == 1) {
         if (!p->graph.exec && (st = build_graph_mixed(p))) return st;
         GBBA_CUDA(cudaGraphLaunch(p->graph.exec, p->stream));
     } else {
-        enqueue_solve_predicated_mixed(p, *o);
+        enqueue_solve_predicated_mixed(p, *o, p->stream);
         GBBA_CUDA(cudaGetLastError());
     }
     p->linearized = true;
@@ -648,18 +777,21 @@ ba_status ba_apply_normal(ba_problem* p, double mu, const void* vin, void* out, 
     GBBA_CUDA(cudaMemcpyAsync(&dst->mu, &mu, sizeof(double), cudaMemcpyHostToDevice, s));
     int32_t one = 1;
     GBBA_CUDA(cudaMemcpyAsync(&dst->lm_active, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    launch_precond(v, p->L, s, 0, 0);
+    launch_precond(v, p->L, s, 0, 0, nullptr);
     launch_set_direction(v, p->L, s, (const float*)vin);
-    launch_matvec(v, p->L, s, nullptr);
+    launch_matvec(v, p->L, s, nullptr, v.p, 0);
     launch_normal_out(v, p->L, s, (float*)out);
     GBBA_CUDA(cudaGetLastError());
-    if (vAv) {
-        double jp2 = 0, pdp = 0;
-        GBBA_CUDA(cudaMemcpyAsync(&jp2, &dst->jp2, sizeof(double), cudaMemcpyDeviceToHost, s));
-        GBBA_CUDA(cudaMemcpyAsync(&pdp, &dst->pDp, sizeof(double), cudaMemcpyDeviceToHost, s));
-        GBBA_CUDA(cudaStreamSynchronize(s));
-        *vAv = jp2 + mu * pdp;
+    double acc[NSLOT * SLOT_STRIDE];
+    GBBA_CUDA(cudaMemcpyAsync(acc, dst->acc_mv, sizeof(acc), cudaMemcpyDeviceToHost, s));
+    GBBA_CUDA(cudaMemsetAsync(dst->acc_mv, 0, sizeof(acc), s));
+    GBBA_CUDA(cudaStreamSynchronize(s));
+    double jp2 = 0, pdp = 0;
+    for (int k = 0; k < NSLOT; ++k) {
+        jp2 += acc[k * SLOT_STRIDE];
+        pdp += acc[k * SLOT_STRIDE + 1];
     }
+    if (vAv) *vAv = jp2 + mu * pdp;
     return BA_OK;
 }
 
@@ -678,9 +810,81 @@ ba_status ba_repeat_normal(ba_problem* p, int32_t launches) {
         set_error("ba_repeat_normal: call ba_apply_normal first");
         return BA_ERR_STATE;
     }
-    for (int i = 0; i < launches; ++i) launch_matvec(p->vf, p->L, p->stream, nullptr);
+    for (int i = 0; i < launches; ++i) launch_matvec(p->vf, p->L, p->stream, nullptr, p->vf.p, 0);
+    GBBA_CUDA(cudaMemsetAsync(p->vf.st->acc_mv, 0, NSLOT * SLOT_STRIDE * sizeof(double), p->stream));
     GBBA_CUDA(cudaGetLastError());
     return BA_OK;
+}
+
+ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n) {
+    ba_status st = check_bound(p, "ba_profile_kernels");
+    if (st) return st;
+    if (reps < 1 || !us || n < 1) {
+        set_error("ba_profile_kernels: reps >= 1 and an output array are required");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->precision != BA_PREC_MIXED) {
+        set_error("ba_profile_kernels: FP64 form not built yet");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    if (!p->linearized) {
+        set_error("ba_profile_kernels: call ba_evaluate or ba_solve first");
+        return BA_ERR_STATE;
+    }
+    const Views<float>& v = p->vf;
+    cudaStream_t s = p->stream;
+    // keep every gate open: huge PCG cap, zero tolerance, active flags set
+    DevOptions o{};
+    o.max_lm = 1 << 30;
+    o.max_pcg = 1 << 30;
+    o.tol = 0.0;
+    o.mu0 = 0.01;
+    o.min_diag = 1e-6;
+    o.max_diag = 1e32;
+    o.max_mu = 1e300;
+    o.eps = 0.0;
+    GBBA_CUDA(cudaMemcpyAsync(p->ws + p->lay.state, &o, sizeof(o), cudaMemcpyHostToDevice, s));
+    const int32_t flags[4] = {1, 1, 1, 1};
+    auto open_gates = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(&v.st->lm_active, &flags[0], 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&v.st->accepted, &flags[1], 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&v.st->relin, &flags[2], 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&v.st->pcg_active, &flags[3], 4, cudaMemcpyHostToDevice, s);
+        return e;
+    };
+    cudaEvent_t e0, e1;
+    GBBA_CUDA(cudaEventCreate(&e0));
+    GBBA_CUDA(cudaEventCreate(&e1));
+    auto timeit = [&](auto&& launch) -> double {
+        open_gates();
+        launch();   // warm
+        open_gates();
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < reps; ++i) launch();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return 1e3 * ms / reps;
+    };
+    double out[8];
+    out[0] = timeit([&] { launch_camera_precompute(v, p->L, s); });
+    out[1] = timeit([&] { launch_linearize(v, p->L, s, 1, nullptr, nullptr, 0, 0); });
+    out[2] = timeit([&] { launch_precond(v, p->L, s, 0, 0, nullptr); });
+    out[3] = timeit([&] { launch_matvec(v, p->L, s, nullptr, v.z, 1); });
+    out[4] = timeit([&] { launch_update(v, p->L, s, 0, 0); });
+    out[5] = timeit([&] { launch_candidate(v, p->L, s); });
+    out[6] = timeit([&] { launch_eval_candidate(v, p->L, s, 0, 0); });
+    out[7] = timeit([&] { launch_commit(v, p->L, s); });
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    GBBA_CUDA(cudaGetLastError());
+    for (int i = 0; i < n && i < 8; ++i) us[i] = out[i];
+    // restore the default options; the solver state is re-initialised by the next solve
+    ba_options d;
+    ba_options_default(&d);
+    p->linearized = false;
+    return write_options(p, &d);
 }
 
 // ---- not yet available in this build --------------------------------------------

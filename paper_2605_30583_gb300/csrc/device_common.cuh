@@ -77,6 +77,53 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* parti
     return true;
 }
 
+// Slot-spread accumulation: block b adds into slot b % NSLOT.
+__device__ __forceinline__ void slot_add(double* base, int k, double v) {
+    atomicAdd(&base[(blockIdx.x % NSLOT) * SLOT_STRIDE + k], v);
+}
+
+// Sum over the NSLOT slots of component k; call with a full warp, result in every lane.
+__device__ __forceinline__ double slot_sum_warp(const double* base, int k) {
+    double v = __ldcg(&base[(threadIdx.x & 31) * SLOT_STRIDE + k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// 1/x in FP64: hardware approximation refined by two Newton-Raphson steps
+// y <- y + y (1 - x y), each roughly doubling the correct bits.
+__device__ __forceinline__ double rcp64(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    y = fma(y, fma(-x, y, 1.0), y);
+    y = fma(y, fma(-x, y, 1.0), y);
+    return y;
+}
+
+// Block sums of two FP32 per-thread partials: FP32 inside each warp (32 terms), FP64
+// across warps.  Results valid in thread 0.  `sh` holds 2 * (blockDim.x / 32) doubles.
+__device__ __forceinline__ void block_sum2(float a, float b, double* sh, double& ra, double& rb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[w] = (double)a;
+        sh[nw + w] = (double)b;
+    }
+    __syncthreads();
+    ra = rb = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < nw; ++i) {
+            ra += sh[i];
+            rb += sh[nw + i];
+        }
+    }
+}
+
 __device__ __forceinline__ long long global_ns() {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -192,6 +239,57 @@ __device__ __forceinline__ Geo project_geo(const Cam& c, float X0, float X1, flo
     g.A[4] = niz * m11;
     g.A[5] = niz * fmaf(m01, g.p[0], m11 * g.p[1]);
     return g;
+}
+
+// 1/x to within 1 ulp (the hardware reciprocal approximation, denormals flushed).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Geometry of one observation without the explicit 2x3 A: J d and J^T t are applied
+// in factored form (see apply_A / apply_At).
+struct GeoLite {
+    float RX[3];
+    float p[2];
+    float n2, s, iz, a, b;   // a = f s, b = 2 f s'
+};
+
+__device__ __forceinline__ GeoLite project_lite(const Cam& c, float X0, float X1, float X2, float eps) {
+    GeoLite g;
+    g.RX[0] = fmaf(c.R[0], X0, fmaf(c.R[1], X1, c.R[2] * X2));
+    g.RX[1] = fmaf(c.R[3], X0, fmaf(c.R[4], X1, c.R[5] * X2));
+    g.RX[2] = fmaf(c.R[6], X0, fmaf(c.R[7], X1, c.R[8] * X2));
+    const float P2 = g.RX[2] + c.t[2];
+    const float d = P2 + (P2 >= 0.0f ? eps : -eps);
+    g.iz = rcp_approx(d);
+    g.p[0] = -(g.RX[0] + c.t[0]) * g.iz;
+    g.p[1] = -(g.RX[1] + c.t[1]) * g.iz;
+    g.n2 = fmaf(g.p[0], g.p[0], g.p[1] * g.p[1]);
+    g.s = fmaf(g.n2, fmaf(c.k2, g.n2, c.k1), 1.0f);
+    g.a = c.f * g.s;
+    g.b = 2.0f * c.f * fmaf(2.0f * c.k2, g.n2, c.k1);
+    return g;
+}
+
+// A dP with A = M dp/dP, M = a I + b p p^T, dp/dP = -iz [[1, 0, px], [0, 1, py]].
+__device__ __forceinline__ void apply_A(const GeoLite& g, float d0, float d1, float d2, float& t0, float& t1) {
+    const float e0 = -g.iz * fmaf(g.p[0], d2, d0);
+    const float e1 = -g.iz * fmaf(g.p[1], d2, d1);
+    const float pe = g.b * fmaf(g.p[0], e0, g.p[1] * e1);
+    t0 = fmaf(g.a, e0, pe * g.p[0]);
+    t1 = fmaf(g.a, e1, pe * g.p[1]);
+}
+
+// A^T t (M symmetric).
+__device__ __forceinline__ void apply_At(const GeoLite& g, float t0, float t1, float& u0, float& u1, float& u2) {
+    const float pt = g.b * fmaf(g.p[0], t0, g.p[1] * t1);
+    const float w0 = -g.iz * fmaf(g.a, t0, pt * g.p[0]);
+    const float w1 = -g.iz * fmaf(g.a, t1, pt * g.p[1]);
+    u0 = w0;
+    u1 = w1;
+    u2 = fmaf(g.p[0], w0, g.p[1] * w1);
 }
 
 // Residual only (no Jacobian): f s p - u.

@@ -13,6 +13,7 @@ typedef unsigned long long CondHandle;   // cudaGraphConditionalHandle
 constexpr int LIN_TB = 128;   // threads per tile CTA, linearisation
 constexpr int MV_TB = 128;    // threads per tile CTA, normal operator
 constexpr int EV_TB = 128;    // threads per tile CTA, candidate evaluation
+constexpr int PCG_TB = 512;   // threads per CTA of the persistent PCG kernel
 
 struct LaunchCfg {
     int item_block = 256;
@@ -26,9 +27,10 @@ struct LaunchCfg {
 void launch_camera_precompute(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
 void launch_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode,
                       float* res_out, float* jac_out, CondHandle lm_cond, int use_cond);
-void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
-void launch_direction(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
-void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate);
+void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
+                    double* pslots);
+void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
+                   const float* zs, int use_beta);
 void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
 void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
 void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
@@ -41,6 +43,12 @@ void launch_unpack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, co
                    void* pts, int dtype);
 void launch_set_direction(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const float* src);
 void launch_normal_out(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, float* out);
+// persistent PCG (pcg_persistent.cu)
+int persistent_max_smem();
+cudaError_t persistent_prepare(int smem_bytes, int* blocks_per_sm);
+cudaError_t launch_pcg_persistent(const Views<float>& v, const uint32_t* blk_tile, const uint32_t* blk_cam_off,
+                                  const uint32_t* blk_cams, double* pslots, int grid, int smem_bytes,
+                                  cudaStream_t s);
 int occupancy_blocks_linearize();
 int occupancy_blocks_matvec();
 int occupancy_blocks_eval();

@@ -17,72 +17,14 @@
 // shared memory (the tile owns its points) and are written once per tile.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "kernels.h"
+#include "mixed_common.cuh"
 
 namespace gbba {
 
-namespace {
-
-constexpr uint32_t FULL = 0xffffffffu;
-constexpr uint32_t NO_CAM = 0xffffffffu;
-
-// Warp-segmented suffix sum: lanes with equal `key` in consecutive positions form a
-// segment; afterwards the first lane of each segment holds the segment's sum.
-template <int V>
-__device__ __forceinline__ bool seg_reduce(uint32_t key, float (&acc)[V]) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t prev = __shfl_up_sync(FULL, key, 1);
-    const bool head = (lane == 0) || (prev != key);
-    const uint32_t hm = __ballot_sync(FULL, head);
-    const uint32_t after = hm & ~((2u << lane) - 1u);
-    const int end = after ? (__ffs(after) - 1) : 32;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            const float o = __shfl_down_sync(FULL, acc[k], d);
-            if (lane + d < end) acc[k] += o;
-        }
-    }
-    return head;
-}
-
-__device__ __forceinline__ void flush_matvec(float* __restrict__ dst, float (&a)[9]) {
-    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a[0], a[1], a[2], a[3]));
-    atomicAdd(reinterpret_cast<float4*>(dst + 4), make_float4(a[4], a[5], a[6], a[7]));
-    atomicAdd(dst + 8, a[8]);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) a[k] = 0.0f;
-}
-
-__device__ __forceinline__ void load_dir(const float* __restrict__ rec, float (&d)[9]) {
-    const float4* r4 = reinterpret_cast<const float4*>(rec);
-    const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
-    d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
-    d[4] = b.x; d[5] = b.y; d[6] = b.z; d[7] = b.w; d[8] = c.x;
-}
-
-// t = J d for one observation: J d = A (phi x RX + d_t + R d_X) + c_i p with
-// phi = J_l d_w (precomputed per camera) and c_i = s d_f + f n2 d_k1 + f n2^2 d_k2.
-__device__ __forceinline__ void jdir(const Geo& g, const Cam& c, const float (&dir)[9],
-                                     float dX0, float dX1, float dX2, float& t0, float& t1) {
-    const float* phi = dir + CD_PHI;
-    float dP0 = fmaf(phi[1], g.RX[2], -phi[2] * g.RX[1]) + dir[CD_T + 0];
-    float dP1 = fmaf(phi[2], g.RX[0], -phi[0] * g.RX[2]) + dir[CD_T + 1];
-    float dP2 = fmaf(phi[0], g.RX[1], -phi[1] * g.RX[0]) + dir[CD_T + 2];
-    dP0 = fmaf(c.R[0], dX0, fmaf(c.R[1], dX1, fmaf(c.R[2], dX2, dP0)));
-    dP1 = fmaf(c.R[3], dX0, fmaf(c.R[4], dX1, fmaf(c.R[5], dX2, dP1)));
-    dP2 = fmaf(c.R[6], dX0, fmaf(c.R[7], dX1, fmaf(c.R[8], dX2, dP2)));
-    const float fn2 = c.f * g.n2;
-    const float ci = fmaf(g.s, dir[CD_I + 0], fmaf(fn2, dir[CD_I + 1], fn2 * g.n2 * dir[CD_I + 2]));
-    t0 = fmaf(g.A[0], dP0, fmaf(g.A[1], dP1, fmaf(g.A[2], dP2, ci * g.p[0])));
-    t1 = fmaf(g.A[3], dP0, fmaf(g.A[4], dP1, fmaf(g.A[5], dP2, ci * g.p[1])));
-}
-
-__device__ __forceinline__ bool gated_off(const int32_t* gate) { return gate != nullptr && *gate == 0; }
-
-}  // namespace
 
 // ------------------------------------------------------------------ K0 --------
 // Camera records from the current parameters; zeroes the linearisation sums.
@@ -93,136 +35,162 @@ __global__ void k_camera_precompute(Views<float> v) {
         for (int k = 0; k < 9; ++k) p[k] = (double)v.x[9 * (size_t)c + k];
         camera_record(p, v.cam_pre + (size_t)c * CP_STRIDE);
         double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
-#pragma unroll 8
+#pragma unroll
         for (int k = 0; k < CL_STRIDE; ++k) cl[k] = 0.0;
+        float* ch = v.cam_H + (size_t)c * CH_STRIDE;
+#pragma unroll
+        for (int k = 0; k < CH_STRIDE; ++k) ch[k] = 0.0f;
     }
 }
 
 // ------------------------------------------------------------------ K1 --------
 // Linearisation (fused score + Jacobian products, Sec. V-A): cost F = 1/2 |r|^2,
-// g = J^T r and the diagonal blocks J_c^T J_c, J_p^T J_p.  `mode`: 0 = first
-// linearisation of a solve (initialises the LM state), 1 = relinearisation after an
-// accepted step (gated by st->relin), 2 = evaluation only (optional r and J output in
-// the caller's observation order).
+// g = J^T r and the diagonal blocks J_c^T J_c, J_p^T J_p.  Two passes per tile:
+//   camera pass: the tile's camera-sorted observations, camera sums in registers,
+//     one set of atomics per camera run (g in FP64, J_c^T J_c in FP32 float4 atomics);
+//   point pass: one thread per point over its observations (point-major index), point
+//     sums in registers, no atomics; it also sums the cost.
+// `mode`: 0 = first linearisation of a solve (initialises the LM state), 1 =
+// relinearisation after an accepted step (gated by st->relin), 2 = evaluation only
+// (optional r and J output in the caller's observation order).
+constexpr int LIN_ACC = 9 + CH_STRIDE;   // g (9) + J_c^T J_c upper triangle padded to 48
+
+__device__ __forceinline__ void flush_lin(const Views<float>& v, uint32_t c, float (&a)[LIN_ACC]) {
+    double* g = v.cam_lin + (size_t)c * CL_STRIDE;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) atomicAdd(g + k, (double)a[k]);
+    float4* h = reinterpret_cast<float4*>(v.cam_H + (size_t)c * CH_STRIDE);
+#pragma unroll
+    for (int k = 0; k < CH_STRIDE / 4; ++k)
+        atomicAdd(h + k, make_float4(a[9 + 4 * k], a[10 + 4 * k], a[11 + 4 * k], a[12 + 4 * k]));
+#pragma unroll
+    for (int k = 0; k < LIN_ACC; ++k) a[k] = 0.0f;
+}
+
 template <int TB>
-__global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, float* res_out,
-                                                  float* jac_out, CondHandle lm_cond, int use_cond) {
+__global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, float* res_out, float* jac_out,
+                                                  CondHandle lm_cond, int use_cond) {
     if (mode == 1 && v.st->relin == 0) return;
-    __shared__ float sp[TILE_PTS * 9];   // per point: g (3), H upper triangle (6)
+    __shared__ float4 sx[TILE_PTS];
     const float eps = (float)v.st->opt.eps;
-    double cost = 0.0;
+    float cost = 0.0f;
     for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
         const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
         const int pt0 = tile * TILE_PTS;
         const int npt = min(TILE_PTS, v.n_pts - pt0);
-        for (int i = threadIdx.x; i < TILE_PTS * 9; i += TB) sp[i] = 0.0f;
+        const size_t base = v.pt_off + 3 * (size_t)pt0;
         __syncthreads();
-        const uint32_t n = hi - lo;
-        const uint32_t chunk = (n + TB - 1) / TB;
-        const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
-        uint32_t cur = NO_CAM;
-        float acc[54];
+        for (int i = threadIdx.x; i < npt; i += TB)
+            sx[i] = make_float4(v.x[base + 3 * i], v.x[base + 3 * i + 1], v.x[base + 3 * i + 2], 0.0f);
+        __syncthreads();
+        // ---- camera pass
+        {
+            const uint32_t n = hi - lo;
+            const uint32_t chunk = (n + TB - 1) / TB;
+            const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
+            uint32_t cur = NO_CAM;
+            float acc[LIN_ACC];
 #pragma unroll
-        for (int k = 0; k < 54; ++k) acc[k] = 0.0f;
-        Cam cam;
-        float JL[9];
-        float costc = 0.0f;
-        for (uint32_t j = a; j < b; ++j) {
-            const uint32_t key = v.obs_key[j];
-            const uint32_t c = key >> 8, slot = key & 0xffu;
-            if (c != cur) {
-                if (cur != NO_CAM) {
-                    double* dst = v.cam_lin + (size_t)cur * CL_STRIDE;
+            for (int k = 0; k < LIN_ACC; ++k) acc[k] = 0.0f;
+            Cam cam;
+            float JL[9];
+            for (uint32_t j = a; j < b; ++j) {
+                const uint32_t key = __ldg(v.obs_key + j);
+                const uint32_t c = key >> 8, slot = key & 0xffu;
+                if (c != cur) {
+                    if (cur != NO_CAM) flush_lin(v, cur, acc);
+                    cur = c;
+                    cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
 #pragma unroll
-                    for (int k = 0; k < 54; ++k) {
-                        atomicAdd(dst + k, (double)acc[k]);
-                        acc[k] = 0.0f;
+                    for (int k = 0; k < 9; ++k) JL[k] = __ldg(v.cam_pre + (size_t)c * CP_STRIDE + CP_JL + k);
+                }
+                const float4 X = sx[slot];
+                const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
+                const float fs = cam.f * g.s;
+                const float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
+                const float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
+                // camera Jacobian rows: [J_w | J_t | J_intr], J_w[:,k] = A (J_l[:,k] x RX)
+                float j0[9], j1[9];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float w0 = JL[k], w1 = JL[3 + k], w2 = JL[6 + k];
+                    const float c0 = fmaf(w1, g.RX[2], -w2 * g.RX[1]);
+                    const float c1 = fmaf(w2, g.RX[0], -w0 * g.RX[2]);
+                    const float c2 = fmaf(w0, g.RX[1], -w1 * g.RX[0]);
+                    j0[k] = fmaf(g.A[0], c0, fmaf(g.A[1], c1, g.A[2] * c2));
+                    j1[k] = fmaf(g.A[3], c0, fmaf(g.A[4], c1, g.A[5] * c2));
+                    j0[3 + k] = g.A[k];
+                    j1[3 + k] = g.A[3 + k];
+                }
+                const float fn2 = cam.f * g.n2;
+                j0[6] = g.s * g.p[0]; j0[7] = fn2 * g.p[0]; j0[8] = fn2 * g.n2 * g.p[0];
+                j1[6] = g.s * g.p[1]; j1[7] = fn2 * g.p[1]; j1[8] = fn2 * g.n2 * g.p[1];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) acc[CL_G + i] = fmaf(j0[i], r0, fmaf(j1[i], r1, acc[CL_G + i]));
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+#pragma unroll
+                    for (int k = i; k < 9; ++k) {
+                        const int t = 9 + tri_index(9, i, k);
+                        acc[t] = fmaf(j0[i], j0[k], fmaf(j1[i], j1[k], acc[t]));
+                    }
+                if (mode == 2) {
+                    const uint32_t o = v.obs_user[j];
+                    if (res_out) { res_out[2 * (size_t)o] = r0; res_out[2 * (size_t)o + 1] = r1; }
+                    if (jac_out) {
+                        float* Jo = jac_out + 24 * (size_t)o;
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) { Jo[k] = j0[k]; Jo[12 + k] = j1[k]; }
                     }
                 }
-                cur = c;
-                cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
-#pragma unroll
-                for (int k = 0; k < 9; ++k) JL[k] = __ldg(v.cam_pre + (size_t)c * CP_STRIDE + CP_JL + k);
             }
-            const size_t xi = v.pt_off + 3 * (size_t)(pt0 + slot);
-            const float X0 = v.x[xi], X1 = v.x[xi + 1], X2 = v.x[xi + 2];
-            const Geo g = project_geo(cam, X0, X1, X2, eps);
-            const float fs = cam.f * g.s;
-            const float r0 = fmaf(fs, g.p[0], -v.obs_uv[2 * (size_t)j]);
-            const float r1 = fmaf(fs, g.p[1], -v.obs_uv[2 * (size_t)j + 1]);
-            costc = fmaf(r0, r0, fmaf(r1, r1, costc));
-            // camera Jacobian rows: [J_w | J_t | J_intr], J_w[:,k] = A (J_l[:,k] x RX)
-            float j0[9], j1[9];
+            // camera sums: combine lanes of the same camera, one set of atomics per run
+            const bool head = seg_reduce<LIN_ACC>(cur, acc);
+            if (head && cur != NO_CAM) flush_lin(v, cur, acc);
+        }
+        // ---- point pass: one thread per point, its observations in point-major order
+        for (int i = threadIdx.x; i < npt; i += TB) {
+            const int ip = pt0 + i;
+            const float4 X = sx[i];
+            float gp[3] = {0.0f, 0.0f, 0.0f}, hp[6] = {0, 0, 0, 0, 0, 0};
+            const uint32_t k0 = __ldg(v.pt_obs_off + ip), k1 = __ldg(v.pt_obs_off + ip + 1);
+            for (uint32_t k = k0; k < k1; ++k) {
+                const uint32_t j = __ldg(v.obs_pm + k);
+                const uint32_t c = __ldg(v.obs_key + j) >> 8;
+                const Cam cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+                const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
+                const float fs = cam.f * g.s;
+                const float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
+                const float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
+                cost = fmaf(r0, r0, fmaf(r1, r1, cost));
+                float jx0[3], jx1[3];   // J_X = A R
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float w0 = JL[k], w1 = JL[3 + k], w2 = JL[6 + k];
-                const float c0 = fmaf(w1, g.RX[2], -w2 * g.RX[1]);
-                const float c1 = fmaf(w2, g.RX[0], -w0 * g.RX[2]);
-                const float c2 = fmaf(w0, g.RX[1], -w1 * g.RX[0]);
-                j0[k] = fmaf(g.A[0], c0, fmaf(g.A[1], c1, g.A[2] * c2));
-                j1[k] = fmaf(g.A[3], c0, fmaf(g.A[4], c1, g.A[5] * c2));
-                j0[3 + k] = g.A[k];
-                j1[3 + k] = g.A[3 + k];
-            }
-            const float fn2 = cam.f * g.n2;
-            j0[6] = g.s * g.p[0]; j0[7] = fn2 * g.p[0]; j0[8] = fn2 * g.n2 * g.p[0];
-            j1[6] = g.s * g.p[1]; j1[7] = fn2 * g.p[1]; j1[8] = fn2 * g.n2 * g.p[1];
-            // point Jacobian J_X = A R
-            float jx0[3], jx1[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                jx0[k] = fmaf(g.A[0], cam.R[k], fmaf(g.A[1], cam.R[3 + k], g.A[2] * cam.R[6 + k]));
-                jx1[k] = fmaf(g.A[3], cam.R[k], fmaf(g.A[4], cam.R[3 + k], g.A[5] * cam.R[6 + k]));
-            }
-#pragma unroll
-            for (int i = 0; i < 9; ++i) acc[CL_G + i] = fmaf(j0[i], r0, fmaf(j1[i], r1, acc[CL_G + i]));
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-#pragma unroll
-                for (int k = i; k < 9; ++k) {
-                    const int t = CL_H + tri_index(9, i, k);
-                    acc[t] = fmaf(j0[i], j0[k], fmaf(j1[i], j1[k], acc[t]));
+                for (int q = 0; q < 3; ++q) {
+                    jx0[q] = fmaf(g.A[0], cam.R[q], fmaf(g.A[1], cam.R[3 + q], g.A[2] * cam.R[6 + q]));
+                    jx1[q] = fmaf(g.A[3], cam.R[q], fmaf(g.A[4], cam.R[3 + q], g.A[5] * cam.R[6 + q]));
                 }
-            float* ps = sp + 9 * slot;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) atomicAdd(ps + i, fmaf(jx0[i], r0, jx1[i] * r1));
+                for (int q = 0; q < 3; ++q) gp[q] = fmaf(jx0[q], r0, fmaf(jx1[q], r1, gp[q]));
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+                for (int a2 = 0; a2 < 3; ++a2)
 #pragma unroll
-                for (int k = i; k < 3; ++k)
-                    atomicAdd(ps + 3 + tri_index(3, i, k), fmaf(jx0[i], jx0[k], jx1[i] * jx1[k]));
-            if (mode == 2) {
-                const uint32_t o = v.obs_user[j];
-                if (res_out) { res_out[2 * (size_t)o] = r0; res_out[2 * (size_t)o + 1] = r1; }
-                if (jac_out) {
-                    float* J = jac_out + 24 * (size_t)o;
+                    for (int b2 = a2; b2 < 3; ++b2) {
+                        const int t = tri_index(3, a2, b2);
+                        hp[t] = fmaf(jx0[a2], jx0[b2], fmaf(jx1[a2], jx1[b2], hp[t]));
+                    }
+                if (mode == 2 && jac_out) {
+                    float* Jo = jac_out + 24 * (size_t)v.obs_user[j];
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) { J[k] = j0[k]; J[12 + k] = j1[k]; }
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) { J[9 + k] = jx0[k]; J[21 + k] = jx1[k]; }
+                    for (int q = 0; q < 3; ++q) { Jo[9 + q] = jx0[q]; Jo[21 + q] = jx1[q]; }
                 }
             }
-        }
-        // camera sums: combine lanes of the same camera, one set of atomics per run
-        const bool head = seg_reduce<54>(cur, acc);
-        if (head && cur != NO_CAM) {
-            double* dst = v.cam_lin + (size_t)cur * CL_STRIDE;
 #pragma unroll
-            for (int k = 0; k < 54; ++k) atomicAdd(dst + k, (double)acc[k]);
+            for (int q = 0; q < 3; ++q) v.g[base + 3 * i + q] = gp[q];
+#pragma unroll
+            for (int q = 0; q < PH_STRIDE; ++q) v.pt_H[(size_t)ip * PH_STRIDE + q] = hp[q];
         }
-        cost += (double)costc;
-        __syncthreads();
-        for (int i = threadIdx.x; i < npt * 3; i += TB) {
-            const int s = i / 3, k = i % 3;
-            v.g[v.pt_off + 3 * (size_t)pt0 + i] = sp[9 * s + k];
-        }
-        for (int i = threadIdx.x; i < npt * PH_STRIDE; i += TB) {
-            const int s = i / PH_STRIDE, k = i % PH_STRIDE;
-            v.pt_H[(size_t)(pt0 + s) * PH_STRIDE + k] = sp[9 * s + 3 + k];
-        }
-        __syncthreads();
     }
-    double in[1] = {cost}, out[1];
+    double in[1] = {(double)cost}, out[1];
     if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_LIN], out) && threadIdx.x == 0) {
         DevState* st = v.st;
         const double F = 0.5 * out[0];
@@ -243,41 +211,45 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
 // ------------------------------------------------------------------ K3 --------
 // Block-Jacobi preconditioner (Sec. V: one block per node) of J^T J + mu D, inverted
 // by FP64 Cholesky, and the start of PCGNR: h = 0, r = -g, z = M^-1 r, p = 0.
-__device__ void chol_inverse(double* A, int n, double* Minv, bool& ok) {
-    // A: n x n full, row-major, overwritten by L.  Minv = L^-T L^-1.
-    for (int j = 0; j < n; ++j) {
-        double s = A[j * n + j];
-        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
-        if (!(s > 0.0)) { ok = false; return; }
-        const double d = sqrt(s);
-        A[j * n + j] = d;
-        for (int i = j + 1; i < n; ++i) {
-            double t = A[i * n + j];
-            for (int k = 0; k < j; ++k) t -= A[i * n + k] * A[j * n + k];
-            A[i * n + j] = t / d;
+// Camera c of an item kernel runs in block c % gridDim, thread c / gridDim, so the
+// (slow, FP64) per-camera work spreads over every SM.
+#define FOR_CAMERAS(c, v) \
+    for (int c = blockIdx.x + gridDim.x * threadIdx.x; c < (v).n_cams; c += gridDim.x * blockDim.x)
+#define FOR_POINTS(i, v) \
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (v).n_pts; i += gridDim.x * blockDim.x)
+
+// Inverse of one camera block, one warp per camera: lane j < 18 holds column j of
+// the augmented matrix [A | I] (A = H + mu D, 9 x 9, SPD) and Gauss-Jordan elimination
+// without pivoting runs over the 9 pivots in FP64.  Lanes 9..17 end with the columns
+// of A^-1.  Returns false (in every lane) if a pivot is not positive.
+__device__ __forceinline__ bool warp_block_inverse9(double (&col)[9], int lane) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double piv = __shfl_sync(0xffffffffu, col[k], k);
+        ok = ok && (piv > 0.0) && isfinite(piv);
+        const double ip = rcp64(piv > 0.0 ? piv : 1.0);
+        const double rk = col[k] * ip;   // row k of the updated matrix, this lane's column
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double aik = __shfl_sync(0xffffffffu, col[i], k);
+            if (i != k) col[i] = fma(-aik, rk, col[i]);
         }
+        col[k] = rk;
     }
-    // L^-1 (lower) into Minv's storage first, column by column
-    double Li[81];
-    for (int i = 0; i < n * n; ++i) Li[i] = 0.0;
-    for (int j = 0; j < n; ++j) {
-        Li[j * n + j] = 1.0 / A[j * n + j];
-        for (int i = j + 1; i < n; ++i) {
-            double t = 0.0;
-            for (int k = j; k < i; ++k) t -= A[i * n + k] * Li[k * n + j];
-            Li[i * n + j] = t / A[i * n + i];
-        }
-    }
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-            double t = 0.0;
-            for (int k = (i > j ? i : j); k < n; ++k) t += Li[k * n + i] * Li[k * n + j];
-            Minv[i * n + j] = t;
-        }
+    (void)lane;
+    return ok;
 }
 
-__global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond) {
+__global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, double* pslots) {
     DevState* st = v.st;
+    if (pslots != nullptr && blockIdx.x == 0) {   // state of the persistent PCG kernel
+        for (int i = threadIdx.x; i < PSLOT_DOUBLES; i += blockDim.x) pslots[i] = 0.0;
+        if (threadIdx.x == 0) {
+            st->bar_count = 0u;
+            st->bar_err = 0;
+        }
+    }
     if (st->lm_active == 0) {
         // the PCG loop that follows must see a cleared flag
         if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(pcg_cond, 0u);
@@ -285,107 +257,90 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond) {
     }
     const double mu = st->mu, lo = st->opt.min_diag, hi = st->opt.max_diag;
     double rz = 0.0, rr = 0.0;
-    const int items = v.n_cams + v.n_pts;
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
-        if (it < v.n_cams) {
-            const int c = it;
-            const double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
-            double A[81], M[81];
-            double Dd[9];
-            for (int i = 0; i < 9; ++i)
-                for (int j = i; j < 9; ++j) {
-                    const double h = cl[CL_H + tri_index(9, i, j)];
-                    A[i * 9 + j] = h;
-                    A[j * 9 + i] = h;
-                }
-            for (int i = 0; i < 9; ++i) {
-                Dd[i] = fmin(fmax(A[i * 9 + i], lo), hi);
-                A[i * 9 + i] += mu * Dd[i];
-            }
-            double diag[9];
-            for (int i = 0; i < 9; ++i) diag[i] = A[i * 9 + i];
-            bool ok = true;
-            chol_inverse(A, 9, M, ok);
-            if (!ok) {   // not SPD in FP64: fall back to the inverse diagonal
-                for (int i = 0; i < 81; ++i) M[i] = 0.0;
-                for (int i = 0; i < 9; ++i) M[i * 9 + i] = diag[i] > 0.0 ? 1.0 / diag[i] : 0.0;
-            }
-            float* Mo = v.Minv_c + (size_t)c * MC_STRIDE;
-            for (int i = 0; i < 81; ++i) Mo[i] = (float)M[i];
-            float rf[9];
-            for (int i = 0; i < 9; ++i) {
-                v.D[9 * (size_t)c + i] = (float)Dd[i];
-                rf[i] = (float)(-cl[CL_G + i]);
-            }
-            for (int i = 0; i < 9; ++i) {
-                float z = 0.0f;
-                for (int k = 0; k < 9; ++k) z = fmaf(Mo[i * 9 + k], rf[k], z);
-                const size_t e = 9 * (size_t)c + i;
-                v.r[e] = rf[i];
-                v.z[e] = z;
-                v.p[e] = 0.0f;
-                v.h[e] = 0.0f;
-                rz += (double)rf[i] * (double)z;
-                rr += (double)rf[i] * (double)rf[i];
-            }
-            float* ca = v.cam_acc + (size_t)c * CA_STRIDE;
-            for (int k = 0; k < CA_STRIDE; ++k) ca[k] = 0.0f;
-        } else {
-            const int i = it - v.n_cams;
-            const float* H = v.pt_H + (size_t)i * PH_STRIDE;
-            const size_t e = v.pt_off + 3 * (size_t)i;
-            double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
-            const double d0 = fmin(fmax(a00, lo), hi), d1 = fmin(fmax(a11, lo), hi), d2 = fmin(fmax(a22, lo), hi);
-            a00 += mu * d0; a11 += mu * d1; a22 += mu * d2;
-            // Cholesky of the 3x3 block and its inverse M = L^-T L^-1
-            double m[6];
-            const double l00s = a00;
-            bool ok = l00s > 0.0;
-            double l00 = 0, l10 = 0, l20 = 0, l11 = 0, l21 = 0, l22 = 0;
-            if (ok) {
-                l00 = sqrt(l00s);
-                l10 = a01 / l00;
-                l20 = a02 / l00;
-                const double s11 = a11 - l10 * l10;
-                ok = s11 > 0.0;
-                if (ok) {
-                    l11 = sqrt(s11);
-                    l21 = (a12 - l20 * l10) / l11;
-                    const double s22 = a22 - l20 * l20 - l21 * l21;
-                    ok = s22 > 0.0;
-                    if (ok) l22 = sqrt(s22);
-                }
-            }
-            if (ok) {
-                const double i00 = 1.0 / l00, i11 = 1.0 / l11, i22 = 1.0 / l22;
-                const double i10 = -l10 * i00 * i11;
-                const double i21 = -l21 * i11 * i22;
-                const double i20 = -(l20 * i00 + l21 * i10) * i22;
-                m[0] = i00 * i00 + i10 * i10 + i20 * i20;
-                m[1] = i10 * i11 + i20 * i21;
-                m[2] = i20 * i22;
-                m[3] = i11 * i11 + i21 * i21;
-                m[4] = i21 * i22;
-                m[5] = i22 * i22;
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < v.n_cams; c += warps) {
+        const double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
+        double col[9];
+        const int j = lane < 18 ? lane : 17;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            if (j < 9) {
+                const int lo_i = i < j ? i : j, hi_i = i < j ? j : i;
+                double h = (double)v.cam_H[(size_t)c * CH_STRIDE + tri_index(9, lo_i, hi_i)];
+                if (i == j) h += mu * fmin(fmax(h, lo), hi);
+                col[i] = h;
             } else {
-                m[0] = a00 > 0 ? 1.0 / a00 : 0.0; m[1] = 0.0; m[2] = 0.0;
-                m[3] = a11 > 0 ? 1.0 / a11 : 0.0; m[4] = 0.0;
-                m[5] = a22 > 0 ? 1.0 / a22 : 0.0;
+                col[i] = (i == j - 9) ? 1.0 : 0.0;
             }
-            float* Mo = v.Minv_p + (size_t)i * MP_STRIDE;
-            for (int k = 0; k < 6; ++k) Mo[k] = (float)m[k];
-            v.D[e] = (float)d0; v.D[e + 1] = (float)d1; v.D[e + 2] = (float)d2;
-            const float r0 = -v.g[e], r1 = -v.g[e + 1], r2 = -v.g[e + 2];
-            const float z0 = fmaf(Mo[0], r0, fmaf(Mo[1], r1, Mo[2] * r2));
-            const float z1 = fmaf(Mo[1], r0, fmaf(Mo[3], r1, Mo[4] * r2));
-            const float z2 = fmaf(Mo[2], r0, fmaf(Mo[4], r1, Mo[5] * r2));
-            v.r[e] = r0; v.r[e + 1] = r1; v.r[e + 2] = r2;
-            v.z[e] = z0; v.z[e + 1] = z1; v.z[e + 2] = z2;
-            v.p[e] = 0.0f; v.p[e + 1] = 0.0f; v.p[e + 2] = 0.0f;
-            v.h[e] = 0.0f; v.h[e + 1] = 0.0f; v.h[e + 2] = 0.0f;
-            rz += (double)(r0 * z0 + r1 * z1 + r2 * z2);
-            rr += (double)(r0 * r0 + r1 * r1 + r2 * r2);
         }
+        // diagonal of J^T J for D and for the fallback, before elimination
+        const double hdiag = (lane < 9) ? (double)v.cam_H[(size_t)c * CH_STRIDE + tri_index(9, lane, lane)] : 0.0;
+        const bool ok = warp_block_inverse9(col, lane);
+        float* Mo = v.Minv_c + (size_t)c * MC_STRIDE;
+        if (lane >= 9 && lane < 18) {
+            const int jj = lane - 9;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Mo[i * 9 + jj] = (float)col[i];
+        }
+        if (!ok && lane < 9) {   // not SPD in FP64: inverse diagonal
+            const double dd = hdiag + mu * fmin(fmax(hdiag, lo), hi);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Mo[i * 9 + lane] = (i == lane && dd > 0.0) ? (float)(1.0 / dd) : 0.0f;
+        }
+        __syncwarp();
+        if (lane < 9) {
+            const size_t e = 9 * (size_t)c + lane;
+            v.D[e] = (float)fmin(fmax(hdiag, lo), hi);
+            const float ri = (float)(-cl[CL_G + lane]);
+            // z_i = sum_k M[i][k] r_k
+            float z = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) z = fmaf(Mo[lane * 9 + k], (float)(-cl[CL_G + k]), z);
+            v.r[e] = ri;
+            v.z[e] = z;
+            v.p[e] = 0.0f;
+            v.h[e] = 0.0f;
+            v.pc[e] = 0.0f;
+            v.pc[v.pc_stride + e] = 0.0f;
+            rz += (double)ri * (double)z;
+            rr += (double)ri * (double)ri;
+        }
+        if (lane < CA_STRIDE) v.cam_acc[(size_t)c * CA_STRIDE + lane] = 0.0f;
+    }
+    FOR_POINTS(i, v) {
+        const float* H = v.pt_H + (size_t)i * PH_STRIDE;
+        const size_t e = v.pt_off + 3 * (size_t)i;
+        double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
+        const double d0 = fmin(fmax(a00, lo), hi), d1 = fmin(fmax(a11, lo), hi), d2 = fmin(fmax(a22, lo), hi);
+        a00 += mu * d0; a11 += mu * d1; a22 += mu * d2;
+        // inverse of the SPD 3x3 block by its adjugate: M = adj(A) / det(A)
+        double m[6];
+        const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+        const double c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+        const double det = a00 * c00 + a01 * c01 + a02 * c02;
+        if (det > 0.0 && isfinite(det) && a00 > 0.0 && c22 > 0.0) {
+            const double id = rcp64(det);
+            m[0] = c00 * id; m[1] = c01 * id; m[2] = c02 * id;
+            m[3] = c11 * id; m[4] = c12 * id; m[5] = c22 * id;
+        } else {   // not SPD in FP64: inverse diagonal
+            m[0] = a00 > 0 ? 1.0 / a00 : 0.0; m[1] = 0.0; m[2] = 0.0;
+            m[3] = a11 > 0 ? 1.0 / a11 : 0.0; m[4] = 0.0;
+            m[5] = a22 > 0 ? 1.0 / a22 : 0.0;
+        }
+        float* Mo = v.Minv_p + (size_t)i * MP_STRIDE;
+        for (int k = 0; k < 6; ++k) Mo[k] = (float)m[k];
+        v.D[e] = (float)d0; v.D[e + 1] = (float)d1; v.D[e + 2] = (float)d2;
+        const float r0 = -v.g[e], r1 = -v.g[e + 1], r2 = -v.g[e + 2];
+        const float z0 = fmaf(Mo[0], r0, fmaf(Mo[1], r1, Mo[2] * r2));
+        const float z1 = fmaf(Mo[1], r0, fmaf(Mo[3], r1, Mo[4] * r2));
+        const float z2 = fmaf(Mo[2], r0, fmaf(Mo[4], r1, Mo[5] * r2));
+        v.r[e] = r0; v.r[e + 1] = r1; v.r[e + 2] = r2;
+        v.z[e] = z0; v.z[e + 1] = z1; v.z[e + 2] = z2;
+        v.p[e] = 0.0f; v.p[e + 1] = 0.0f; v.p[e + 2] = 0.0f;
+        v.h[e] = 0.0f; v.h[e + 1] = 0.0f; v.h[e + 2] = 0.0f;
+        rz += (double)(r0 * z0 + r1 * z1 + r2 * z2);
+        rr += (double)(r0 * r0 + r1 * r1 + r2 * r2);
     }
     double in[2] = {rz, rr}, out[2];
     if (grid_reduce<2>(in, v.partials, &st->tickets[TK_PRE], out) && threadIdx.x == 0) {
@@ -394,71 +349,57 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond) {
         st->rr = out[1];
         st->beta = 0.0;
         st->pcg_iter = 0;
+        for (int k = 0; k < NSLOT * SLOT_STRIDE; ++k) st->acc_mv[k] = st->acc_up[k] = 0.0;
         st->pcg_active = (out[1] > 0.0 && isfinite(out[0]) && st->opt.max_pcg > 0) ? 1 : 0;
         if (use_cond) cudaGraphSetConditional(pcg_cond, st->pcg_active ? 1u : 0u);
     }
 }
 
-// ------------------------------------------------------------------ K6 --------
-// PCG direction p = z + beta p; camera direction records phi = J_l p_w; p^T D p.
-__global__ void k_direction(Views<float> v) {
-    DevState* st = v.st;
-    if (st->pcg_active == 0) return;
-    const float beta = (float)st->beta;
-    double pdp = 0.0;
-    const int items = v.n_cams + v.n_pts;
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
-        if (it < v.n_cams) {
-            const size_t e = 9 * (size_t)it;
-            float pc[9];
-            float s = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                pc[k] = fmaf(beta, v.p[e + k], v.z[e + k]);
-                v.p[e + k] = pc[k];
-                s = fmaf(v.D[e + k] * pc[k], pc[k], s);
-            }
-            pdp += (double)s;
-            const float* JL = v.cam_pre + (size_t)it * CP_STRIDE + CP_JL;
-            float* d = v.cam_dir + (size_t)it * CD_STRIDE;
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-                d[CD_PHI + i] = fmaf(JL[3 * i], pc[0], fmaf(JL[3 * i + 1], pc[1], JL[3 * i + 2] * pc[2]));
-#pragma unroll
-            for (int k = 0; k < 6; ++k) d[CD_T + k] = pc[3 + k];
-        } else {
-            const size_t e = v.pt_off + 3 * (size_t)(it - v.n_cams);
-            float s = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float pk = fmaf(beta, v.p[e + k], v.z[e + k]);
-                v.p[e + k] = pk;
-                s = fmaf(v.D[e + k] * pk, pk, s);
-            }
-            pdp += (double)s;
-        }
-    }
-    double in[1] = {pdp}, out[1];
-    if (grid_reduce<1>(in, v.partials, &st->tickets[TK_DIR], out) && threadIdx.x == 0) st->pDp = out[0];
-}
-
 // ------------------------------------------------------------------ K4 --------
-// Damped normal operator q = J^T J p + mu D p (points; cameras finish in K5) and
-// |J p|^2.  The last block forms alpha = r^T z / (|J p|^2 + mu p^T D p).
-// gate: pointer to the flag that enables the kernel (null = always run).
+// One PCG direction step fused with the damped normal operator:
+//   p = zs + beta p_prev                 (zs = z during PCG; beta = 0 applies to a given p)
+//   q = J^T J p + mu D p                 (points; cameras are finished in K5)
+//   |J p|^2 and p^T D p are added to st->acc_mv.
+// Camera directions are double-buffered (pc[parity] holds p_prev, pc[parity ^ 1]
+// receives p); every CTA recomputes the direction record of the cameras it meets
+// from (zs, p_prev, J_l), and CTA b writes p for cameras b, b + grid, ...
+// Each tile's keys, points and point directions are staged in shared memory.
+
 template <int TB>
-__global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* gate) {
+__global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* gate, const float* zs, int use_beta) {
     if (gated_off(gate)) return;
-    __shared__ float qp[TILE_PTS * 3];
+    __shared__ float sx[3 * TILE_PTS], sd[3 * TILE_PTS], sq[3 * TILE_PTS];
+    __shared__ double red[32];
     DevState* st = v.st;
+    const int par = st->pcg_iter & 1;
+    const float beta = use_beta ? (float)st->beta : 0.0f;
+    const float* pc_old = v.pc + (size_t)par * v.pc_stride;
+    float* pc_new = v.pc + (size_t)(par ^ 1) * v.pc_stride;
     const float mu = (float)st->mu;
     const float eps = (float)st->opt.eps;
-    double jp2 = 0.0;
+    float pdp = 0.0f, jp2 = 0.0f;
+    // camera part of p owned by this CTA
+    for (int c = blockIdx.x; c < v.n_cams; c += gridDim.x) {
+        if (threadIdx.x < 9) {
+            const size_t e = 9 * (size_t)c + threadIdx.x;
+            const float pk = beta != 0.0f ? fmaf(beta, pc_old[e], zs[e]) : zs[e];
+            pc_new[e] = pk;
+            pdp = fmaf(v.D[e] * pk, pk, pdp);
+        }
+    }
     for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
         const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
         const int pt0 = tile * TILE_PTS;
         const int npt = min(TILE_PTS, v.n_pts - pt0);
-        for (int i = threadIdx.x; i < TILE_PTS * 3; i += TB) qp[i] = 0.0f;
+        const size_t base = v.pt_off + 3 * (size_t)pt0;
+        for (int i = threadIdx.x; i < 3 * npt; i += TB) {
+            const float pn = beta != 0.0f ? fmaf(beta, v.p[base + i], zs[base + i]) : zs[base + i];
+            v.p[base + i] = pn;
+            sd[i] = pn;
+            sx[i] = v.x[base + i];
+            sq[i] = 0.0f;
+            pdp = fmaf(v.D[base + i] * pn, pn, pdp);
+        }
         __syncthreads();
         const uint32_t n = hi - lo;
         const uint32_t chunk = (n + TB - 1) / TB;
@@ -469,156 +410,198 @@ __global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* ga
         for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
         Cam cam;
         float dir[9];
-        float jp2c = 0.0f;
-        for (uint32_t j = a; j < b; ++j) {
+        uint32_t j = a;
+        while (j < b) {
             const uint32_t key = __ldg(v.obs_key + j);
             const uint32_t c = key >> 8, slot = key & 0xffu;
             if (c != cur) {
                 if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
                 cur = c;
                 cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
-                load_dir(v.cam_dir + (size_t)c * CD_STRIDE, dir);
+                camera_dir(v, c, zs, pc_old, beta, dir);
             }
-            const size_t xi = v.pt_off + 3 * (size_t)(pt0 + slot);
-            const float X0 = __ldg(v.x + xi), X1 = __ldg(v.x + xi + 1), X2 = __ldg(v.x + xi + 2);
-            const float dX0 = v.p[xi], dX1 = v.p[xi + 1], dX2 = v.p[xi + 2];
-            const Geo g = project_geo(cam, X0, X1, X2, eps);
-            float t0, t1;
-            jdir(g, cam, dir, dX0, dX1, dX2, t0, t1);
-            jp2c = fmaf(t0, t0, fmaf(t1, t1, jp2c));
-            // adjoint: u = A^T t; camera gets (RX x u, u, intrinsic part), point gets R^T u
-            const float u0 = fmaf(g.A[0], t0, g.A[3] * t1);
-            const float u1 = fmaf(g.A[1], t0, g.A[4] * t1);
-            const float u2 = fmaf(g.A[2], t0, g.A[5] * t1);
-            acc[0] += fmaf(g.RX[1], u2, -g.RX[2] * u1);
-            acc[1] += fmaf(g.RX[2], u0, -g.RX[0] * u2);
-            acc[2] += fmaf(g.RX[0], u1, -g.RX[1] * u0);
-            acc[3] += u0;
-            acc[4] += u1;
-            acc[5] += u2;
-            const float pt = fmaf(g.p[0], t0, g.p[1] * t1);
-            const float fn2 = cam.f * g.n2;
-            acc[6] = fmaf(g.s, pt, acc[6]);
-            acc[7] = fmaf(fn2, pt, acc[7]);
-            acc[8] = fmaf(fn2 * g.n2, pt, acc[8]);
-            float* qs = qp + 3 * slot;
-            atomicAdd(qs + 0, fmaf(cam.R[0], u0, fmaf(cam.R[3], u1, cam.R[6] * u2)));
-            atomicAdd(qs + 1, fmaf(cam.R[1], u0, fmaf(cam.R[4], u1, cam.R[7] * u2)));
-            atomicAdd(qs + 2, fmaf(cam.R[2], u0, fmaf(cam.R[5], u1, cam.R[8] * u2)));
+            if (j + 1 < b) {
+                const uint32_t key1 = __ldg(v.obs_key + j + 1);
+                if ((key1 >> 8) == c) {
+                    // two observations of the same camera: independent chains interleave
+                    const uint32_t slot1 = key1 & 0xffu;
+                    const float a0 = obs_normal(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc, sq + 3 * slot);
+                    const float a1 = obs_normal(cam, dir, sx + 3 * slot1, sd + 3 * slot1, eps, acc, sq + 3 * slot1);
+                    jp2 += a0 + a1;
+                    j += 2;
+                    continue;
+                }
+            }
+            jp2 += obs_normal(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc, sq + 3 * slot);
+            j += 1;
         }
         const bool head = seg_reduce<9>(cur, acc);
         if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
-        jp2 += (double)jp2c;
         __syncthreads();
-        const size_t base = v.pt_off + 3 * (size_t)pt0;
-        for (int i = threadIdx.x; i < npt * 3; i += TB)
-            v.q[base + i] = fmaf(mu * v.D[base + i], v.p[base + i], qp[i]);
+        for (int i = threadIdx.x; i < 3 * npt; i += TB) v.q[base + i] = fmaf(mu * v.D[base + i], sd[i], sq[i]);
         __syncthreads();
     }
-    double in[1] = {jp2}, out[1];
-    if (grid_reduce<1>(in, v.partials, &st->tickets[TK_MV], out) && threadIdx.x == 0) {
-        st->jp2 = out[0];
-        const double denom = out[0] + st->mu * st->pDp;
-        if (denom > 0.0 && isfinite(denom)) {
-            st->alpha = st->rz / denom;
-        } else {
-            st->alpha = 0.0;
-            if (st->pcg_active) {
-                st->pcg_active = 0;
-                if (!isfinite(denom)) st->status = 4;
-            }
-        }
+    const double bj = block_sum((double)jp2, red);
+    const double bp = block_sum((double)pdp, red);
+    if (threadIdx.x == 0) {
+        slot_add(st->acc_mv, 0, bj);
+        slot_add(st->acc_mv, 1, bp);
     }
 }
 
 // ------------------------------------------------------------------ K5 --------
-// h += alpha p; r -= alpha q; z = M^-1 r; r^T z and |r|^2.  Cameras first finish
-// q = J_l^T (sum RX x u), sum u, intrinsic part + mu D p from the K4 accumulators.
-// Never gated: its last block decides whether PCG continues and sets the loop flag.
+// alpha = r^T z / (|J p|^2 + mu p^T D p); h += alpha p; r -= alpha q; z = M^-1 r; the
+// sums r^T z and |r|^2 go to st->acc_up.  Cameras first finish
+// q = (J_l^T sum RX x u, sum u, intrinsic part) + mu D p from the K4 accumulators.
+// Points run four at a time with float4 accesses.  Never gated: its last block
+// decides whether PCG continues, sets the loop flag and clears the accumulators.
 __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond) {
     DevState* st = v.st;
+    __shared__ double red[32];
+    __shared__ double sh_mv[2];
+    __shared__ bool is_last;
     const int active = st->pcg_active;
-    double rz = 0.0, rr = 0.0;
+    float rz = 0.0f, rr = 0.0f;
+    double alpha_d = 0.0;
+    bool bad = false;
     if (active) {
-        const float alpha = (float)st->alpha;
+        if (threadIdx.x < 32) {
+            const double a0 = slot_sum_warp(st->acc_mv, 0), a1 = slot_sum_warp(st->acc_mv, 1);
+            if (threadIdx.x == 0) { sh_mv[0] = a0; sh_mv[1] = a1; }
+        }
+        __syncthreads();
+        const double denom = sh_mv[0] + st->mu * sh_mv[1];
+        bad = !(denom > 0.0) || !isfinite(denom);
+        alpha_d = bad ? 0.0 : st->rz / denom;
+    }
+    if (active && !bad) {
+        const float alpha = (float)alpha_d;
         const float mu = (float)st->mu;
-        const int items = v.n_cams + v.n_pts;
-        for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
-            if (it < v.n_cams) {
-                const int c = it;
-                const size_t e = 9 * (size_t)c;
-                float* ca = v.cam_acc + (size_t)c * CA_STRIDE;
-                const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
-                float q[9];
+        const float* pcur = v.pc + (size_t)((st->pcg_iter & 1) ^ 1) * v.pc_stride;
+        FOR_CAMERAS(c, v) {
+            const size_t e = 9 * (size_t)c;
+            float* ca = v.cam_acc + (size_t)c * CA_STRIDE;
+            const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
+            float q[9];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) q[k] = fmaf(JL[k], ca[0], fmaf(JL[3 + k], ca[1], JL[6 + k] * ca[2]));
+            for (int k = 0; k < 3; ++k) q[k] = fmaf(JL[k], ca[0], fmaf(JL[3 + k], ca[1], JL[6 + k] * ca[2]));
 #pragma unroll
-                for (int k = 3; k < 9; ++k) q[k] = ca[k];
+            for (int k = 3; k < 9; ++k) q[k] = ca[k];
 #pragma unroll
-                for (int k = 0; k < CA_STRIDE; ++k) ca[k] = 0.0f;
-                float rn[9];
+            for (int k = 0; k < CA_STRIDE; ++k) ca[k] = 0.0f;
+            float rn[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const float pk = v.p[e + k];
-                    const float qk = fmaf(mu * v.D[e + k], pk, q[k]);
-                    v.h[e + k] = fmaf(alpha, pk, v.h[e + k]);
-                    rn[k] = fmaf(-alpha, qk, v.r[e + k]);
-                    v.r[e + k] = rn[k];
-                }
-                const float* M = v.Minv_c + (size_t)c * MC_STRIDE;
-                float s_rz = 0.0f, s_rr = 0.0f;
+            for (int k = 0; k < 9; ++k) {
+                const float pk = pcur[e + k];
+                const float qk = fmaf(mu * v.D[e + k], pk, q[k]);
+                v.p[e + k] = pk;
+                v.h[e + k] = fmaf(alpha, pk, v.h[e + k]);
+                rn[k] = fmaf(-alpha, qk, v.r[e + k]);
+                v.r[e + k] = rn[k];
+            }
+            const float* M = v.Minv_c + (size_t)c * MC_STRIDE;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    float z = 0.0f;
+            for (int i = 0; i < 9; ++i) {
+                float z = 0.0f;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) z = fmaf(M[9 * i + k], rn[k], z);
-                    v.z[e + i] = z;
-                    s_rz = fmaf(rn[i], z, s_rz);
-                    s_rr = fmaf(rn[i], rn[i], s_rr);
-                }
-                rz += (double)s_rz;
-                rr += (double)s_rr;
-            } else {
-                const int i = it - v.n_cams;
-                const size_t e = v.pt_off + 3 * (size_t)i;
-                float rn[3];
+                for (int k = 0; k < 9; ++k) z = fmaf(M[9 * i + k], rn[k], z);
+                v.z[e + i] = z;
+                rz = fmaf(rn[i], z, rz);
+                rr = fmaf(rn[i], rn[i], rr);
+            }
+        }
+        for (int qd = blockIdx.x * blockDim.x + threadIdx.x; qd < v.n_quads; qd += gridDim.x * blockDim.x) {
+            const size_t e = v.pt_off + 12 * (size_t)qd;
+            float4* p4 = reinterpret_cast<float4*>(v.p + e);
+            float4* h4 = reinterpret_cast<float4*>(v.h + e);
+            float4* r4 = reinterpret_cast<float4*>(v.r + e);
+            const float4* q4 = reinterpret_cast<const float4*>(v.q + e);
+            float4* z4 = reinterpret_cast<float4*>(v.z + e);
+            const float4* m4 = reinterpret_cast<const float4*>(v.Minv_p + 24 * (size_t)qd);
+            float P[12], H[12], R[12], Q[12], M[24];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float pk = v.p[e + k];
-                    v.h[e + k] = fmaf(alpha, pk, v.h[e + k]);
-                    rn[k] = fmaf(-alpha, v.q[e + k], v.r[e + k]);
-                    v.r[e + k] = rn[k];
-                }
-                const float* M = v.Minv_p + (size_t)i * MP_STRIDE;
-                const float z0 = fmaf(M[0], rn[0], fmaf(M[1], rn[1], M[2] * rn[2]));
-                const float z1 = fmaf(M[1], rn[0], fmaf(M[3], rn[1], M[4] * rn[2]));
-                const float z2 = fmaf(M[2], rn[0], fmaf(M[4], rn[1], M[5] * rn[2]));
-                v.z[e] = z0; v.z[e + 1] = z1; v.z[e + 2] = z2;
-                rz += (double)fmaf(rn[0], z0, fmaf(rn[1], z1, rn[2] * z2));
-                rr += (double)fmaf(rn[0], rn[0], fmaf(rn[1], rn[1], rn[2] * rn[2]));
+            for (int k = 0; k < 3; ++k) {
+                const float4 a = p4[k], b = h4[k], c = r4[k], d = q4[k];
+                P[4 * k] = a.x; P[4 * k + 1] = a.y; P[4 * k + 2] = a.z; P[4 * k + 3] = a.w;
+                H[4 * k] = b.x; H[4 * k + 1] = b.y; H[4 * k + 2] = b.z; H[4 * k + 3] = b.w;
+                R[4 * k] = c.x; R[4 * k + 1] = c.y; R[4 * k + 2] = c.z; R[4 * k + 3] = c.w;
+                Q[4 * k] = d.x; Q[4 * k + 1] = d.y; Q[4 * k + 2] = d.z; Q[4 * k + 3] = d.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float4 a = __ldg(m4 + k);
+                M[4 * k] = a.x; M[4 * k + 1] = a.y; M[4 * k + 2] = a.z; M[4 * k + 3] = a.w;
+            }
+            float Z[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                H[k] = fmaf(alpha, P[k], H[k]);
+                R[k] = fmaf(-alpha, Q[k], R[k]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float* m = M + 6 * j;
+                const float* rj = R + 3 * j;
+                Z[3 * j + 0] = fmaf(m[0], rj[0], fmaf(m[1], rj[1], m[2] * rj[2]));
+                Z[3 * j + 1] = fmaf(m[1], rj[0], fmaf(m[3], rj[1], m[4] * rj[2]));
+                Z[3 * j + 2] = fmaf(m[2], rj[0], fmaf(m[4], rj[1], m[5] * rj[2]));
+            }
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                rz = fmaf(R[k], Z[k], rz);
+                rr = fmaf(R[k], R[k], rr);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                h4[k] = make_float4(H[4 * k], H[4 * k + 1], H[4 * k + 2], H[4 * k + 3]);
+                r4[k] = make_float4(R[4 * k], R[4 * k + 1], R[4 * k + 2], R[4 * k + 3]);
+                z4[k] = make_float4(Z[4 * k], Z[4 * k + 1], Z[4 * k + 2], Z[4 * k + 3]);
             }
         }
     }
-    double in[2] = {rz, rr}, out[2];
-    if (grid_reduce<2>(in, v.partials, &st->tickets[TK_UPD], out) && threadIdx.x == 0) {
-        if (active) {
+    const double brz = block_sum((double)rz, red);
+    const double brr = block_sum((double)rr, red);
+    if (threadIdx.x == 0) {
+        if (active && !bad) {
+            slot_add(st->acc_up, 0, brz);
+            slot_add(st->acc_up, 1, brr);
+        }
+        __threadfence();
+        const unsigned int t = atomicAdd(&st->tickets[TK_UPD], 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last || threadIdx.x >= 32) return;
+    __threadfence();
+    const double rzn = slot_sum_warp(st->acc_up, 0), rrn = slot_sum_warp(st->acc_up, 1);
+    // the whole warp clears the slots; lane 0 takes the decisions
+    for (int k = threadIdx.x; k < NSLOT * SLOT_STRIDE; k += 32) st->acc_mv[k] = st->acc_up[k] = 0.0;
+    if (threadIdx.x != 0) return;
+    if (active) {
+        if (bad) {
+            st->pcg_active = 0;
+            if (!isfinite(sh_mv[0]) || !isfinite(sh_mv[1])) st->status = 4;
+        } else {
+            st->alpha = alpha_d;
+            st->jp2 = sh_mv[0];
+            st->pDp = sh_mv[1];
             st->pcg_iter += 1;
             st->pcg_total += 1;
-            st->rr = out[1];
+            st->rr = rrn;
             const double tol = st->opt.tol;
-            const bool converged = out[1] <= tol * tol * st->rr0;
-            if (!isfinite(out[0]) || !isfinite(out[1])) {
+            if (!isfinite(rzn) || !isfinite(rrn)) {
                 st->status = 4;
                 st->pcg_active = 0;
-            } else if (converged || st->pcg_iter >= st->opt.max_pcg) {
+            } else if (rrn <= tol * tol * st->rr0 || st->pcg_iter >= st->opt.max_pcg) {
                 st->pcg_active = 0;
             } else {
-                st->beta = out[0] / st->rz;
-                st->rz = out[0];
+                st->beta = rzn / st->rz;
+                st->rz = rzn;
             }
         }
-        if (use_cond) cudaGraphSetConditional(pcg_cond, st->pcg_active ? 1u : 0u);
     }
+    st->tickets[TK_UPD] = 0u;
+    if (use_cond) cudaGraphSetConditional(pcg_cond, st->pcg_active ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------ K7 --------
@@ -628,10 +611,8 @@ __global__ void k_candidate(Views<float> v) {
     DevState* st = v.st;
     if (st->lm_active == 0) return;
     double gh = 0.0;
-    const int items = v.n_cams + v.n_pts;
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
-        if (it < v.n_cams) {
-            const int c = it;
+    FOR_CAMERAS(c, v) {
+        {
             const size_t e = 9 * (size_t)c;
             const double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
             double xn[9];
@@ -652,8 +633,11 @@ __global__ void k_candidate(Views<float> v) {
                 d[CD_PHI + i] = fmaf(JL[3 * i], hc[0], fmaf(JL[3 * i + 1], hc[1], JL[3 * i + 2] * hc[2]));
 #pragma unroll
             for (int k = 0; k < 6; ++k) d[CD_T + k] = hc[3 + k];
-        } else {
-            const size_t e = v.pt_off + 3 * (size_t)(it - v.n_cams);
+        }
+    }
+    FOR_POINTS(i, v) {
+        {
+            const size_t e = v.pt_off + 3 * (size_t)i;
             float s = 0.0f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -777,8 +761,11 @@ __global__ void k_commit(Views<float> v) {
 #pragma unroll
             for (int k = 0; k < CP_STRIDE / 4; ++k) d[k] = s[k];
             double* cl = v.cam_lin + (size_t)it * CL_STRIDE;
-#pragma unroll 8
+#pragma unroll
             for (int k = 0; k < CL_STRIDE; ++k) cl[k] = 0.0;
+            float* ch = v.cam_H + (size_t)it * CH_STRIDE;
+#pragma unroll
+            for (int k = 0; k < CH_STRIDE; ++k) ch[k] = 0.0f;
         } else {
             const size_t e = v.pt_off + 3 * (size_t)(it - v.n_cams);
 #pragma unroll
@@ -861,37 +848,16 @@ __global__ void k_normal_out(Views<float> v, S* out) {
     }
 }
 
-// p from a caller-layout vector; camera direction records and p^T D p.
+// p (internal layout) from a caller-layout vector.
 template <typename S>
 __global__ void k_set_direction(Views<float> v, const S* src) {
-    double pdp = 0.0;
-    const int items = v.n_cams + v.n_pts;
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
-        if (it < v.n_cams) {
-            const size_t e = 9 * (size_t)it;
-            float pc[9];
-            for (int k = 0; k < 9; ++k) {
-                pc[k] = (float)src[e + k];
-                v.p[e + k] = pc[k];
-                pdp += (double)v.D[e + k] * pc[k] * pc[k];
-            }
-            const float* JL = v.cam_pre + (size_t)it * CP_STRIDE + CP_JL;
-            float* d = v.cam_dir + (size_t)it * CD_STRIDE;
-            for (int i = 0; i < 3; ++i)
-                d[CD_PHI + i] = fmaf(JL[3 * i], pc[0], fmaf(JL[3 * i + 1], pc[1], JL[3 * i + 2] * pc[2]));
-            for (int k = 0; k < 6; ++k) d[CD_T + k] = pc[3 + k];
-        } else {
-            const int u = it - v.n_cams;
-            const size_t e = v.pt_off + 3 * (size_t)v.pt_internal[u];
-            for (int k = 0; k < 3; ++k) {
-                const float pk = (float)src[9 * (size_t)v.n_cams + 3 * (size_t)u + k];
-                v.p[e + k] = pk;
-                pdp += (double)v.D[e + k] * pk * pk;
-            }
-        }
+    FOR_CAMERAS(c, v) {
+        for (int k = 0; k < 9; ++k) v.p[9 * (size_t)c + k] = (float)src[9 * (size_t)c + k];
     }
-    double in[1] = {pdp}, out[1];
-    if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_DIR], out) && threadIdx.x == 0) v.st->pDp = out[0];
+    FOR_POINTS(u, v) {
+        const size_t e = v.pt_off + 3 * (size_t)v.pt_internal[u];
+        for (int k = 0; k < 3; ++k) v.p[e + k] = (float)src[9 * (size_t)v.n_cams + 3 * (size_t)u + k];
+    }
 }
 
 // ------------------------------------------------------------------ launchers --
@@ -912,17 +878,17 @@ void launch_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s,
     k_linearize<LIN_TB><<<grid_tiles(L.lin_grid, v.n_tiles), LIN_TB, 0, s>>>(v, mode, res_out, jac_out,
                                                                              lm_cond, use_cond);
 }
-void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
-    k_precond<<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v, c, use);
+void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
+                    double* pslots) {
+    k_precond<<<grid_items(L, std::max(v.n_pts, 32 * v.n_cams)), L.item_block, 0, s>>>(v, c, use, pslots);
 }
-void launch_direction(const Views<float>& v, const LaunchCfg& L, cudaStream_t s) {
-    k_direction<<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v);
-}
-void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate) {
-    k_matvec<MV_TB><<<grid_tiles(L.mv_grid, v.n_tiles), MV_TB, 0, s>>>(v, gate);
+void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
+                   const float* zs, int use_beta) {
+    (void)L;
+    k_matvec<MV_TB><<<v.n_tiles > 0 ? v.n_tiles : 1, MV_TB, 0, s>>>(v, gate, zs, use_beta);
 }
 void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
-    k_update<<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v, c, use);
+    k_update<<<grid_items(L, v.n_quads), L.item_block, 0, s>>>(v, c, use);
 }
 void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s) {
     k_candidate<<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v);

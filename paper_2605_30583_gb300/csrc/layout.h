@@ -2,8 +2,10 @@
 // one allocation for the whole optimisation, every array a view into it).
 //
 // Parameter-space vectors (x, h, r, z, p, q, g, D) are FP32 (FP64 in the plain form)
-// of length n_vec = pt_off + round_up(3 n_pts, 4), with camera c at [9c, 9c+9) and
-// internal point i at [pt_off + 3i, pt_off + 3i + 3).  Internal point order is the
+// of length n_vec = pt_off + 12 n_quads, n_quads = ceil(n_pts / 4), with camera c at
+// [9c, 9c+9) and internal point i at [pt_off + 3i, pt_off + 3i + 3); pt_off is a
+// multiple of 4, so four consecutive points are three aligned float4.  Padding
+// entries stay zero.  Internal point order is the
 // locality order built at bind time; pt_user / pt_internal map between the two.
 #pragma once
 
@@ -12,10 +14,14 @@
 
 namespace gbba {
 
-constexpr int TILE_PTS = 128;       // points per tile; an observation's tile slot fits 8 bits
+constexpr int TILE_PTS = 256;       // points per tile; an observation's tile slot fits 8 bits
 constexpr int HIST_CAP = 1024;      // LM iterations recorded in the device history
 constexpr int MAX_GRID = 4096;      // upper bound on blocks of any reduction kernel
 constexpr int NPART = 4;            // doubles of partial sums per block
+constexpr int NSLOT = 32;           // atomic accumulator slots per scalar sum
+constexpr int SLOT_STRIDE = 16;     // doubles between slots (one 128-byte line)
+constexpr int MAX_PBLOCKS = 1024;   // CTAs of the persistent PCG kernel
+constexpr int PSLOT_DOUBLES = 6 * NSLOT * SLOT_STRIDE;   // 3 rotating sets x (matvec, update)
 
 // Camera record (floats), written once per parameter change (FP64 math, FP32 store).
 enum : int { CP_R = 0, CP_T = 9, CP_F = 12, CP_K1 = 13, CP_K2 = 14, CP_PAD = 15,
@@ -24,9 +30,10 @@ enum : int { CP_R = 0, CP_T = 9, CP_F = 12, CP_K1 = 13, CP_K2 = 14, CP_PAD = 15,
 enum : int { CD_PHI = 0, CD_T = 3, CD_I = 6, CD_STRIDE = 12 };
 // Camera matvec accumulator (floats): sum (R X) x u (3), sum u (3), intrinsic part (3), pad.
 enum : int { CA_STRIDE = 12 };
-// Camera linearisation accumulator (doubles): g = J_c^T r (9), upper triangle of
-// J_c^T J_c row by row (45), pad (2).
-enum : int { CL_G = 0, CL_H = 9, CL_STRIDE = 56 };
+// Camera gradient accumulator (doubles): g = J_c^T r (9), pad (3).
+enum : int { CL_G = 0, CL_STRIDE = 12 };
+// Camera block accumulator (floats): upper triangle of J_c^T J_c row by row (45), pad (3).
+enum : int { CH_STRIDE = 48 };
 // Point linearisation record (floats): upper triangle xx, xy, xz, yy, yz, zz.
 enum : int { PH_STRIDE = 6 };
 // Inverse preconditioner blocks: full 9x9 per camera (floats), packed 3x3 per point.
@@ -55,19 +62,26 @@ struct DevState {
     DevOptions opt;
     double mu, nu, F, F_new, F0, rho, L, gh, jh2;
     double rz, rr0, rr, alpha, beta, pDp, jp2, cost_out;
+    // Per-iteration sums, spread over NSLOT slots (block b adds into slot b % NSLOT,
+    // one 128-byte line each) so concurrent atomics do not queue on one address.
+    double acc_mv[NSLOT * SLOT_STRIDE];   // k = 0: |J p|^2, k = 1: p^T D p
+    double acc_up[NSLOT * SLOT_STRIDE];   // k = 0: r^T z,   k = 1: |r|^2
     int32_t lm_iter, lm_active, accepted, relin, n_accepted, status;
     int32_t pcg_iter, pcg_active, pcg_total, pad0;
     int64_t t_start, t_end;
     uint32_t tickets[TK_COUNT];
+    uint32_t bar_count, bar_gen;   // grid barrier of the persistent PCG kernel
+    int32_t bar_err, pad1;
     IterRec hist[HIST_CAP];
 };
 
 // Device views of one bound problem.  Built on the host from the workspace base.
 template <typename T>
 struct Views {
-    int32_t n_cams, n_pts, n_tiles;
+    int32_t n_cams, n_pts, n_tiles, n_quads;
     int64_t n_obs;
     int64_t pt_off, n_vec;
+    int64_t pc_stride;           // floats between the two camera-direction buffers
     // observations, tile-major and camera-sorted inside each tile
     const uint32_t* obs_key;     // cam << 8 | tile slot
     const T* obs_uv;             // [n_obs][2]
@@ -75,14 +89,18 @@ struct Views {
     const uint32_t* tile_off;    // [n_tiles + 1]
     const uint32_t* pt_user;     // internal -> caller point index
     const uint32_t* pt_internal; // caller -> internal point index
+    const uint32_t* obs_pm;      // point-major order: positions (in the order above) of each
+    const uint32_t* pt_obs_off;  //   internal point's observations, offsets [n_pts + 1]
     // vectors of length n_vec
     T *x, *x_new, *h, *r, *z, *p, *q, *g, *D;
     // camera records
     float *cam_pre, *cam_pre_new, *cam_dir, *cam_acc;
+    float* pc;        // camera part of the PCG direction, double-buffered [2][pc_stride]
     double* cam_lin;
-    T* pt_H;          // [n_pts][6]
+    float* cam_H;
+    T* pt_H;          // [4 n_quads][6]
     T* Minv_c;        // [n_cams][81]
-    T* Minv_p;        // [n_pts][6]
+    T* Minv_p;        // [4 n_quads][6]
     T* jac;           // plain form only: stored Jacobian [n_obs][2][12]
     T* res;           // plain form only: stored residuals [n_obs][2]
     DevState* st;

@@ -119,6 +119,23 @@ __global__ void k_obs_gather(const uint64_t* keys, const uint32_t* vals, const d
     }
 }
 
+// Point-major index: key = (internal point, position in the tile-major order).
+__global__ void k_pm_keys(const uint32_t* vals, const uint32_t* pt_idx, const uint32_t* pt_internal, int64_t n_obs,
+                          size_t sort_n, uint64_t* keys) {
+    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < sort_n; j += (size_t)gridDim.x * blockDim.x)
+        keys[j] = j < (size_t)n_obs ? (((uint64_t)pt_internal[pt_idx[vals[j]]] << 32) | (uint64_t)j) : ~0ull;
+}
+
+__global__ void k_pm_finish(const uint64_t* keys, int64_t n_obs, int n_pts, uint32_t* obs_pm, uint32_t* pt_obs_off) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_obs; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = keys[k];
+        obs_pm[k] = (uint32_t)(key & 0xffffffffu);
+        const uint32_t ip = (uint32_t)(key >> 32);
+        if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != ip) pt_obs_off[ip] = (uint32_t)k;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) pt_obs_off[n_pts] = (uint32_t)n_obs;
+}
+
 // --- bitonic network --------------------------------------------------------------
 
 // Compare-exchange of positions i < l = i + j; ascending iff (i & k) == 0.
@@ -232,6 +249,12 @@ void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s) {
                                                            const_cast<uint32_t*>(v.obs_key),
                                                            const_cast<T*>(v.obs_uv),
                                                            const_cast<uint32_t*>(v.obs_user));
+    // 4. point-major index over the tile-major order (every point has >= 2 observations,
+    //    so every internal point owns a non-empty run)
+    k_pm_keys<<<blocks_for(no2, TB), TB, 0, s>>>(b.vals, b.pt_idx, pt_internal, v.n_obs, no2, b.keys);
+    bitonic_sort(b.keys, b.vals, no2, s);
+    k_pm_finish<<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.keys, v.n_obs, v.n_pts, const_cast<uint32_t*>(v.obs_pm),
+                                                        const_cast<uint32_t*>(v.pt_obs_off));
 }
 
 template void build_order<float>(const Views<float>&, const OrderBuffers&, cudaStream_t);

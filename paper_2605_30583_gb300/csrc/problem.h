@@ -23,9 +23,10 @@ ba_status cuda_status(cudaError_t e, const char* what);
 
 // Offsets (bytes) of every array inside the workspace.
 struct Layout {
-    size_t state, partials, obs_key, obs_uv, obs_user, tile_off, pt_user, pt_internal;
+    size_t state, partials, obs_key, obs_uv, obs_user, tile_off, pt_user, pt_internal, obs_pm, pt_obs_off;
     size_t vec[9];                       // x, x_new, h, r, z, p, q, g, D
-    size_t cam_pre, cam_pre_new, cam_dir, cam_acc, cam_lin, pt_H, Minv_c, Minv_p, jac, res, staging;
+    size_t blk_tile, blk_cam_off, blk_cams, pslots;
+    size_t cam_pre, cam_pre_new, cam_dir, cam_acc, pc, cam_lin, cam_H, pt_H, Minv_c, Minv_p, jac, res, staging;
     size_t s_cam_idx, s_pt_idx, s_pixels, s_pt_key, s_tile_cnt, s_keys, s_vals, sort_cap;
     size_t total;
 };
@@ -55,8 +56,18 @@ struct ba_problem {
     gbba::Views<float> vf{};
     gbba::Views<double> vd{};
     gbba::LaunchCfg L{};
-    gbba::GraphCache graph{};
+    gbba::GraphCache graph{};            // conditional-loop graph (any options)
+    gbba::GraphCache graph_unrolled{};   // fixed predicated sequence for (unrolled_lm, unrolled_pcg)
+    int32_t unrolled_lm = -1, unrolled_pcg = -1;
     int device = 0;
+    // persistent PCG plan (mixed precision, problems whose tiles fit in shared memory)
+    bool persistent = false;        // the plan fits
+    bool use_persistent = false;    // the plan is used by the current solve sequences
+    int p_grid = 0, p_smem = 0;
+    uint32_t* blk_tile = nullptr;   // device, [p_grid + 1]
+    uint32_t* blk_cam_off = nullptr;   // device, [p_grid + 1]: per-CTA camera list offsets
+    uint32_t* blk_cams = nullptr;      // device, the lists (inside the ordering region of the workspace)
+    double* pslots = nullptr;       // device, [PSLOT_DOUBLES]
 };
 
 namespace gbba {
