@@ -97,8 +97,11 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     if (precision == BA_PREC_FP64) {
         l.jac = s.take(T * 24 * no);
         l.res = s.take(T * 2 * no);
+        l.cam64 = s.take(8 * CP_STRIDE * nc);
+        l.cam64_new = s.take(8 * CP_STRIDE * nc);
+        l.cam_H64 = s.take(8 * CH_STRIDE * nc);
     } else {
-        l.jac = l.res = 0;
+        l.jac = l.res = l.cam64 = l.cam64_new = l.cam_H64 = 0;
     }
     // ordering scratch (only live during ba_bind_workspace), overlaps the solver arrays
     Bump o;
@@ -148,6 +151,9 @@ Views<T> make_views(ba_problem* p) {
     v.pt_H = (T*)(w + l.pt_H);
     v.Minv_c = (T*)(w + l.Minv_c);
     v.Minv_p = (T*)(w + l.Minv_p);
+    v.cam64 = l.cam64 ? (double*)(w + l.cam64) : nullptr;
+    v.cam64_new = l.cam64_new ? (double*)(w + l.cam64_new) : nullptr;
+    v.cam_H64 = l.cam_H64 ? (double*)(w + l.cam_H64) : nullptr;
     v.jac = l.jac ? (T*)(w + l.jac) : nullptr;
     v.res = l.res ? (T*)(w + l.res) : nullptr;
     v.st = (DevState*)(w + l.state);
@@ -160,35 +166,69 @@ template Views<float> make_views<float>(ba_problem*);
 template Views<double> make_views<double>(ba_problem*);
 
 // ------------------------------------------------------------------ solve ------
+// The solve is four kinds of steps, for either precision:
+//   init      first linearisation of the solve;
+//   lm_head   block-Jacobi preconditioner (and, with the persistent plan, the whole PCG);
+//   pcg_iter  one PCG iteration (multi-kernel PCG only);
+//   lm_tail   candidate step, its evaluation and the LM decision, commit, relinearise.
 
-static void enqueue_lm_body_mixed(ba_problem* p, cudaStream_t s, CondHandle lm_c, CondHandle pcg_c, int use_cond,
-                                  cudaStream_t pcg_stream, bool inline_pcg, int max_pcg);
+static bool inner_pcg(const ba_problem* p) { return !(p->precision == BA_PREC_MIXED && p->use_persistent); }
 
-static void enqueue_pcg_iteration_mixed(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int use_cond) {
-    const Views<float>& v = p->vf;
-    launch_matvec(v, p->L, s, &v.st->pcg_active, v.z, 1);
-    launch_update(v, p->L, s, pcg_c, use_cond);
-}
-
-static void enqueue_lm_body_mixed(ba_problem* p, cudaStream_t s, CondHandle lm_c, CondHandle pcg_c, int use_cond,
-                                  cudaStream_t, bool inline_pcg, int max_pcg) {
-    const Views<float>& v = p->vf;
-    launch_precond(v, p->L, s, pcg_c, use_cond, p->use_persistent ? p->pslots : nullptr);
-    if (p->use_persistent) {
-        launch_pcg_persistent(v, p->blk_tile, p->blk_cam_off, p->blk_cams, p->pslots, p->p_grid, p->p_smem, s);
-    } else if (inline_pcg) {
-        for (int k = 0; k < max_pcg; ++k) enqueue_pcg_iteration_mixed(p, s, pcg_c, use_cond);
+static void step_init(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use) {
+    if (p->precision == BA_PREC_MIXED) {
+        launch_init_state(p->vf.st, s);
+        launch_camera_precompute(p->vf, p->L, s);
+        launch_linearize(p->vf, p->L, s, 0, nullptr, nullptr, lm_c, use);
+    } else {
+        launch_init_state(p->vd.st, s);
+        launch64_camera_precompute(p->vd, p->L, s);
+        launch64_linearize(p->vd, p->L, s, 0, nullptr, nullptr, lm_c, use);
     }
-    (void)lm_c;
 }
 
-static void enqueue_lm_tail_mixed(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use_cond) {
-    const Views<float>& v = p->vf;
-    launch_candidate(v, p->L, s);
-    launch_eval_candidate(v, p->L, s, lm_c, use_cond);
-    launch_commit(v, p->L, s);
-    launch_linearize(v, p->L, s, 1, nullptr, nullptr, lm_c, 0);
+static void step_pcg_iter(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int use) {
+    if (p->precision == BA_PREC_MIXED) {
+        const Views<float>& v = p->vf;
+        launch_matvec(v, p->L, s, &v.st->pcg_active, v.z, 1);
+        launch_update(v, p->L, s, pcg_c, use);
+    } else {
+        const Views<double>& v = p->vd;
+        launch64_direction(v, p->L, s, v.z, 1, &v.st->pcg_active);
+        launch64_matvec(v, p->L, s, &v.st->pcg_active);
+        launch64_update(v, p->L, s, pcg_c, use);
+    }
 }
+
+static void step_lm_head(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int use, bool inline_pcg, int max_pcg) {
+    if (p->precision == BA_PREC_MIXED) {
+        const Views<float>& v = p->vf;
+        launch_precond(v, p->L, s, pcg_c, use, p->use_persistent ? p->pslots : nullptr);
+        if (p->use_persistent)
+            launch_pcg_persistent(v, p->blk_tile, p->blk_cam_off, p->blk_cams, p->pslots, p->p_grid, p->p_smem, s);
+    } else {
+        launch64_precond(p->vd, p->L, s, pcg_c, use);
+    }
+    if (inline_pcg && inner_pcg(p))
+        for (int k = 0; k < max_pcg; ++k) step_pcg_iter(p, s, pcg_c, use);
+}
+
+static void step_lm_tail(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use) {
+    if (p->precision == BA_PREC_MIXED) {
+        const Views<float>& v = p->vf;
+        launch_candidate(v, p->L, s);
+        launch_eval_candidate(v, p->L, s, lm_c, use);
+        launch_commit(v, p->L, s);
+        launch_linearize(v, p->L, s, 1, nullptr, nullptr, lm_c, 0);
+    } else {
+        const Views<double>& v = p->vd;
+        launch64_candidate(v, p->L, s);
+        launch64_eval_candidate(v, p->L, s, lm_c, use);
+        launch64_commit(v, p->L, s);
+        launch64_linearize(v, p->L, s, 1, nullptr, nullptr, lm_c, 0);
+    }
+}
+
+static DevState* dev_state(ba_problem* p) { return p->precision == BA_PREC_MIXED ? p->vf.st : p->vd.st; }
 
 // Adds a WHILE conditional node at the current capture position of `s`; returns its
 // body graph.  The handle must already exist on the capturing graph.
@@ -212,44 +252,41 @@ static cudaError_t add_while_node(cudaStream_t s, CondHandle h, cudaGraph_t* bod
     return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
-// One CUDA graph for a whole solve: init, then WHILE(lm) { precond; WHILE(pcg)
-// { direction; matvec; update }; candidate; evaluate; commit; relinearise }, finish.
-// Loop flags are set on the device by the kernels that decide them; both loops are
-// bounded by the iteration caps held in the device state.
-static ba_status build_graph_mixed(ba_problem* p) {
+// One CUDA graph for a whole solve: init, then WHILE(lm) { lm_head; WHILE(pcg)
+// { pcg_iter }; lm_tail }, finish.  Loop flags are set on the device by the kernels
+// that decide them; both loops are bounded by the iteration caps in the device state.
+static ba_status build_graph_loops(ba_problem* p) {
     cudaStream_t s0 = p->cap[0], s1 = p->cap[1], s2 = p->cap[2];
-    const Views<float>& v = p->vf;
     cudaGraph_t top;
     GBBA_CUDA(cudaGraphCreate(&top, 0));
     cudaGraphConditionalHandle lm_h, pcg_h;
     GBBA_CUDA(cudaGraphConditionalHandleCreate(&lm_h, top, 0, cudaGraphCondAssignDefault));
     GBBA_CUDA(cudaStreamBeginCaptureToGraph(s0, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    launch_init_state(v.st, s0);
-    launch_camera_precompute(v, p->L, s0);
-    launch_linearize(v, p->L, s0, 0, nullptr, nullptr, (CondHandle)lm_h, 1);
+    step_init(p, s0, (CondHandle)lm_h, 1);
     cudaGraph_t lm_body;
     cudaError_t e = add_while_node(s0, (CondHandle)lm_h, &lm_body);
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&pcg_h, lm_body, 0, 0);
     if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(s1, lm_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        enqueue_lm_body_mixed(p, s1, (CondHandle)lm_h, (CondHandle)pcg_h, p->use_persistent ? 0 : 1, s2, false, 0);
-        if (!p->use_persistent) {
+        const bool inner = inner_pcg(p);
+        step_lm_head(p, s1, (CondHandle)pcg_h, inner ? 1 : 0, false, 0);
+        if (inner) {
             cudaGraph_t pcg_body;
             e = add_while_node(s1, (CondHandle)pcg_h, &pcg_body);
             if (e == cudaSuccess)
                 e = cudaStreamBeginCaptureToGraph(s2, pcg_body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
-                enqueue_pcg_iteration_mixed(p, s2, (CondHandle)pcg_h, 1);
+                step_pcg_iter(p, s2, (CondHandle)pcg_h, 1);
                 cudaGraph_t tmp;
                 e = cudaStreamEndCapture(s2, &tmp);
             }
         }
-        if (e == cudaSuccess) enqueue_lm_tail_mixed(p, s1, (CondHandle)lm_h, 1);
+        if (e == cudaSuccess) step_lm_tail(p, s1, (CondHandle)lm_h, 1);
         cudaGraph_t tmp1;
         cudaError_t e1 = cudaStreamEndCapture(s1, &tmp1);
         if (e == cudaSuccess) e = e1;
     }
-    if (e == cudaSuccess) launch_finish_state(v.st, s0);
+    if (e == cudaSuccess) launch_finish_state(dev_state(p), s0);
     cudaGraph_t tmp0;
     cudaError_t e0 = cudaStreamEndCapture(s0, &tmp0);
     if (e == cudaSuccess) e = e0;
@@ -268,16 +305,15 @@ static ba_status build_graph_mixed(ba_problem* p) {
     return BA_OK;
 }
 
-static void enqueue_solve_predicated_mixed(ba_problem* p, const ba_options& o, cudaStream_t s) {
-    const Views<float>& v = p->vf;
-    launch_init_state(v.st, s);
-    launch_camera_precompute(v, p->L, s);
-    launch_linearize(v, p->L, s, 0, nullptr, nullptr, 0, 0);
+// The fixed predicated sequence: max_lm_iters LM slots of max_pcg_iters PCG slots;
+// kernels of idle slots return at once.
+static void enqueue_solve_predicated(ba_problem* p, const ba_options& o, cudaStream_t s) {
+    step_init(p, s, 0, 0);
     for (int it = 0; it < o.max_lm_iters; ++it) {
-        enqueue_lm_body_mixed(p, s, 0, 0, 0, s, true, o.max_pcg_iters);
-        enqueue_lm_tail_mixed(p, s, 0, 0);
+        step_lm_head(p, s, 0, 0, true, o.max_pcg_iters);
+        step_lm_tail(p, s, 0, 0);
     }
-    launch_finish_state(v.st, s);
+    launch_finish_state(dev_state(p), s);
 }
 
 }  // namespace gbba
@@ -591,11 +627,8 @@ ba_status ba_set_params_device(ba_problem* p, const void* cams, const void* pts,
         set_error("ba_set_params_device: null pointer or bad dtype %d", dtype);
         return BA_ERR_INVALID_ARG;
     }
-    if (p->precision != BA_PREC_MIXED) {
-        set_error("ba_set_params_device: FP64 form not built yet");
-        return BA_ERR_NOT_IMPLEMENTED;
-    }
-    launch_pack(p->vf, p->L, p->stream, cams, pts, dtype);
+    if (p->precision == BA_PREC_MIXED) launch_pack(p->vf, p->L, p->stream, cams, pts, dtype);
+    else launch64_pack(p->vd, p->L, p->stream, cams, pts, dtype);
     GBBA_CUDA(cudaGetLastError());
     p->linearized = false;
     return BA_OK;
@@ -608,11 +641,8 @@ ba_status ba_get_params_device(ba_problem* p, void* cams, void* pts, int32_t dty
         set_error("ba_get_params_device: null pointer or bad dtype %d", dtype);
         return BA_ERR_INVALID_ARG;
     }
-    if (p->precision != BA_PREC_MIXED) {
-        set_error("ba_get_params_device: FP64 form not built yet");
-        return BA_ERR_NOT_IMPLEMENTED;
-    }
-    launch_unpack(p->vf, p->L, p->stream, p->vf.x, cams, pts, dtype);
+    if (p->precision == BA_PREC_MIXED) launch_unpack(p->vf, p->L, p->stream, p->vf.x, cams, pts, dtype);
+    else launch64_unpack(p->vd, p->L, p->stream, cams, pts, dtype);
     GBBA_CUDA(cudaGetLastError());
     return BA_OK;
 }
@@ -626,18 +656,19 @@ static ba_status read_state(ba_problem* p, DevState* host) {
 ba_status ba_evaluate(ba_problem* p, double* cost_out, void* residuals, void* jacobian) {
     ba_status st = check_bound(p, "ba_evaluate");
     if (st) return st;
-    if (p->precision != BA_PREC_MIXED) {
-        set_error("ba_evaluate: FP64 form not built yet");
-        return BA_ERR_NOT_IMPLEMENTED;
+    DevState* dst = dev_state(p);
+    if (p->precision == BA_PREC_MIXED) {
+        launch_camera_precompute(p->vf, p->L, p->stream);
+        launch_linearize(p->vf, p->L, p->stream, 2, (float*)residuals, (float*)jacobian, 0, 0);
+    } else {
+        launch64_camera_precompute(p->vd, p->L, p->stream);
+        launch64_linearize(p->vd, p->L, p->stream, 2, (double*)residuals, (double*)jacobian, 0, 0);
     }
-    const Views<float>& v = p->vf;
-    launch_camera_precompute(v, p->L, p->stream);
-    launch_linearize(v, p->L, p->stream, 2, (float*)residuals, (float*)jacobian, 0, 0);
     GBBA_CUDA(cudaGetLastError());
     p->linearized = true;
     if (cost_out) {
         double c = 0;
-        GBBA_CUDA(cudaMemcpyAsync(&c, &v.st->cost_out, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        GBBA_CUDA(cudaMemcpyAsync(&c, &dst->cost_out, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
         GBBA_CUDA(cudaStreamSynchronize(p->stream));
         *cost_out = c;
     }
@@ -706,10 +737,6 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
     ba_status st = check_bound(p, "ba_solve");
     if (st) return st;
     if ((st = check_options(o))) return st;
-    if (p->precision != BA_PREC_MIXED) {
-        set_error("ba_solve: FP64 form not built yet");
-        return BA_ERR_NOT_IMPLEMENTED;
-    }
     if ((st = write_options(p, o))) return st;
     const bool want_persistent = p->persistent && o->pcg_kernel == 0;
     if (want_persistent != p->use_persistent) {   // cached graphs were built for the other PCG form
@@ -728,7 +755,7 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
             p->graph_unrolled = GraphCache{};
             cudaStream_t cs = p->cap[0];
             GBBA_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
-            enqueue_solve_predicated_mixed(p, *o, cs);
+            enqueue_solve_predicated(p, *o, cs);
             cudaGraph_t g;
             GBBA_CUDA(cudaStreamEndCapture(cs, &g));
             cudaGraphExec_t ex;
@@ -744,10 +771,10 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
         }
         GBBA_CUDA(cudaGraphLaunch(p->graph_unrolled.exec, p->stream));
     } else if (graph_mode == 1) {
-        if (!p->graph.exec && (st = build_graph_mixed(p))) return st;
+        if (!p->graph.exec && (st = build_graph_loops(p))) return st;
         GBBA_CUDA(cudaGraphLaunch(p->graph.exec, p->stream));
     } else {
-        enqueue_solve_predicated_mixed(p, *o, p->stream);
+        enqueue_solve_predicated(p, *o, p->stream);
         GBBA_CUDA(cudaGetLastError());
     }
     p->linearized = true;
@@ -762,36 +789,47 @@ ba_status ba_apply_normal(ba_problem* p, double mu, const void* vin, void* out, 
         set_error("ba_apply_normal: null vector or negative mu");
         return BA_ERR_INVALID_ARG;
     }
-    if (p->precision != BA_PREC_MIXED) {
-        set_error("ba_apply_normal: FP64 form not built yet");
-        return BA_ERR_NOT_IMPLEMENTED;
-    }
     if (!p->linearized) {
         set_error("ba_apply_normal: call ba_evaluate first");
         return BA_ERR_STATE;
     }
-    const Views<float>& v = p->vf;
     cudaStream_t s = p->stream;
     // state: mu, an active LM iteration so the preconditioner kernel runs
-    DevState* dst = v.st;
+    DevState* dst = dev_state(p);
     GBBA_CUDA(cudaMemcpyAsync(&dst->mu, &mu, sizeof(double), cudaMemcpyHostToDevice, s));
     int32_t one = 1;
     GBBA_CUDA(cudaMemcpyAsync(&dst->lm_active, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    launch_precond(v, p->L, s, 0, 0, nullptr);
-    launch_set_direction(v, p->L, s, (const float*)vin);
-    launch_matvec(v, p->L, s, nullptr, v.p, 0);
-    launch_normal_out(v, p->L, s, (float*)out);
-    GBBA_CUDA(cudaGetLastError());
-    double acc[NSLOT * SLOT_STRIDE];
-    GBBA_CUDA(cudaMemcpyAsync(acc, dst->acc_mv, sizeof(acc), cudaMemcpyDeviceToHost, s));
-    GBBA_CUDA(cudaMemsetAsync(dst->acc_mv, 0, sizeof(acc), s));
-    GBBA_CUDA(cudaStreamSynchronize(s));
-    double jp2 = 0, pdp = 0;
-    for (int k = 0; k < NSLOT; ++k) {
-        jp2 += acc[k * SLOT_STRIDE];
-        pdp += acc[k * SLOT_STRIDE + 1];
+    if (p->precision == BA_PREC_MIXED) {
+        const Views<float>& v = p->vf;
+        launch_precond(v, p->L, s, 0, 0, nullptr);
+        launch_set_direction(v, p->L, s, (const float*)vin);
+        launch_matvec(v, p->L, s, nullptr, v.p, 0);
+        launch_normal_out(v, p->L, s, (float*)out);
+        GBBA_CUDA(cudaGetLastError());
+        double acc[NSLOT * SLOT_STRIDE];
+        GBBA_CUDA(cudaMemcpyAsync(acc, dst->acc_mv, sizeof(acc), cudaMemcpyDeviceToHost, s));
+        GBBA_CUDA(cudaMemsetAsync(dst->acc_mv, 0, sizeof(acc), s));
+        GBBA_CUDA(cudaStreamSynchronize(s));
+        double jp2 = 0, pdp = 0;
+        for (int k = 0; k < NSLOT; ++k) {
+            jp2 += acc[k * SLOT_STRIDE];
+            pdp += acc[k * SLOT_STRIDE + 1];
+        }
+        if (vAv) *vAv = jp2 + mu * pdp;
+    } else {
+        const Views<double>& v = p->vd;
+        launch64_precond(v, p->L, s, 0, 0);
+        launch64_set_vec(v, p->L, s, (const double*)vin, v.z);   // the given vector as zs
+        launch64_direction(v, p->L, s, v.z, 0, nullptr);          // p = v, q = mu D p
+        launch64_matvec(v, p->L, s, nullptr);                     // q += J^T J p
+        launch64_get_vec(v, p->L, s, v.q, (double*)out);
+        GBBA_CUDA(cudaGetLastError());
+        double jp2 = 0, pdp = 0;
+        GBBA_CUDA(cudaMemcpyAsync(&jp2, &dst->jp2, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GBBA_CUDA(cudaMemcpyAsync(&pdp, &dst->pDp, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GBBA_CUDA(cudaStreamSynchronize(s));
+        if (vAv) *vAv = jp2 + mu * pdp;
     }
-    if (vAv) *vAv = jp2 + mu * pdp;
     return BA_OK;
 }
 
@@ -802,16 +840,16 @@ ba_status ba_repeat_normal(ba_problem* p, int32_t launches) {
         set_error("ba_repeat_normal: negative count");
         return BA_ERR_INVALID_ARG;
     }
-    if (p->precision != BA_PREC_MIXED) {
-        set_error("ba_repeat_normal: FP64 form not built yet");
-        return BA_ERR_NOT_IMPLEMENTED;
-    }
     if (!p->linearized) {
         set_error("ba_repeat_normal: call ba_apply_normal first");
         return BA_ERR_STATE;
     }
-    for (int i = 0; i < launches; ++i) launch_matvec(p->vf, p->L, p->stream, nullptr, p->vf.p, 0);
-    GBBA_CUDA(cudaMemsetAsync(p->vf.st->acc_mv, 0, NSLOT * SLOT_STRIDE * sizeof(double), p->stream));
+    if (p->precision == BA_PREC_MIXED) {
+        for (int i = 0; i < launches; ++i) launch_matvec(p->vf, p->L, p->stream, nullptr, p->vf.p, 0);
+        GBBA_CUDA(cudaMemsetAsync(p->vf.st->acc_mv, 0, NSLOT * SLOT_STRIDE * sizeof(double), p->stream));
+    } else {
+        for (int i = 0; i < launches; ++i) launch64_matvec(p->vd, p->L, p->stream, nullptr);
+    }
     GBBA_CUDA(cudaGetLastError());
     return BA_OK;
 }

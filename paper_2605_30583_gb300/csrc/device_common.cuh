@@ -241,6 +241,76 @@ __device__ __forceinline__ Geo project_geo(const Cam& c, float X0, float X1, flo
     return g;
 }
 
+// Inverse of one camera block, one warp per camera: lane j < 18 holds column j of
+// the augmented matrix [A | I] (A = H + mu D, 9 x 9, SPD) and Gauss-Jordan elimination
+// without pivoting runs over the 9 pivots in FP64.  Lanes 9..17 end with the columns
+// of A^-1.  Returns false (in every lane) if a pivot is not positive.
+__device__ __forceinline__ bool warp_block_inverse9(double (&col)[9], int lane) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double piv = __shfl_sync(0xffffffffu, col[k], k);
+        ok = ok && (piv > 0.0) && isfinite(piv);
+        const double ip = rcp64(piv > 0.0 ? piv : 1.0);
+        const double rk = col[k] * ip;   // row k of the updated matrix, this lane's column
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double aik = __shfl_sync(0xffffffffu, col[i], k);
+            if (i != k) col[i] = fma(-aik, rk, col[i]);
+        }
+        col[k] = rk;
+    }
+    (void)lane;
+    return ok;
+}
+
+// Levenberg-Marquardt decision after a candidate evaluation (Sec. V, Madsen's
+// quality-based damping).  Fn = F(x + h), jh2 = |J h|^2, st->gh = g^T h.
+// L = -g^T h - 1/2 |J h|^2, rho = (F - Fn) / L; the step is accepted iff Fn is finite,
+// L > 0 and rho > 0; then mu <- mu max(1/3, 1 - (2 rho - 1)^3), nu <- 2, else
+// mu <- mu nu, nu <- 2 nu.  Records the iteration and sets the loop flags.  One thread.
+__device__ __forceinline__ void lm_decide(DevState* st, int active, double Fn, double jh2) {
+    if (!active) {
+        st->accepted = 0;
+        st->relin = 0;
+        return;
+    }
+    const double L = -st->gh - 0.5 * jh2;
+    const double rho = (L > 0.0) ? (st->F - Fn) / L : -1.0;
+    const bool acc = isfinite(Fn) && L > 0.0 && rho > 0.0;
+    const int itn = st->lm_iter;
+    if (itn < HIST_CAP) {
+        IterRec& h = st->hist[itn];
+        h.cost = st->F;
+        h.cost_new = Fn;
+        h.mu = st->mu;
+        h.rho = rho;
+        h.model_decrease = L;
+        h.pcg_iters = st->pcg_iter;
+        h.accepted = acc ? 1 : 0;
+        h.t_ns = global_ns() - st->t_start;
+    }
+    st->F_new = Fn;
+    st->rho = rho;
+    st->L = L;
+    st->jh2 = jh2;
+    st->lm_iter = itn + 1;
+    if (acc) {
+        const double t = 2.0 * rho - 1.0;
+        st->mu = st->mu * fmax(1.0 / 3.0, 1.0 - t * t * t);
+        st->nu = 2.0;
+        st->F = Fn;
+        st->n_accepted += 1;
+    } else {
+        st->mu = st->mu * st->nu;
+        st->nu = 2.0 * st->nu;
+    }
+    st->accepted = acc ? 1 : 0;
+    const bool more = st->lm_iter < st->opt.max_lm && st->mu <= st->opt.max_mu && st->F > 0.0 && st->status == 0;
+    st->lm_active = more ? 1 : 0;
+    st->relin = (acc && more) ? 1 : 0;
+}
+
 // 1/x to within 1 ulp (the hardware reciprocal approximation, denormals flushed).
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;

@@ -53,6 +53,24 @@ int occupancy_blocks_linearize();
 int occupancy_blocks_matvec();
 int occupancy_blocks_eval();
 
+// plain FP64 form (kernels_fp64.cu)
+void launch64_camera_precompute(const Views<double>& v, const LaunchCfg& L, cudaStream_t s);
+void launch64_linearize(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, int mode, double* r, double* J,
+                        CondHandle c, int use);
+void launch64_precond(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
+void launch64_direction(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const double* zs, int use_beta,
+                        const int32_t* gate);
+void launch64_matvec(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate);
+void launch64_update(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
+void launch64_candidate(const Views<double>& v, const LaunchCfg& L, cudaStream_t s);
+void launch64_eval_candidate(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
+void launch64_commit(const Views<double>& v, const LaunchCfg& L, cudaStream_t s);
+void launch64_pack(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const void* cams, const void* pts,
+                   int dtype);
+void launch64_unpack(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, void* cams, void* pts, int dtype);
+void launch64_set_vec(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const double* src, double* dst);
+void launch64_get_vec(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const double* src, double* dst);
+
 // ordering (order.cu).  All buffers are device memory inside the workspace.
 struct OrderBuffers {
     const uint32_t* cam_idx;   // [n_obs] uploaded

@@ -218,29 +218,6 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
 #define FOR_POINTS(i, v) \
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (v).n_pts; i += gridDim.x * blockDim.x)
 
-// Inverse of one camera block, one warp per camera: lane j < 18 holds column j of
-// the augmented matrix [A | I] (A = H + mu D, 9 x 9, SPD) and Gauss-Jordan elimination
-// without pivoting runs over the 9 pivots in FP64.  Lanes 9..17 end with the columns
-// of A^-1.  Returns false (in every lane) if a pivot is not positive.
-__device__ __forceinline__ bool warp_block_inverse9(double (&col)[9], int lane) {
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const double piv = __shfl_sync(0xffffffffu, col[k], k);
-        ok = ok && (piv > 0.0) && isfinite(piv);
-        const double ip = rcp64(piv > 0.0 ? piv : 1.0);
-        const double rk = col[k] * ip;   // row k of the updated matrix, this lane's column
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const double aik = __shfl_sync(0xffffffffu, col[i], k);
-            if (i != k) col[i] = fma(-aik, rk, col[i]);
-        }
-        col[k] = rk;
-    }
-    (void)lane;
-    return ok;
-}
-
 __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, double* pslots) {
     DevState* st = v.st;
     if (pslots != nullptr && blockIdx.x == 0) {   // state of the persistent PCG kernel
@@ -700,47 +677,7 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
     }
     double in[2] = {fnew, jh2}, out[2];
     if (grid_reduce<2>(in, v.partials, &st->tickets[TK_COST], out) && threadIdx.x == 0) {
-        if (active) {
-            const double Fn = 0.5 * out[0];
-            const double L = -st->gh - 0.5 * out[1];
-            const double rho = (L > 0.0) ? (st->F - Fn) / L : -1.0;
-            const bool acc = isfinite(Fn) && L > 0.0 && rho > 0.0;
-            const int itn = st->lm_iter;
-            if (itn < HIST_CAP) {
-                IterRec& h = st->hist[itn];
-                h.cost = st->F;
-                h.cost_new = Fn;
-                h.mu = st->mu;
-                h.rho = rho;
-                h.model_decrease = L;
-                h.pcg_iters = st->pcg_iter;
-                h.accepted = acc ? 1 : 0;
-                h.t_ns = global_ns() - st->t_start;
-            }
-            st->F_new = Fn;
-            st->rho = rho;
-            st->L = L;
-            st->jh2 = out[1];
-            st->lm_iter = itn + 1;
-            if (acc) {
-                const double t = 2.0 * rho - 1.0;
-                st->mu = st->mu * fmax(1.0 / 3.0, 1.0 - t * t * t);
-                st->nu = 2.0;
-                st->F = Fn;
-                st->n_accepted += 1;
-            } else {
-                st->mu = st->mu * st->nu;
-                st->nu = 2.0 * st->nu;
-            }
-            st->accepted = acc ? 1 : 0;
-            const bool more = st->lm_iter < st->opt.max_lm && st->mu <= st->opt.max_mu &&
-                              st->F > 0.0 && st->status == 0;
-            st->lm_active = more ? 1 : 0;
-            st->relin = (acc && more) ? 1 : 0;
-        } else {
-            st->accepted = 0;
-            st->relin = 0;
-        }
+        lm_decide(st, active, 0.5 * out[0], out[1]);
         if (use_cond) cudaGraphSetConditional(lm_cond, st->lm_active ? 1u : 0u);
     }
 }

@@ -98,6 +98,7 @@ struct Views {
     float* pc;        // camera part of the PCG direction, double-buffered [2][pc_stride]
     double* cam_lin;
     float* cam_H;
+    double *cam64, *cam64_new, *cam_H64;   // plain FP64 form: camera records and J_c^T J_c
     T* pt_H;          // [4 n_quads][6]
     T* Minv_c;        // [n_cams][81]
     T* Minv_p;        // [4 n_quads][6]
