@@ -196,6 +196,32 @@ ba_status ba_cost_forward(ba_problem* problem, const void* cams, const void* pts
 ba_status ba_cost_backward(ba_problem* problem, const void* cams, const void* pts, int32_t dtype,
                            const double* grad_out_dev, void* grad_cams, void* grad_pts);
 
+/* Allocation-free cost, for callers that cannot allocate device memory: code that
+ * runs while a stream is being captured into a CUDA graph, hosts whose device memory
+ * belongs entirely to another allocator, or real-time loops in which allocation is
+ * forbidden.  (The paper has no counterpart; this is a library service.)
+ *
+ * Computes F = 1/2 sum_o |r_o|^2 with the arithmetic of ba_evaluate for
+ * BA_PREC_MIXED (FP32 residuals, FP64 sum) from caller-provided device arrays in user
+ * layout: cams float[n_cams][9], pts float[n_pts][3], cam_idx / pt_idx uint32[n_obs],
+ * pixels float[n_obs][2].  The result goes to *cost_dev (device double).  Enqueued on
+ * `stream` (cudaStream_t); no synchronisation, no cudaMalloc, no cudaFree and no
+ * allocating library call.
+ *
+ * Scratch (camera records and per-block partial sums, about 1.1 MiB) is a fixed array
+ * inside the library: every GPU that loads the library holds it until the process
+ * exits.  Limits: n_cams <= BA_NOALLOC_MAX_CAMS and n_obs <= BA_NOALLOC_MAX_BLOCKS *
+ * 1024; larger sizes are rejected with BA_ERR_INVALID_ARG before any GPU work.  The
+ * first call on each device looks up the array's device address once (with that
+ * device current); make that first call before any stream capture.  All calls share
+ * the one array, so calls whose GPU work overlaps (other streams, other host threads
+ * on the same device) race and must be serialised by the caller. */
+#define BA_NOALLOC_MAX_CAMS 16384
+#define BA_NOALLOC_MAX_BLOCKS 16384
+ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_pts, int64_t n_obs, const float* cams, const float* pts,
+                          const uint32_t* cam_idx, const uint32_t* pt_idx, const float* pixels, double eps_depth,
+                          double* cost_dev, void* stream);
+
 /* Batched mode: many independent small problems solved by one persistent kernel.
  * Offsets are host prefix arrays of length n_problems + 1 into the concatenated
  * camera, point and observation arrays; cam_idx / pt_idx are LOCAL to each

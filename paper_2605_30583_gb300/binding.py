@@ -71,6 +71,7 @@ SIGNATURES = {
     "ba_profile_kernels": (I32, [P, I32, P, I32]),
     "ba_cost_forward": (I32, [P, P, P, I32, P]),
     "ba_cost_backward": (I32, [P, P, P, I32, P, P, P]),
+    "ba_cost_noalloc": (I32, [I32, I32, I64, P, P, P, P, P, ctypes.c_double, P, P]),
     "ba_batch_create": (I32, [I32, P, P, P, P, P, P, ctypes.POINTER(P)]),
     "ba_batch_destroy": (None, [P]),
     "ba_batch_workspace_size": (I32, [P, ctypes.POINTER(SZ)]),
