@@ -185,12 +185,16 @@ ba_status ba_repeat_normal(ba_problem* problem, int32_t launches);
  * (the next ba_solve starts afresh).  Synchronises. */
 ba_status ba_profile_kernels(ba_problem* problem, int32_t reps, double* us_out, int32_t n);
 
-/* Total reprojection cost F = 1/2 sum |r|^2 (FP64) at caller parameters, and its
- * adjoint.  cams/pts are device arrays in user layout of dtype (0 float32,
- * 1 float64).  Forward writes F to *cost_dev (device double).  Backward writes
- * grad_cams = grad_out * J_c^T r and grad_pts = grad_out * J_p^T r (device, same
- * dtype, user layout), where grad_out is a device double.  Neither call
- * synchronises.  Used by the torch.autograd.Function of the Python binding. */
+/* Total reprojection cost F = 1/2 sum |r|^2 (FP64 sum; residuals in the problem's
+ * precision) at caller parameters, and its adjoint (Sec. V: the Jacobian of the
+ * factor with respect to its tunable nodes).  cams/pts are device arrays in user
+ * layout of dtype (0 float32, 1 float64).  Forward writes F to *cost_dev (device
+ * double).  Backward recomputes the residuals and writes grad_cams = grad_out *
+ * J_c^T r and grad_pts = grad_out * J_p^T r (device, same dtype, user layout), where
+ * grad_out is a device double.  The problem's own parameters are not changed; the
+ * backward reuses the linearisation buffers, so ba_apply_normal needs a new
+ * ba_evaluate afterwards.  Neither call synchronises.  These back the
+ * torch.autograd.Function of the Python binding. */
 ba_status ba_cost_forward(ba_problem* problem, const void* cams, const void* pts, int32_t dtype,
                           double* cost_dev);
 ba_status ba_cost_backward(ba_problem* problem, const void* cams, const void* pts, int32_t dtype,

@@ -927,14 +927,40 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
 
 // ---- not yet available in this build --------------------------------------------
 
-ba_status ba_cost_forward(ba_problem*, const void*, const void*, int32_t, double*) {
-    set_error("ba_cost_forward: not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
+ba_status ba_cost_forward(ba_problem* p, const void* cams, const void* pts, int32_t dtype, double* cost_dev) {
+    ba_status st = check_bound(p, "ba_cost_forward");
+    if (st) return st;
+    if (!cams || !pts || !cost_dev || (dtype != 0 && dtype != 1)) {
+        set_error("ba_cost_forward: null pointer or bad dtype %d", dtype);
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->precision == BA_PREC_MIXED) launch_cost_grad(p->vf, p->L, p->stream, cams, pts, dtype, 0, cost_dev);
+    else launch64_cost_grad(p->vd, p->L, p->stream, cams, pts, dtype, 0, cost_dev);
+    GBBA_CUDA(cudaGetLastError());
+    p->linearized = false;   // the camera gradient buffer was cleared as scratch
+    return BA_OK;
 }
-ba_status ba_cost_backward(ba_problem*, const void*, const void*, int32_t, const double*, void*, void*) {
-    set_error("ba_cost_backward: not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
+
+ba_status ba_cost_backward(ba_problem* p, const void* cams, const void* pts, int32_t dtype, const double* grad_out,
+                           void* grad_cams, void* grad_pts) {
+    ba_status st = check_bound(p, "ba_cost_backward");
+    if (st) return st;
+    if (!cams || !pts || !grad_out || !grad_cams || !grad_pts || (dtype != 0 && dtype != 1)) {
+        set_error("ba_cost_backward: null pointer or bad dtype %d", dtype);
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->precision == BA_PREC_MIXED) {
+        launch_cost_grad(p->vf, p->L, p->stream, cams, pts, dtype, 1, nullptr);
+        launch_grad_out(p->vf, p->L, p->stream, grad_out, grad_cams, grad_pts, dtype);
+    } else {
+        launch64_cost_grad(p->vd, p->L, p->stream, cams, pts, dtype, 1, nullptr);
+        launch64_grad_out(p->vd, p->L, p->stream, grad_out, grad_cams, grad_pts, dtype);
+    }
+    GBBA_CUDA(cudaGetLastError());
+    p->linearized = false;   // the gradient buffers of the linearisation were used as scratch
+    return BA_OK;
 }
+
 ba_status ba_batch_create(int32_t, const int32_t*, const int32_t*, const int64_t*, const uint32_t*,
                           const uint32_t*, const double*, ba_batch** out) {
     if (out) *out = nullptr;

@@ -71,6 +71,17 @@ void launch64_unpack(const Views<double>& v, const LaunchCfg& L, cudaStream_t s,
 void launch64_set_vec(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const double* src, double* dst);
 void launch64_get_vec(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const double* src, double* dst);
 
+// autograd (cost and its adjoint at caller parameters; x' and the candidate camera
+// records serve as scratch, the problem's parameters are left untouched)
+void launch_cost_grad(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const void* cams, const void* pts,
+                      int dtype, int want_grad, double* cost_dev);
+void launch_grad_out(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const double* grad_out, void* gc,
+                     void* gp, int dtype);
+void launch64_cost_grad(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const void* cams, const void* pts,
+                        int dtype, int want_grad, double* cost_dev);
+void launch64_grad_out(const Views<double>& v, const LaunchCfg& L, cudaStream_t s, const double* grad_out, void* gc,
+                       void* gp, int dtype);
+
 // ordering (order.cu).  All buffers are device memory inside the workspace.
 struct OrderBuffers {
     const uint32_t* cam_idx;   // [n_obs] uploaded

@@ -472,6 +472,64 @@ __global__ void k64_get_vec(V64 v, const double* src, double* dst) {
     }
 }
 
+// ------------------------------------------------------------- autograd ------
+template <typename S>
+__global__ void k64_pack_to(V64 v, const S* cams, const S* pts, double* dst) {
+    for (int c = gtid(); c < v.n_cams; c += grid_threads())
+        for (int k = 0; k < 9; ++k) dst[9 * (size_t)c + k] = (double)cams[9 * (size_t)c + k];
+    for (int u = gtid(); u < v.n_pts; u += grid_threads()) {
+        const size_t e = v.pt_off + 3 * (size_t)v.pt_internal[u];
+        for (int k = 0; k < 3; ++k) dst[e + k] = (double)pts[3 * (size_t)u + k];
+    }
+}
+
+__global__ void k64_records_from(V64 v, const double* src, double* dst) {
+    for (int c = gtid(); c < v.n_cams; c += grid_threads()) {
+        camera_record64(src + 9 * (size_t)c, dst + (size_t)c * CP_STRIDE);
+        for (int k = 0; k < CL_STRIDE; ++k) v.cam_lin[(size_t)c * CL_STRIDE + k] = 0.0;
+    }
+}
+
+// F = 1/2 |r|^2 and, if want_grad, J^T r (cameras by FP64 atomics, points in registers).
+__global__ void k64_cost_grad(V64 v, const double* xs, const double* crec, int want_grad, double* cost_dev) {
+    const double eps = v.st->opt.eps;
+    double cost = 0.0;
+    for (int ip = gtid(); ip < v.n_pts; ip += grid_threads()) {
+        const double* X = xs + v.pt_off + 3 * (size_t)ip;
+        double gp[3] = {0, 0, 0};
+        for (uint32_t k = v.pt_obs_off[ip]; k < v.pt_obs_off[ip + 1]; ++k) {
+            const uint32_t j = v.obs_pm[k];
+            const uint32_t c = v.obs_key[j] >> 8;
+            double J[24], r0, r1;
+            obs_jacobian64(crec + (size_t)c * CP_STRIDE, X[0], X[1], X[2], eps, v.obs_uv[2 * (size_t)j],
+                           v.obs_uv[2 * (size_t)j + 1], r0, r1, want_grad ? J : nullptr);
+            cost += r0 * r0 + r1 * r1;
+            if (want_grad) {
+                for (int a = 0; a < 9; ++a) atomicAdd(v.cam_lin + (size_t)c * CL_STRIDE + a, J[a] * r0 + J[12 + a] * r1);
+                for (int a = 0; a < 3; ++a) gp[a] += J[9 + a] * r0 + J[21 + a] * r1;
+            }
+        }
+        if (want_grad)
+            for (int a = 0; a < 3; ++a) v.g[v.pt_off + 3 * (size_t)ip + a] = gp[a];
+    }
+    double in[1] = {cost}, out[1];
+    if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_MISC], out) && threadIdx.x == 0) {
+        v.st->cost_out = 0.5 * out[0];
+        if (cost_dev) *cost_dev = 0.5 * out[0];
+    }
+}
+
+template <typename S>
+__global__ void k64_grad_out(V64 v, const double* grad_out, S* gc, S* gp) {
+    const double s = *grad_out;
+    for (int c = gtid(); c < v.n_cams; c += grid_threads())
+        for (int k = 0; k < 9; ++k) gc[9 * (size_t)c + k] = (S)(s * v.cam_lin[(size_t)c * CL_STRIDE + k]);
+    for (int u = gtid(); u < v.n_pts; u += grid_threads()) {
+        const size_t e = v.pt_off + 3 * (size_t)v.pt_internal[u];
+        for (int k = 0; k < 3; ++k) gp[3 * (size_t)u + k] = (S)(s * v.g[e + k]);
+    }
+}
+
 // ------------------------------------------------------------------ launchers --
 
 namespace {
@@ -522,6 +580,20 @@ void launch64_unpack(const V64& v, const LaunchCfg& L, cudaStream_t s, void* cam
 }
 void launch64_set_vec(const V64& v, const LaunchCfg& L, cudaStream_t s, const double* src, double* dst) {
     k64_set_vec<<<g64(L, std::max(v.n_cams, v.n_pts)), L.item_block, 0, s>>>(v, src, dst);
+}
+void launch64_cost_grad(const V64& v, const LaunchCfg& L, cudaStream_t s, const void* cams, const void* pts, int dtype,
+                        int want_grad, double* cost_dev) {
+    const int g = g64(L, std::max(v.n_cams, v.n_pts));
+    if (dtype == 1) k64_pack_to<double><<<g, L.item_block, 0, s>>>(v, (const double*)cams, (const double*)pts, v.x_new);
+    else k64_pack_to<float><<<g, L.item_block, 0, s>>>(v, (const float*)cams, (const float*)pts, v.x_new);
+    k64_records_from<<<g64(L, v.n_cams), L.item_block, 0, s>>>(v, v.x_new, v.cam64_new);
+    k64_cost_grad<<<g64(L, v.n_pts), L.item_block, 0, s>>>(v, v.x_new, v.cam64_new, want_grad, cost_dev);
+}
+void launch64_grad_out(const V64& v, const LaunchCfg& L, cudaStream_t s, const double* grad_out, void* gc, void* gp,
+                       int dtype) {
+    const int g = g64(L, std::max(v.n_cams, v.n_pts));
+    if (dtype == 1) k64_grad_out<double><<<g, L.item_block, 0, s>>>(v, grad_out, (double*)gc, (double*)gp);
+    else k64_grad_out<float><<<g, L.item_block, 0, s>>>(v, grad_out, (float*)gc, (float*)gp);
 }
 void launch64_get_vec(const V64& v, const LaunchCfg& L, cudaStream_t s, const double* src, double* dst) {
     k64_get_vec<<<g64(L, std::max(v.n_cams, v.n_pts)), L.item_block, 0, s>>>(v, src, dst);

@@ -875,3 +875,174 @@ int occupancy_blocks_eval() {
 }
 
 }  // namespace gbba
+
+// ------------------------------------------------------------- autograd ------
+namespace gbba {
+
+// Parameters in caller layout -> internal layout at `dst` (x' is used as scratch so
+// the problem's own parameters stay untouched).
+template <typename S>
+__global__ void k_pack_to(Views<float> v, const S* cams, const S* pts, float* dst) {
+    const int items = v.n_cams + v.n_pts;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+        if (it < v.n_cams) {
+            for (int k = 0; k < 9; ++k) dst[9 * (size_t)it + k] = (float)cams[9 * (size_t)it + k];
+        } else {
+            const int u = it - v.n_cams;
+            const size_t e = v.pt_off + 3 * (size_t)v.pt_internal[u];
+            for (int k = 0; k < 3; ++k) dst[e + k] = (float)pts[3 * (size_t)u + k];
+        }
+    }
+}
+
+__global__ void k_camera_records_from(Views<float> v, const float* src, float* dst) {
+    FOR_CAMERAS(c, v) {
+        double p[9];
+        for (int k = 0; k < 9; ++k) p[k] = (double)src[9 * (size_t)c + k];
+        camera_record(p, dst + (size_t)c * CP_STRIDE);
+        for (int k = 0; k < CL_STRIDE; ++k) v.cam_lin[(size_t)c * CL_STRIDE + k] = 0.0;
+    }
+}
+
+// Cost F = 1/2 |r|^2 at (xs, camera records crec) and, if want_grad, its adjoint
+// J^T r: camera part into cam_lin (FP64 atomics once per camera run), point part into
+// g (internal layout).  Camera pass over the tile's camera-sorted observations, point
+// pass per point over its observations (which also sums the cost).
+template <int TB>
+__global__ void __launch_bounds__(TB) k_cost_grad(Views<float> v, const float* __restrict__ xs,
+                                                  const float* __restrict__ crec, int want_grad, double* cost_dev) {
+    __shared__ float4 sx[TILE_PTS];
+    const float eps = (float)v.st->opt.eps;
+    float cost = 0.0f;
+    for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
+        const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
+        const int pt0 = tile * TILE_PTS;
+        const int npt = min(TILE_PTS, v.n_pts - pt0);
+        const size_t base = v.pt_off + 3 * (size_t)pt0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < npt; i += TB)
+            sx[i] = make_float4(xs[base + 3 * i], xs[base + 3 * i + 1], xs[base + 3 * i + 2], 0.0f);
+        __syncthreads();
+        if (want_grad) {
+            const uint32_t n = hi - lo;
+            const uint32_t chunk = (n + TB - 1) / TB;
+            const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
+            uint32_t cur = NO_CAM;
+            float acc[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+            Cam cam;
+            float JL[9];
+            for (uint32_t j = a; j < b; ++j) {
+                const uint32_t key = __ldg(v.obs_key + j);
+                const uint32_t c = key >> 8, slot = key & 0xffu;
+                if (c != cur) {
+                    if (cur != NO_CAM) {
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) {
+                            atomicAdd(v.cam_lin + (size_t)cur * CL_STRIDE + k, (double)acc[k]);
+                            acc[k] = 0.0f;
+                        }
+                    }
+                    cur = c;
+                    cam = load_cam(crec + (size_t)c * CP_STRIDE);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) JL[k] = __ldg(crec + (size_t)c * CP_STRIDE + CP_JL + k);
+                }
+                const float4 X = sx[slot];
+                const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
+                const float fs = cam.f * g.s;
+                const float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
+                const float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
+                // J_c^T r: rotation part J_l^T (RX x u) with u = A^T r, then u, then intrinsics
+                const float u0 = fmaf(g.A[0], r0, g.A[3] * r1);
+                const float u1 = fmaf(g.A[1], r0, g.A[4] * r1);
+                const float u2 = fmaf(g.A[2], r0, g.A[5] * r1);
+                const float w0 = fmaf(g.RX[1], u2, -g.RX[2] * u1);
+                const float w1 = fmaf(g.RX[2], u0, -g.RX[0] * u2);
+                const float w2 = fmaf(g.RX[0], u1, -g.RX[1] * u0);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) acc[k] = fmaf(JL[k], w0, fmaf(JL[3 + k], w1, fmaf(JL[6 + k], w2, acc[k])));
+                acc[3] += u0;
+                acc[4] += u1;
+                acc[5] += u2;
+                const float pr = fmaf(g.p[0], r0, g.p[1] * r1);
+                const float fn2 = cam.f * g.n2;
+                acc[6] = fmaf(g.s, pr, acc[6]);
+                acc[7] = fmaf(fn2, pr, acc[7]);
+                acc[8] = fmaf(fn2 * g.n2, pr, acc[8]);
+            }
+            const bool head = seg_reduce<9>(cur, acc);
+            if (head && cur != NO_CAM) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) atomicAdd(v.cam_lin + (size_t)cur * CL_STRIDE + k, (double)acc[k]);
+            }
+        }
+        for (int i = threadIdx.x; i < npt; i += TB) {
+            const int ip = pt0 + i;
+            const float4 X = sx[i];
+            float gp0 = 0.0f, gp1 = 0.0f, gp2 = 0.0f;
+            const uint32_t k0 = __ldg(v.pt_obs_off + ip), k1 = __ldg(v.pt_obs_off + ip + 1);
+            for (uint32_t k = k0; k < k1; ++k) {
+                const uint32_t j = __ldg(v.obs_pm + k);
+                const uint32_t c = __ldg(v.obs_key + j) >> 8;
+                const Cam cam = load_cam(crec + (size_t)c * CP_STRIDE);
+                const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
+                const float fs = cam.f * g.s;
+                const float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
+                const float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
+                cost = fmaf(r0, r0, fmaf(r1, r1, cost));
+                if (want_grad) {   // J_X^T r = R^T A^T r
+                    const float u0 = fmaf(g.A[0], r0, g.A[3] * r1);
+                    const float u1 = fmaf(g.A[1], r0, g.A[4] * r1);
+                    const float u2 = fmaf(g.A[2], r0, g.A[5] * r1);
+                    gp0 += fmaf(cam.R[0], u0, fmaf(cam.R[3], u1, cam.R[6] * u2));
+                    gp1 += fmaf(cam.R[1], u0, fmaf(cam.R[4], u1, cam.R[7] * u2));
+                    gp2 += fmaf(cam.R[2], u0, fmaf(cam.R[5], u1, cam.R[8] * u2));
+                }
+            }
+            if (want_grad) {
+                v.g[base + 3 * i] = gp0;
+                v.g[base + 3 * i + 1] = gp1;
+                v.g[base + 3 * i + 2] = gp2;
+            }
+        }
+    }
+    double in[1] = {(double)cost}, out[1];
+    if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_MISC], out) && threadIdx.x == 0) {
+        v.st->cost_out = 0.5 * out[0];
+        if (cost_dev) *cost_dev = 0.5 * out[0];
+    }
+}
+
+// grad_cams = grad_out * g_c, grad_pts = grad_out * g_p, caller layout.
+template <typename S>
+__global__ void k_grad_out(Views<float> v, const double* __restrict__ grad_out, S* gc, S* gp) {
+    const double s = *grad_out;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.n_cams; c += gridDim.x * blockDim.x)
+        for (int k = 0; k < 9; ++k) gc[9 * (size_t)c + k] = (S)(s * v.cam_lin[(size_t)c * CL_STRIDE + k]);
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < v.n_pts; u += gridDim.x * blockDim.x) {
+        const size_t e = v.pt_off + 3 * (size_t)v.pt_internal[u];
+        for (int k = 0; k < 3; ++k) gp[3 * (size_t)u + k] = (S)(s * (double)v.g[e + k]);
+    }
+}
+
+void launch_cost_grad(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const void* cams, const void* pts,
+                      int dtype, int want_grad, double* cost_dev) {
+    const int gi = std::max(1, std::min((v.n_cams + v.n_pts + 255) / 256, L.item_grid));
+    if (dtype == 1) k_pack_to<double><<<gi, 256, 0, s>>>(v, (const double*)cams, (const double*)pts, v.x_new);
+    else k_pack_to<float><<<gi, 256, 0, s>>>(v, (const float*)cams, (const float*)pts, v.x_new);
+    k_camera_records_from<<<std::max(1, std::min((v.n_cams + 255) / 256, L.item_grid)), 256, 0, s>>>(v, v.x_new,
+                                                                                                     v.cam_pre_new);
+    const int gt = std::max(1, std::min(v.n_tiles, L.lin_grid));
+    k_cost_grad<LIN_TB><<<gt, LIN_TB, 0, s>>>(v, v.x_new, v.cam_pre_new, want_grad, cost_dev);
+}
+
+void launch_grad_out(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const double* grad_out, void* gc,
+                     void* gp, int dtype) {
+    const int g = std::max(1, std::min((std::max(v.n_cams, v.n_pts) + 255) / 256, L.item_grid));
+    if (dtype == 1) k_grad_out<double><<<g, 256, 0, s>>>(v, grad_out, (double*)gc, (double*)gp);
+    else k_grad_out<float><<<g, 256, 0, s>>>(v, grad_out, (float*)gc, (float*)gp);
+}
+
+}  // namespace gbba
