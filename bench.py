@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1, 2],
                     help="1: conditional-loop graph; 2: unrolled predicated graph; 0: host-enqueued sequence")
     return ap.parse_args()
@@ -355,6 +356,8 @@ def run_ours(args, rank, world, local_rank):
         except binding.BAError as e:
             fp64 = {"unavailable": str(e)}
 
+    batched = None if args.no_batch else run_batched(args, binding, synth, torch, dev, stream, flush)
+
     launches_per_step = 1 + 3 + 5 * last.lm_iters + 3 * last.pcg_iters_total + 1
     ttc = time_to_cost(last.history, target * (1 + 1e-4) if target else None)
     out = {
@@ -368,12 +371,81 @@ def run_ours(args, rank, world, local_rank):
         "time_to_cost_ms": ttc, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
         "step_ms": step_ms,
         "roofline": roofline, "roofline_other": other,
-        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "batched": batched, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def run_batched(args, binding, synth, torch, dev, stream, flush):
+    """The uneven-size batch: 512 problems (cameras U[5,60], points U[200,5000],
+    2+Poisson(3) views) solved by one persistent launch under a captured graph, after
+    the autotuner picked the schedule; beside it the same problems solved one by one
+    with the single-problem solver."""
+    probs = synth.make_batch(512)
+    opts = binding.default_options(use_graph=1)
+    b = binding.Batch(probs)
+    cams0 = np.concatenate([q.cams_init for q in probs])
+    pts0 = np.concatenate([q.pts_init for q in probs])
+    b.set_params(cams0, pts0)
+    trials = b.autotune(opts)
+    sched = b.schedule()
+    b.set_params(cams0, pts0)
+    b.solve(opts, wait=False)                      # graph capture + warm-up
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(max(1, min(3, args.steps))):
+        b.set_params(cams0, pts0)
+        flush.fill_(4)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.solve(opts, wait=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    # per-problem statistics of one more solve
+    b.set_params(cams0, pts0)
+    res = b.solve(opts)
+    pcg = sum(r.pcg_iters_total for r in res)
+    lm = sum(r.lm_iters for r in res)
+    # the same problems one at a time with the single-problem solver (graph mode)
+    singles = []
+    for q in probs:
+        sp = binding.Problem(q.n_cams, q.n_pts, q.cam_idx, q.pt_idx, q.pixels)
+        singles.append(sp)
+    for sp, q in zip(singles, probs):
+        sp.set_params(q.cams_init, q.pts_init)
+        sp.solve(opts, wait=False)
+    torch.cuda.synchronize()
+    for sp, q in zip(singles, probs):
+        sp.set_params(q.cams_init, q.pts_init)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for sp in singles:
+        sp.solve(opts, wait=False)
+    e1.record(stream)
+    e1.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    seq_fin = np.array([sp.stats().final_cost for sp in singles])
+    for sp in singles:
+        sp.close()
+    fin = np.array([r.final_cost for r in res])
+    t = sum(ms) / len(ms)
+    out = {"workload": f"512 problems, {sum(q.n_cams for q in probs)} cameras, {sum(q.n_pts for q in probs)} points, "
+                       f"{sum(q.n_obs for q in probs)} observations, 20 LM x <=50 PCG each",
+           "ms_per_batch_solve": t, "step_ms": ms, "problems_per_s": 512 / (t / 1e3),
+           "pcg_iters_per_s": pcg / (t / 1e3), "pcg_iters": pcg, "lm_iters": lm,
+           "schedule": sched, "autotune_trials": trials,
+           "sequential_single_solver_ms": seq_ms,
+           "final_cost_max_rel_diff_vs_single_solver": float(np.max(np.abs(fin - seq_fin) / seq_fin)),
+           "status_nonzero": int(sum(r.status != 0 for r in res))}
+    b.close()
+    return out
 
 
 def main():

@@ -226,11 +226,60 @@ ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_pts, int64_t n_obs, const fl
                           const uint32_t* cam_idx, const uint32_t* pt_idx, const float* pixels, double eps_depth,
                           double* cost_dev, void* stream);
 
-/* Batched mode: many independent small problems solved by one persistent kernel.
- * Offsets are host prefix arrays of length n_problems + 1 into the concatenated
- * camera, point and observation arrays; cam_idx / pt_idx are LOCAL to each
- * problem.  Problems must each satisfy the ba_problem_create requirements. */
+/* ---- Batched mode ---------------------------------------------------------------
+ * Many independent small problems (the uneven-size batch of the paper's evaluation,
+ * Sec. VI) solved together by ONE persistent kernel: each CTA takes whole problems
+ * from a device work queue, largest first, and runs the complete LM + PCGNR of Sec. V
+ * for that problem with block-level synchronisation only.  Arithmetic as in
+ * BA_PRECISION_MIXED (FP32 bulk, FP64 reductions and block inversions).  No CTA waits
+ * on another, so the kernel has no inter-block spin-waits.
+ *
+ * ba_batch_create: host arrays, copied; the caller keeps ownership.
+ *   cam_off, pt_off: int32 prefix offsets [n_problems + 1] into the concatenated
+ *   camera and point arrays; obs_off: int64 prefix offsets into the observations.
+ *   cam_idx / pt_idx [obs_off[n_problems]] are LOCAL to each problem (camera index <
+ *   its camera count, point index < its point count); pixels [n_obs][2] FP64.
+ *   Limits per problem: 1..BA_BATCH_MAX_CAMS cameras, 1..BA_BATCH_MAX_PTS points,
+ *   every point observed at least twice; otherwise BA_ERR_INVALID_ARG.
+ * ba_batch_workspace_size / ba_batch_bind_workspace: one device arena (256-byte
+ *   aligned) and a borrowed stream, as for ba_problem.  Binding sorts the observations
+ *   on the device (problem, camera, point) and builds the point-major index; it fails
+ *   with BA_ERR_INVALID_ARG if the largest problem's shared-memory tables (376 bytes
+ *   per camera + 12 bytes per point) do not fit one CTA.  Binding selects the default
+ *   schedule (256 threads, occupancy-limited CTAs per SM).
+ * ba_batch_set_params / ba_batch_get_params: host FP64, cameras [total_cams][9] and
+ *   points [total_pts][3] in the concatenated order of ba_batch_create.  Synchronous.
+ * ba_batch_solve: solves every problem with the same options (use_graph != 0: the
+ *   work-queue reset and the persistent launch run as one captured CUDA graph, rebuilt
+ *   when options or schedule change; pcg_kernel is ignored).  stats_per_problem NULL =
+ *   asynchronous on the bound stream; otherwise an array of n_problems entries that is
+ *   filled after a synchronisation (solve_ns = 0, no per-iteration history).
+ * ba_batch_get_costs: initial and final cost of every problem of the last solve
+ *   (either pointer may be NULL).  Synchronous.
+ * ba_batch_set_schedule: threads per CTA (128, 256 or 512), resident CTAs per SM
+ *   (0 = as many as occupancy allows; larger values are capped there) and flags:
+ *   BA_SCHED_STAGE_POINTS keeps the points' parameters and search directions in
+ *   shared memory during PCG (256 or 512 threads; needs 376 bytes per camera + 36 bytes
+ *   per point of the largest problem per CTA, else BA_ERR_INVALID_ARG).
+ * ba_batch_get_schedule: the current schedule and the resulting grid size.  Binding
+ *   selects 512 threads with staged points when they fit, else 256 threads.
+ * ba_batch_autotune: times one full solve per candidate schedule (every compiled block
+ *   size at each CTAs-per-SM count its occupancy allows, with and without staged points)
+ *   from the current parameters, restores the parameters,
+ *   and keeps the fastest schedule.  Choices are cached for the life of the process,
+ *   keyed by the GPU's name, the batch shape and the iteration options; a cached key
+ *   applies its schedule without timing unless flags has BA_TUNE_IGNORE_CACHE.
+ *   trials (capacity trial_cap, may be NULL when trial_cap = 0) receives the timings;
+ *   *n_trials the number written (0 on a cache hit).  Synchronous. */
+#define BA_BATCH_MAX_CAMS 1024
+#define BA_BATCH_MAX_PTS 16384
+#define BA_TUNE_IGNORE_CACHE 1
+#define BA_SCHED_STAGE_POINTS 1
 typedef struct ba_batch ba_batch;
+typedef struct ba_batch_trial {
+    int32_t threads, ctas_per_sm, flags, grid;
+    float ms;
+} ba_batch_trial;
 ba_status ba_batch_create(int32_t n_problems, const int32_t* cam_off, const int32_t* pt_off,
                           const int64_t* obs_off, const uint32_t* cam_idx, const uint32_t* pt_idx,
                           const double* pixels, ba_batch** out);
@@ -239,9 +288,13 @@ ba_status ba_batch_workspace_size(const ba_batch* batch, size_t* bytes);
 ba_status ba_batch_bind_workspace(ba_batch* batch, void* workspace, size_t bytes, void* stream);
 ba_status ba_batch_set_params(ba_batch* batch, const double* cams, const double* pts);
 ba_status ba_batch_get_params(ba_batch* batch, double* cams, double* pts);
-/* Solves every problem with the same options; NULL stats = asynchronous. */
 ba_status ba_batch_solve(ba_batch* batch, const ba_options* opts, ba_stats* stats_per_problem);
 ba_status ba_batch_get_costs(ba_batch* batch, double* initial_costs, double* final_costs);
+ba_status ba_batch_set_schedule(ba_batch* batch, int32_t threads, int32_t ctas_per_sm, int32_t flags);
+ba_status ba_batch_get_schedule(const ba_batch* batch, int32_t* threads, int32_t* ctas_per_sm, int32_t* flags,
+                                int32_t* grid);
+ba_status ba_batch_autotune(ba_batch* batch, const ba_options* opts, int32_t flags, ba_batch_trial* trials,
+                            int32_t trial_cap, int32_t* n_trials);
 
 #ifdef __cplusplus
 }

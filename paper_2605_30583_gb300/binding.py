@@ -46,6 +46,14 @@ class Stats(ctypes.Structure):
                 ("solve_ns", ctypes.c_int64)]
 
 
+class BatchTrial(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+
+BA_TUNE_IGNORE_CACHE = 1
+BA_SCHED_STAGE_POINTS = 1
+
 P = ctypes.c_void_p
 I32, I64, U32P, DP, SZ = ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p, ctypes.c_size_t
 
@@ -80,6 +88,11 @@ SIGNATURES = {
     "ba_batch_get_params": (I32, [P, P, P]),
     "ba_batch_solve": (I32, [P, ctypes.POINTER(Options), ctypes.POINTER(Stats)]),
     "ba_batch_get_costs": (I32, [P, P, P]),
+    "ba_batch_set_schedule": (I32, [P, I32, I32, I32]),
+    "ba_batch_get_schedule": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                    ctypes.POINTER(I32)]),
+    "ba_batch_autotune": (I32, [P, ctypes.POINTER(Options), I32, ctypes.POINTER(BatchTrial), I32,
+                                ctypes.POINTER(I32)]),
 }
 
 _lib = None
@@ -253,6 +266,101 @@ class Problem:
             lib().ba_problem_destroy(self._h)
             self._h = None
             self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent problems solved by one persistent launch (ba_batch_*).
+
+    problems: sequence of objects with n_cams, n_pts, cam_idx, pt_idx (local indices)
+    and pixels [n_obs, 2]; they are concatenated in the given order."""
+
+    def __init__(self, problems, stream=None):
+        torch = _torch()
+        self.n_problems = len(problems)
+        nc = np.array([p.n_cams for p in problems], dtype=np.int64)
+        npt = np.array([p.n_pts for p in problems], dtype=np.int64)
+        no = np.array([len(p.cam_idx) for p in problems], dtype=np.int64)
+        self.cam_off = np.concatenate([[0], np.cumsum(nc)]).astype(np.int32)
+        self.pt_off = np.concatenate([[0], np.cumsum(npt)]).astype(np.int32)
+        self.obs_off = np.concatenate([[0], np.cumsum(no)]).astype(np.int64)
+        ci = np.ascontiguousarray(np.concatenate([p.cam_idx for p in problems]), dtype=np.uint32)
+        pi = np.ascontiguousarray(np.concatenate([p.pt_idx for p in problems]), dtype=np.uint32)
+        px = np.ascontiguousarray(np.concatenate([p.pixels for p in problems]), dtype=np.float64)
+        self.total_cams, self.total_pts, self.n_obs = int(self.cam_off[-1]), int(self.pt_off[-1]), int(ci.shape[0])
+        h = ctypes.c_void_p()
+        check(lib().ba_batch_create(self.n_problems, _ptr(self.cam_off), _ptr(self.pt_off), _ptr(self.obs_off),
+                                    _ptr(ci), _ptr(pi), _ptr(px), ctypes.byref(h)))
+        self._h = h
+        nbytes = ctypes.c_size_t()
+        check(lib().ba_batch_workspace_size(h, ctypes.byref(nbytes)))
+        self.workspace_bytes = int(nbytes.value)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(self.workspace_bytes, dtype=torch.uint8, device="cuda")
+        check(lib().ba_batch_bind_workspace(h, self.workspace.data_ptr(), self.workspace_bytes,
+                                            self.stream.cuda_stream))
+
+    def set_params(self, cams, pts):
+        """cams [total_cams, 9], pts [total_pts, 3] (host, concatenated per problem)."""
+        c = np.ascontiguousarray(cams, dtype=np.float64).reshape(self.total_cams, 9)
+        p = np.ascontiguousarray(pts, dtype=np.float64).reshape(self.total_pts, 3)
+        check(lib().ba_batch_set_params(self._h, _ptr(c), _ptr(p)))
+
+    def get_params(self):
+        c = np.empty((self.total_cams, 9))
+        p = np.empty((self.total_pts, 3))
+        check(lib().ba_batch_get_params(self._h, _ptr(c), _ptr(p)))
+        return c, p
+
+    def solve(self, options: Options | None = None, wait=True, **kw):
+        """Solves every problem; returns a list of SolveResult (no history) if wait."""
+        o = options if options is not None else default_options(**kw)
+        if not wait:
+            check(lib().ba_batch_solve(self._h, ctypes.byref(o), None))
+            return None
+        st = (Stats * self.n_problems)()
+        check(lib().ba_batch_solve(self._h, ctypes.byref(o), st))
+        return [SolveResult(s.initial_cost, s.final_cost, s.lm_iters, s.accepted, s.pcg_iters_total, s.status,
+                            s.solve_ns, []) for s in st]
+
+    def costs(self):
+        a = np.empty(self.n_problems)
+        b = np.empty(self.n_problems)
+        check(lib().ba_batch_get_costs(self._h, _ptr(a), _ptr(b)))
+        return a, b
+
+    def set_schedule(self, threads, ctas_per_sm=0, stage_points=False):
+        check(lib().ba_batch_set_schedule(self._h, int(threads), int(ctas_per_sm),
+                                          BA_SCHED_STAGE_POINTS if stage_points else 0))
+
+    def schedule(self):
+        t, c, f, g = I32(), I32(), I32(), I32()
+        check(lib().ba_batch_get_schedule(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(f),
+                                          ctypes.byref(g)))
+        return dict(threads=t.value, ctas_per_sm=c.value, stage_points=bool(f.value & BA_SCHED_STAGE_POINTS),
+                    grid=g.value)
+
+    def autotune(self, options: Options | None = None, ignore_cache=False, **kw):
+        """Times the candidate schedules and keeps the fastest; returns the trials."""
+        o = options if options is not None else default_options(**kw)
+        cap = 64
+        tr = (BatchTrial * cap)()
+        n = I32()
+        check(lib().ba_batch_autotune(self._h, ctypes.byref(o), BA_TUNE_IGNORE_CACHE if ignore_cache else 0, tr, cap,
+                                      ctypes.byref(n)))
+        return [dict(threads=t.threads, ctas_per_sm=t.ctas_per_sm,
+                     stage_points=bool(t.flags & BA_SCHED_STAGE_POINTS), grid=t.grid, ms=t.ms)
+                for t in tr[: n.value]]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ba_batch_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

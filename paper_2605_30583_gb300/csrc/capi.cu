@@ -961,36 +961,4 @@ ba_status ba_cost_backward(ba_problem* p, const void* cams, const void* pts, int
     return BA_OK;
 }
 
-ba_status ba_batch_create(int32_t, const int32_t*, const int32_t*, const int64_t*, const uint32_t*,
-                          const uint32_t*, const double*, ba_batch** out) {
-    if (out) *out = nullptr;
-    set_error("ba_batch_create: not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
-}
-void ba_batch_destroy(ba_batch*) {}
-ba_status ba_batch_workspace_size(const ba_batch*, size_t*) {
-    set_error("not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
-}
-ba_status ba_batch_bind_workspace(ba_batch*, void*, size_t, void*) {
-    set_error("not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
-}
-ba_status ba_batch_set_params(ba_batch*, const double*, const double*) {
-    set_error("not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
-}
-ba_status ba_batch_get_params(ba_batch*, double*, double*) {
-    set_error("not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
-}
-ba_status ba_batch_solve(ba_batch*, const ba_options*, ba_stats*) {
-    set_error("not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
-}
-ba_status ba_batch_get_costs(ba_batch*, double*, double*) {
-    set_error("not implemented");
-    return BA_ERR_NOT_IMPLEMENTED;
-}
-
 }  // extern "C"

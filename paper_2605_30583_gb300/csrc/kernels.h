@@ -15,6 +15,17 @@ constexpr int MV_TB = 128;    // threads per tile CTA, normal operator
 constexpr int EV_TB = 128;    // threads per tile CTA, candidate evaluation
 constexpr int PCG_TB = 512;   // threads per CTA of the persistent PCG kernel
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` and never lowers
+// it: the limit is per function, shared by every problem in the process, so a later
+// problem with smaller tiles must not break launches of an earlier one.
+inline cudaError_t ensure_dynamic_smem(const void* func, int bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, func);
+    if (e != cudaSuccess) return e;
+    if (a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 struct LaunchCfg {
     int item_block = 256;
     int item_grid = 1024;   // cap on blocks of per-node kernels
@@ -95,5 +106,7 @@ struct OrderBuffers {
 };
 template <typename T>
 void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s);
+// Ascending sort of (key, value) pairs, n a power of two >= 2 (order.cu).
+void sort_pairs(uint64_t* keys, uint32_t* vals, size_t n, cudaStream_t s);
 
 }  // namespace gbba

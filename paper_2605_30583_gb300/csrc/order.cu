@@ -257,6 +257,8 @@ void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s) {
                                                         const_cast<uint32_t*>(v.pt_obs_off));
 }
 
+void sort_pairs(uint64_t* keys, uint32_t* vals, size_t n, cudaStream_t s) { bitonic_sort(keys, vals, n, s); }
+
 template void build_order<float>(const Views<float>&, const OrderBuffers&, cudaStream_t);
 template void build_order<double>(const Views<double>&, const OrderBuffers&, cudaStream_t);
 

@@ -365,8 +365,7 @@ int persistent_max_smem() {
 }
 
 cudaError_t persistent_prepare(int smem_bytes, int* blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_pcg_persistent<PCG_TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem_bytes);
+    cudaError_t e = ensure_dynamic_smem((const void*)k_pcg_persistent<PCG_TB>, smem_bytes);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pcg_persistent<PCG_TB>, PCG_TB,
                                                          smem_bytes);

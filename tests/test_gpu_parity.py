@@ -181,3 +181,20 @@ def test_single_tile_and_heavy_point(B):
     refs = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels,
                       O.LMOptions(max_lm_iters=5))
     assert abs(res.final_cost - refs.final_cost) <= 1e-4 * max(refs.final_cost, 1e-9) + 1e-6
+
+
+def test_problems_bound_side_by_side_keep_working(B):
+    """Several problems bound at once, larger first: each keeps its own launch shape
+    (the persistent kernel's shared-memory limit is per function and must only grow)."""
+    # 60,000 points = 235 tiles: more tiles than SMs, so its CTAs hold several tiles
+    big = synth.round_to_f32(synth.make_problem(40, 60000, ("poisson", 4.0), "nearest", seed=61))
+    small = synth.round_to_f32(synth.make_config("tiny", seed=62))
+    opts = dict(max_lm_iters=3, max_pcg_iters=30)
+    pb = _problem(B, big)
+    ps = _problem(B, small)      # bound after the big one
+    rb = pb.solve(**opts)
+    rs = ps.solve(**opts)
+    for prob, r in ((big, rb), (small, rs)):
+        ref = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels, O.LMOptions(**opts))
+        assert r.status == 0
+        assert abs(r.final_cost - ref.final_cost) <= 1e-4 * ref.final_cost
