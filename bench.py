@@ -126,6 +126,25 @@ def matvec_model(prob):
     return nb, nf
 
 
+# DRAM bytes (read + write) per launch of k_pcg_persistent from one ncu capture of the
+# same workload (profiles/k_pcg_persistent_medium.md); None until captured.
+PCG_TRAFFIC = {}
+
+
+def pcg_iter_model(prob):
+    """Algorithmic bytes and FP32 flops of one PCG iteration (recomputed Jacobian).
+
+    Bytes: the normal operator as in matvec_model, plus the vector update and the
+    preconditioner apply at 44 bytes per unknown (p, q, D, r, z read; h, r, z
+    written; h read) and the block-Jacobi inverses (24 bytes per point block, 324 per
+    camera block).  Flops: the operator (120 per observation) plus ~30 per unknown."""
+    nb, nf = matvec_model(prob)
+    n = 9 * prob.n_cams + 3 * prob.n_pts
+    nb += 44 * n + 24 * prob.n_pts + 324 * prob.n_cams
+    nf += 30 * n
+    return nb, nf
+
+
 # ---------------------------------------------------------------- reference arm ---
 
 def run_reference(args, rank, world):
@@ -187,6 +206,25 @@ def cpu_baseline(prob, seconds=12.0):
 
 # ---------------------------------------------------------------- our arm ---------
 
+def replica_seed(config_seed, rank):
+    """Seed of rank `rank`'s replica: every rank solves its own problem of the same shape."""
+    return config_seed + 7919 * rank
+
+
+def aggregate_over_ranks(total_ms, units, world, device):
+    """Whole-job timing of independent replicas: the slowest rank's time and the units
+    (PCG iterations) summed over ranks.  No-op for one rank."""
+    import torch
+    if world <= 1:
+        return float(total_ms), float(units)
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -195,8 +233,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     build.build()
     dev = torch.device("cuda", local_rank)
-    base_seed = synth.CONFIGS[args.config]["seed"]
-    prob = synth.make_config(args.config, seed=base_seed + 7919 * rank)
+    prob = synth.make_config(args.config, seed=replica_seed(synth.CONFIGS[args.config]["seed"], rank))
     target = golden_cost(args.config) if rank == 0 else None
     opts = binding.default_options(use_graph=args.graph_mode)
 
@@ -239,14 +276,7 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms, float(pcg)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
-        pc = t[1:].clone()
-        dist.all_reduce(pc, op=dist.ReduceOp.SUM)
-        t[1] = pc[0]
-    total_ms_max, pcg_all = float(t[0]), float(t[1])
+    total_ms_max, pcg_all = aggregate_over_ranks(sum(step_ms), pcg, world, dev)
     value = pcg_all / (total_ms_max / 1e3)
 
     # ---- normal-operator kernel: live timing with CUDA events on the launching stream
@@ -281,15 +311,31 @@ def run_ours(args, rank, world, local_rank):
     roof_alu = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
                 "traffic": None,
                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
-    roofline = roof_alu if roof_alu["frac"] >= roof_hbm["frac"] else roof_hbm
-    roofline = dict(roofline, kernel="k_matvec (damped normal operator, recomputed Jacobian)",
-                    ms_per_launch=mv_ms, algorithmic_bytes=nb, algorithmic_flops=nf)
-    other = roof_hbm if roofline["bound"] == "alu" else roof_alu
+    matvec_roofline = dict(roof_alu if roof_alu["frac"] >= roof_hbm["frac"] else roof_hbm,
+                           kernel="k_matvec (damped normal operator, recomputed Jacobian, multi-kernel path)",
+                           ms_per_launch=mv_ms, algorithmic_bytes=nb, algorithmic_flops=nf)
 
-    # ---- per-kernel times in isolation (CUDA events, warm, back-to-back)
+    # ---- per-kernel times in isolation (CUDA events, warm, back-to-back); the
+    # persistent PCG kernel (one launch = one PCG solve) is the dominant kernel of the
+    # timed step: its roofline is taken from its own event-timed launches
     p.set_params(cams0, pts0)
     p.evaluate()
     kernel_us = p.profile_kernels(20)
+    pb, pf = pcg_iter_model(prob)
+    it_pcg = kernel_us.get("pcg_persistent_iters", 0.0)
+    us_pcg = kernel_us.get("pcg_persistent", -1.0)
+    if us_pcg > 0 and it_pcg > 0:
+        gbs_p = pb * it_pcg / (us_pcg / 1e6) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs_p, "peak": hbm_peak, "unit": "GB/s", "frac": gbs_p / hbm_peak,
+                    "traffic": PCG_TRAFFIC.get(args.config),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured, burst copy)",
+                    "kernel": "k_pcg_persistent (one PCG solve per launch, tiles resident in shared memory)",
+                    "us_per_launch": us_pcg, "pcg_iters_per_launch": it_pcg,
+                    "algorithmic_bytes_per_pcg_iter": pb, "algorithmic_flops_per_pcg_iter": pf,
+                    "alu_frac": pf * it_pcg / (us_pcg / 1e6) / 1e12 / alu_peak}
+    else:
+        roofline = matvec_roofline
+    other = matvec_roofline
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -356,7 +402,7 @@ def run_ours(args, rank, world, local_rank):
         except binding.BAError as e:
             fp64 = {"unavailable": str(e)}
 
-    batched = None if args.no_batch else run_batched(args, binding, synth, torch, dev, stream, flush)
+    batched = None if args.no_batch else run_batched(args, binding, synth, torch, dev, stream, flush, rank)
 
     launches_per_step = 1 + 3 + 5 * last.lm_iters + 3 * last.pcg_iters_total + 1
     ttc = time_to_cost(last.history, target * (1 + 1e-4) if target else None)
@@ -370,7 +416,7 @@ def run_ours(args, rank, world, local_rank):
         "final_cost": last.final_cost, "oracle_final_cost": target,
         "time_to_cost_ms": ttc, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
         "step_ms": step_ms,
-        "roofline": roofline, "roofline_other": other,
+        "roofline": roofline, "roofline_matvec": other,
         "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "batched": batched, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -379,12 +425,12 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(out), flush=True)
 
 
-def run_batched(args, binding, synth, torch, dev, stream, flush):
+def run_batched(args, binding, synth, torch, dev, stream, flush, rank=0):
     """The uneven-size batch: 512 problems (cameras U[5,60], points U[200,5000],
     2+Poisson(3) views) solved by one persistent launch under a captured graph, after
     the autotuner picked the schedule; beside it the same problems solved one by one
     with the single-problem solver."""
-    probs = synth.make_batch(512)
+    probs = synth.make_batch(512, seed=replica_seed(30000, rank))
     opts = binding.default_options(use_graph=1)
     b = binding.Batch(probs)
     cams0 = np.concatenate([q.cams_init for q in probs])
@@ -448,6 +494,29 @@ def run_batched(args, binding, synth, torch, dev, stream, flush):
     return out
 
 
+def run_batch_only(args, rank, world, local_rank):
+    """The batched workload on its own (bench.py --config batch512): one JSON line."""
+    import torch
+    from paper_2605_30583_gb300 import binding, build, synth
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    b = run_batched(args, binding, synth, torch, dev, torch.cuda.current_stream(), flush, rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ms_max, problems = aggregate_over_ranks(b["ms_per_batch_solve"], 512, world, dev)
+    out = {"metric": "batched BA solve: problems/s", "value": problems / (ms_max / 1e3), "unit": "problems/s",
+           "n_gpus": world, "steps": max(1, min(3, args.steps)), "warmup": 1, "ms_per_step": ms_max,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": b["workload"], "l2": "flushed between timed steps (256 MiB write)"},
+           "batched": b}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -461,7 +530,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.config == "batch512":
+        run_batch_only(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

@@ -181,7 +181,11 @@ ba_status ba_repeat_normal(ba_problem* problem, int32_t launches);
  * `reps` back-to-back launches each, after a prior ba_evaluate or ba_solve.  Writes
  * the average microseconds per launch into us_out[0..n) in this order: camera
  * records, linearisation, preconditioner, normal operator (matvec), PCG update,
- * candidate step, candidate evaluation, commit.  Leaves the solver state undefined
+ * candidate step, candidate evaluation, commit; then [8] one launch of the persistent
+ * PCG kernel (a whole PCG solve capped at 50 iterations with zero tolerance, each
+ * launch after a preconditioner launch that resets its state, events around the PCG
+ * launch alone) and [9] the PCG iterations that launch ran; -1 and 0 there when the
+ * problem does not fit the persistent kernel.  Leaves the solver state undefined
  * (the next ba_solve starts afresh).  Synchronises. */
 ba_status ba_profile_kernels(ba_problem* problem, int32_t reps, double* us_out, int32_t n);
 

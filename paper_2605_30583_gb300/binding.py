@@ -225,7 +225,7 @@ class Problem:
         return out, vav.value
 
     KERNELS = ("camera_records", "linearize", "precond", "matvec", "update", "candidate", "eval_candidate",
-               "commit")
+               "commit", "pcg_persistent", "pcg_persistent_iters")
 
     def profile_kernels(self, reps=20) -> dict:
         out = np.zeros(len(self.KERNELS))
