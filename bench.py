@@ -126,9 +126,10 @@ def matvec_model(prob):
     return nb, nf
 
 
-# DRAM bytes (read + write) per launch of k_pcg_persistent from one ncu capture of the
-# same workload (profiles/k_pcg_persistent_medium.md); None until captured.
-PCG_TRAFFIC = {}
+# DRAM bytes (read + write) per 50-iteration launch of k_pcg_persistent, from one ncu
+# capture of the same workload and launch (profiles/k_pcg_persistent_medium.md).  Set to
+# None whenever the kernel changes until it is captured again.
+PCG_TRAFFIC = {"medium": 19975680}
 
 
 def pcg_iter_model(prob):
