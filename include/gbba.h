@@ -247,7 +247,7 @@ ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_pts, int64_t n_obs, const fl
  *   every point observed at least twice; otherwise BA_ERR_INVALID_ARG.
  * ba_batch_workspace_size / ba_batch_bind_workspace: one device arena (256-byte
  *   aligned) and a borrowed stream, as for ba_problem.  Binding sorts the observations
- *   on the device (problem, camera, point) and builds the point-major index; it fails
+ *   on the device by problem and camera (points in a per-camera rotated order) and builds the point-major index; it fails
  *   with BA_ERR_INVALID_ARG if the largest problem's shared-memory tables (376 bytes
  *   per camera + 12 bytes per point) do not fit one CTA.  Binding selects the default
  *   schedule (256 threads, occupancy-limited CTAs per SM).

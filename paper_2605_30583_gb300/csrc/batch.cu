@@ -6,7 +6,8 @@
 // one of the single-problem mixed-precision path: FP32 residuals, Jacobian products
 // and vectors; FP64 block inversions, PCG dot products and cost sums.
 //
-// Per problem the observations are sorted by (camera, point); a point-major index
+// Per problem the observations are sorted by camera, and within a camera's run by
+// point from a camera-dependent starting point; a point-major index
 // serves the passes that need all observations of one point.  During PCG the CTA keeps
 // the problem's camera records, camera direction records, camera accumulators and the
 // point part of the product q = (J^T J) p in shared memory.
@@ -47,7 +48,7 @@ struct BatchView {
     const int32_t* pt_off;      // [P + 1] global point offsets
     const int64_t* obs_off;     // [P + 1]
     const int64_t* vec_off;     // [P + 1] offsets of each problem's [9 nc | 3 np] vector block
-    const uint32_t* obs_key;    // local camera << 16 | local point, sorted per problem by (camera, point)
+    const uint32_t* obs_key;    // local camera << 16 | local point, sorted per problem by camera
     const float* obs_uv;        // [n_obs][2]
     const uint32_t* pm_pos;     // point-major: global positions of each point's observations
     const uint32_t* pt_obs_off; // [total points + 1] offsets into pm_pos
@@ -746,12 +747,26 @@ __global__ void __launch_bounds__(TB, MINB) k_batch_solve(BatchView b) {
 
 // ------------------------------------------------------------------ ordering -----
 
-// Key of every observation for the camera-major order: (problem, camera, point).
-__global__ void k_batch_keys(const uint32_t* cam_loc, const uint32_t* pt_loc, const int32_t* obs_prob, int64_t n_obs,
-                             size_t sort_n, uint64_t* keys, uint32_t* vals) {
+// Key of every observation for the camera-major order: (problem, camera, rotated
+// point).  Within a camera's run the points start from a camera-dependent offset, so
+// threads walking different cameras' runs in step touch different points.
+constexpr uint32_t PT_ROTATION = 89;
+
+__device__ __forceinline__ uint32_t rot_pt(uint32_t pt, uint32_t cam, uint32_t np) {
+    return (uint32_t)((pt + (uint64_t)PT_ROTATION * cam) % np);
+}
+
+__device__ __forceinline__ uint32_t unrot_pt(uint32_t rpt, uint32_t cam, uint32_t np) {
+    return (uint32_t)((rpt + np - ((uint64_t)PT_ROTATION * cam) % np) % np);
+}
+
+__global__ void k_batch_keys(const uint32_t* cam_loc, const uint32_t* pt_loc, const int32_t* obs_prob,
+                             const int32_t* pt_off, int64_t n_obs, size_t sort_n, uint64_t* keys, uint32_t* vals) {
     for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < sort_n; o += (size_t)gridDim.x * blockDim.x) {
         if (o < (size_t)n_obs) {
-            keys[o] = ((uint64_t)obs_prob[o] << 40) | ((uint64_t)cam_loc[o] << 16) | (uint64_t)pt_loc[o];
+            const int32_t q = obs_prob[o];
+            const uint32_t np = (uint32_t)(pt_off[q + 1] - pt_off[q]);
+            keys[o] = ((uint64_t)q << 40) | ((uint64_t)cam_loc[o] << 16) | (uint64_t)rot_pt(pt_loc[o], cam_loc[o], np);
             vals[o] = (uint32_t)o;
         } else {
             keys[o] = ~0ull;
@@ -760,12 +775,15 @@ __global__ void k_batch_keys(const uint32_t* cam_loc, const uint32_t* pt_loc, co
     }
 }
 
-__global__ void k_batch_gather(const uint64_t* keys, const uint32_t* vals, const double* pixels, int64_t n_obs,
-                               uint32_t* obs_key, float* obs_uv) {
+__global__ void k_batch_gather(const uint64_t* keys, const uint32_t* vals, const double* pixels, const int32_t* pt_off,
+                               int64_t n_obs, uint32_t* obs_key, float* obs_uv) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_obs; j += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t k = keys[j];
         const uint32_t o = vals[j];
-        obs_key[j] = (uint32_t)(k & 0xffffffffull);   // local camera << 16 | local point
+        const int32_t q = (int32_t)(k >> 40);
+        const uint32_t np = (uint32_t)(pt_off[q + 1] - pt_off[q]);
+        const uint32_t cam = (uint32_t)((k >> 16) & 0xffffu);
+        obs_key[j] = (cam << 16) | unrot_pt((uint32_t)(k & 0xffffu), cam, np);   // local camera << 16 | local point
         obs_uv[2 * j] = (float)pixels[2 * (size_t)o];
         obs_uv[2 * j + 1] = (float)pixels[2 * (size_t)o + 1];
     }
@@ -1188,16 +1206,17 @@ ba_status ba_batch_bind_workspace(ba_batch* B, void* ws, size_t bytes, void* str
     GBBA_CUDA(up(B->o_s_cam, B->cam_idx.data(), 4 * B->cam_idx.size()));
     GBBA_CUDA(up(B->o_s_pt, B->pt_idx.data(), 4 * B->pt_idx.size()));
     GBBA_CUDA(up(B->o_s_px, B->pixels.data(), 8 * B->pixels.size()));
-    // (problem, camera, point) order, then the point-major index, sorted on the device
+    // (problem, camera, rotated point) order, then the point-major index, sorted on the device
     uint64_t* keys = (uint64_t*)(w + B->o_s_keys);
     uint32_t* vals = (uint32_t*)(w + B->o_s_vals);
     const int TB = 256;
     const int gb = (int)std::min<size_t>(8192, (B->sort_cap + TB - 1) / TB);
     k_batch_keys<<<gb, TB, 0, s>>>((const uint32_t*)(w + B->o_s_cam), (const uint32_t*)(w + B->o_s_pt),
-                                   (const int32_t*)(w + B->o_obs_prob), B->n_obs, B->sort_cap, keys, vals);
+                                   (const int32_t*)(w + B->o_obs_prob), (const int32_t*)(w + B->o_pt_off), B->n_obs,
+                                   B->sort_cap, keys, vals);
     sort_pairs(keys, vals, B->sort_cap, s);
-    k_batch_gather<<<gb, TB, 0, s>>>(keys, vals, (const double*)(w + B->o_s_px), B->n_obs, (uint32_t*)(w + B->o_key),
-                                     (float*)(w + B->o_uv));
+    k_batch_gather<<<gb, TB, 0, s>>>(keys, vals, (const double*)(w + B->o_s_px), (const int32_t*)(w + B->o_pt_off),
+                                     B->n_obs, (uint32_t*)(w + B->o_key), (float*)(w + B->o_uv));
     k_batch_pm_keys<<<gb, TB, 0, s>>>(vals, (const uint32_t*)(w + B->o_s_pt), (const int32_t*)(w + B->o_obs_prob),
                                       (const int32_t*)(w + B->o_pt_off), B->n_obs, B->sort_cap, keys);
     sort_pairs(keys, vals, B->sort_cap, s);

@@ -18,6 +18,9 @@ namespace gbba {
 
 namespace {
 
+// Odd, so camera-dependent starting slots spread over all TILE_PTS (a power of two).
+constexpr uint64_t SLOT_ROTATION = 89;
+
 constexpr int LOCAL_ELEMS = 2048;
 constexpr int LOCAL_THREADS = LOCAL_ELEMS / 2;
 
@@ -95,7 +98,11 @@ __global__ void k_obs_sort_keys(const uint32_t* cam_idx, const uint32_t* pt_idx,
         if (o < (size_t)n_obs) {
             const uint32_t ip = pt_internal[pt_idx[o]];
             const uint64_t tile = ip / TILE_PTS, slot = ip % TILE_PTS;
-            keys[o] = (tile << 40) | ((uint64_t)cam_idx[o] << 16) | (slot << 8);
+            // within a camera's run the points are ordered from a camera-dependent
+            // starting slot: threads that walk different cameras' runs of one tile in
+            // step then touch different points (no same-address shared atomics)
+            const uint64_t rslot = (slot + SLOT_ROTATION * (uint64_t)cam_idx[o]) % TILE_PTS;
+            keys[o] = (tile << 40) | ((uint64_t)cam_idx[o] << 16) | (rslot << 8);
             vals[o] = (uint32_t)o;
         } else {
             keys[o] = ~0ull;
@@ -111,7 +118,8 @@ __global__ void k_obs_gather(const uint64_t* keys, const uint32_t* vals, const d
         const uint64_t k = keys[j];
         const uint32_t o = vals[j];
         const uint32_t cam = (uint32_t)((k >> 16) & 0xffffffu);
-        const uint32_t slot = (uint32_t)((k >> 8) & 0xffu);
+        const uint32_t rslot = (uint32_t)((k >> 8) & 0xffu);
+        const uint32_t slot = (uint32_t)((rslot + TILE_PTS - (SLOT_ROTATION * (uint64_t)cam) % TILE_PTS) % TILE_PTS);
         obs_key[j] = (cam << 8) | slot;
         obs_uv[2 * j] = (T)pixels[2 * (size_t)o];
         obs_uv[2 * j + 1] = (T)pixels[2 * (size_t)o + 1];
