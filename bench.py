@@ -334,6 +334,13 @@ def run_ours(args, rank, world, local_rank):
                     "us_per_launch": us_pcg, "pcg_iters_per_launch": it_pcg,
                     "algorithmic_bytes_per_pcg_iter": pb, "algorithmic_flops_per_pcg_iter": pf,
                     "alu_frac": pf * it_pcg / (us_pcg / 1e6) / 1e12 / alu_peak}
+        # context: the same iterations priced at what a stored-Jacobian form would have
+        # to move (96 B of J + 8 B of indices per observation, 36 B per point, 108 B per
+        # camera for the operator, plus the same vector traffic)
+        sj_bytes = 104 * prob.n_obs + 36 * prob.n_pts + 108 * prob.n_cams + (pb - matvec_model(prob)[0])
+        sj_gbs = sj_bytes * it_pcg / (us_pcg / 1e6) / 1e9
+        roofline["stored_jacobian_equivalent"] = {"bytes_per_pcg_iter": sj_bytes, "achieved": sj_gbs,
+                                                  "frac": sj_gbs / hbm_peak}
     else:
         roofline = matvec_roofline
     other = matvec_roofline

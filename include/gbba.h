@@ -78,6 +78,15 @@ typedef struct {
     int32_t pcg_kernel;           /* 0: one persistent cooperative kernel per PCG solve when
                                      every CTA's tiles fit in shared memory (default);
                                      1: separate kernels per PCG iteration           */
+    int32_t rotation_update;      /* how a step updates each camera's rotation:
+                                     0 (default): additive angle-axis, w <- w + dw, the
+                                     Jacobian taken w.r.t. w (through the left Jacobian
+                                     J_l(w) of the exponential map);
+                                     1: tangent-space retraction (the paper's Pose3
+                                     update, Sec. VI-A), R <- Exp(d) R(w), the Jacobian
+                                     taken w.r.t. d at d = 0, and w <- Log(Exp(d) Exp(w))
+                                     stored back in angle-axis form.  ba_evaluate, the
+                                     autograd entries and ba_cost_noalloc always use w. */
 } ba_options;
 
 /* One LM iteration (Sec. V): cost before the step, candidate cost, damping used,

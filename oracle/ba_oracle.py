@@ -21,6 +21,8 @@ the paper (arXiv 2605.30583, "Caspar"):
                      are solved by PCGNR (Sec. V-A) with a block-Jacobi
                      preconditioner, one block per node (Sec. V).
 * settings        -- Sec. VI: initial trust region 100, CG tolerance 0.001.
+* retraction      -- Sec. VI-A's Pose3 update as an option: rotations stepped by
+                     R <- Exp(d) R (scipy's rotation composition), Jacobian w.r.t. d.
 
 Readings where the paper is silent (all listed in the design notes): damping
 matrix D = diag(J^T J) clamped to [min_diag, max_diag]; mu_0 = 1 / trust region;
@@ -162,12 +164,16 @@ def _sign_no_zero(x):
     return np.where(_value(x) >= 0.0, 1.0, -1.0)
 
 
-def project(cam, X, eps_depth=0.0):
-    """Pixel predicted for a camera cam = (w0,w1,w2,t0,t1,t2,f,k1,k2) and point X."""
+def project(cam, X, eps_depth=0.0, base_w=None):
+    """Pixel predicted for a camera cam = (w0,w1,w2,t0,t1,t2,f,k1,k2) and point X.
+
+    With base_w given, the camera's rotation is Exp(w) R(base_w): cam[0:3] is then a
+    tangent-space step d applied on the left (the retraction R <- Exp(d) R of the
+    paper's Pose3 update, Sec. VI-A)."""
     w = cam[0:3]
     t = cam[3:6]
     f, k1, k2 = cam[6], cam[7], cam[8]
-    RX = rotate(w, X)
+    RX = rotate(w, X) if base_w is None else rotate(w, rotate(base_w, X))
     P0, P1, P2 = RX[0] + t[0], RX[1] + t[1], RX[2] + t[2]
     d_safe = P2 + eps_depth * _sign_no_zero(P2)
     p0 = -P0 / d_safe
@@ -194,9 +200,12 @@ def cost(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0):
     return 0.5 * float(np.sum(r * r))
 
 
-def jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, chunk=200_000):
+def jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, chunk=200_000, retraction=False):
     """Residuals r [n_obs,2] and Jacobian blocks J_c [n_obs,2,9], J_p [n_obs,2,3], by
-    forward-mode dual numbers seeded with the 12 tangent directions of (camera, point)."""
+    forward-mode dual numbers seeded with the 12 tangent directions of (camera, point).
+
+    retraction=False: the rotation columns are d r / d w (additive angle-axis).
+    retraction=True: they are d r / d d at d = 0 for the rotation Exp(d) R(w)."""
     cams = np.asarray(cams, np.float64)
     pts = np.asarray(pts, np.float64)
     ci = np.asarray(cam_idx, np.int64)
@@ -213,7 +222,11 @@ def jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, chunk=200
         X = pts[pi[s:e]]
         cd = [Dual(c[:, k], np.broadcast_to(eye[k], (m, 12))) for k in range(9)]
         Xd = [Dual(X[:, k], np.broadcast_to(eye[9 + k], (m, 12))) for k in range(3)]
-        u0, u1 = project(cd, Xd, eps_depth)
+        if retraction:   # the step d, seeded at 0, on the left of R(w)
+            cd[0:3] = [Dual(np.zeros(m), np.broadcast_to(eye[k], (m, 12))) for k in range(3)]
+            u0, u1 = project(cd, Xd, eps_depth, base_w=[c[:, 0], c[:, 1], c[:, 2]])
+        else:
+            u0, u1 = project(cd, Xd, eps_depth)
         r[s:e, 0] = u0.v - pixels[s:e, 0]
         r[s:e, 1] = u1.v - pixels[s:e, 1]
         Jc[s:e, 0] = u0.d[:, :9]
@@ -253,9 +266,9 @@ def assemble_jacobian(Jc, Jp, cam_idx, pt_idx, n_cams, n_pts):
     return sp.csr_matrix((vals, (rows, cols)), shape=(2 * n_obs, n))
 
 
-def linearize(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0) -> Linearization:
+def linearize(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, retraction=False) -> Linearization:
     n_cams, n_pts = cams.shape[0], pts.shape[0]
-    r, Jc, Jp = jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth)
+    r, Jc, Jp = jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth, retraction=retraction)
     J = assemble_jacobian(Jc, Jp, cam_idx, pt_idx, n_cams, n_pts)
     rf = r.reshape(-1)
     g = J.T @ rf
@@ -351,6 +364,7 @@ class LMOptions:
     max_diag: float = 1e32
     eps_depth: float = 0.0
     max_mu: float = 1e32
+    rotation_update: str = "additive"   # or "retraction": R <- Exp(d) R, J w.r.t. d
 
 
 @dataclasses.dataclass
@@ -364,9 +378,10 @@ class LMResult:
     pcg_iters_total: int
 
 
-def lm_solve(x0, linearize_fn, cost_fn, make_precond, opts: LMOptions = LMOptions()) -> LMResult:
+def lm_solve(x0, linearize_fn, cost_fn, make_precond, opts: LMOptions = LMOptions(), step_fn=None) -> LMResult:
     """Generic LM over x.  linearize_fn(x) -> object with F, J (sparse) and g = J^T r;
-    cost_fn(x) -> F; make_precond(lin, D, mu) -> callable applying the preconditioner.
+    cost_fn(x) -> F; make_precond(lin, D, mu) -> callable applying the preconditioner;
+    step_fn(x, h) -> x' applies a step (default x + h).
 
     One iteration: solve (J^T J + mu D) h = -g by PCGNR; x' = x + h;
     rho = (F - F') / (-g^T h - 1/2 |J h|^2).  If rho > 0 the step is accepted,
@@ -389,7 +404,7 @@ def lm_solve(x0, linearize_fn, cost_fn, make_precond, opts: LMOptions = LMOption
         pcg_total += res.iters
         Jh = lin.J @ h
         L = float(-(lin.g @ h) - 0.5 * (Jh @ Jh))
-        x_new = x + h
+        x_new = x + h if step_fn is None else step_fn(x, h)
         F_new = cost_fn(x_new)
         rho = (lin.F - F_new) / L if L > 0 else -np.inf
         ok = bool(np.isfinite(F_new) and L > 0 and rho > 0)
@@ -428,19 +443,40 @@ def unpack(x, n_cams):
     return x[: 9 * n_cams].reshape(n_cams, 9), x[9 * n_cams:].reshape(-1, 3)
 
 
+def retract_cams(cams, h_cams):
+    """Cameras after a tangent step: rotation Exp(h_w) R(w), returned as a rotation
+    vector; translation, focal length and distortion updated additively."""
+    from scipy.spatial.transform import Rotation
+    cams = np.asarray(cams, np.float64)
+    h = np.asarray(h_cams, np.float64)
+    out = cams + h
+    out[:, 0:3] = (Rotation.from_rotvec(h[:, 0:3]) * Rotation.from_rotvec(cams[:, 0:3])).as_rotvec()
+    return out
+
+
 def ba_solve(cams0, pts0, cam_idx, pt_idx, pixels, opts: LMOptions = LMOptions()) -> LMResult:
-    """Bundle adjustment by LM + PCGNR over all camera and point parameters."""
+    """Bundle adjustment by LM + PCGNR over all camera and point parameters.  With
+    opts.rotation_update == "retraction" each step updates the rotations by
+    R <- Exp(d) R (Jacobian w.r.t. d), the rest additively."""
     n_cams = cams0.shape[0]
+    retraction = opts.rotation_update == "retraction"
+    if opts.rotation_update not in ("additive", "retraction"):
+        raise ValueError(opts.rotation_update)
 
     def lin_fn(x):
         c, p = unpack(x, n_cams)
-        return linearize(c, p, cam_idx, pt_idx, pixels, opts.eps_depth)
+        return linearize(c, p, cam_idx, pt_idx, pixels, opts.eps_depth, retraction=retraction)
 
     def cost_fn(x):
         c, p = unpack(x, n_cams)
         return cost(c, p, cam_idx, pt_idx, pixels, opts.eps_depth)
 
-    return lm_solve(pack(cams0, pts0), lin_fn, cost_fn, _ba_precond, opts)
+    def step_fn(x, h):
+        c, p = unpack(x, n_cams)
+        hc, hp = unpack(h, n_cams)
+        return pack(retract_cams(c, hc), p + hp)
+
+    return lm_solve(pack(cams0, pts0), lin_fn, cost_fn, _ba_precond, opts, step_fn if retraction else None)
 
 
 def normal_matvec(lin: Linearization, D, mu, v):

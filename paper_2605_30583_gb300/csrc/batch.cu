@@ -131,7 +131,7 @@ __device__ void b_camera_records(const BatchView& b, const Prob& P, const float*
     for (int c = threadIdx.x; c < P.nc; c += blockDim.x) {
         double pr[9];
         for (int k = 0; k < 9; ++k) pr[k] = (double)xs[P.v0 + 9 * c + k];
-        camera_record(pr, rec + (size_t)(P.c0 + c) * CP_STRIDE);
+        camera_record(pr, rec + (size_t)(P.c0 + c) * CP_STRIDE, b.opt.retract != 0);
         if (clear) {
             for (int k = 0; k < CL_STRIDE; ++k) b.cam_g[(size_t)(P.c0 + c) * CL_STRIDE + k] = 0.0;
             for (int k = 0; k < CH_STRIDE; ++k) b.cam_H[(size_t)(P.c0 + c) * CH_STRIDE + k] = 0.0f;
@@ -599,6 +599,16 @@ __device__ void b_candidate(const BatchView& b, const Prob& P, const float* sCam
         lgh += ge * (double)h[e];
     }
     __syncthreads();
+    if (b.opt.retract) {   // rotations: R' = Exp(h_w) R(w)
+        for (int c = tid; c < P.nc; c += TB) {
+            const double w[3] = {x[9 * c], x[9 * c + 1], x[9 * c + 2]};
+            const double hw[3] = {h[9 * c], h[9 * c + 1], h[9 * c + 2]};
+            double wn[3];
+            compose_rotvec(hw, w, wn);
+            for (int k = 0; k < 3; ++k) xn[9 * c + k] = (float)wn[k];
+        }
+        __syncthreads();
+    }
     b_camera_records(b, P, b.x_new, b.cam_pre_new, false);
     for (int c = tid; c < P.nc; c += TB) {   // direction records of h at x
         const float* JL = b.cam_pre + (size_t)(P.c0 + c) * CP_STRIDE + CP_JL;
@@ -992,12 +1002,14 @@ DevOptions dev_options(const ba_options* o) {
     d.max_diag = o->max_diag;
     d.max_mu = o->max_mu;
     d.eps = o->eps_depth;
+    d.retract = o->rotation_update;
     return d;
 }
 
 bool options_ok(const ba_options* o) {
     return o && o->max_lm_iters >= 0 && o->max_pcg_iters >= 0 && o->initial_trust_region > 0 && o->min_diag > 0 &&
-           o->max_diag >= o->min_diag && o->pcg_rel_tol >= 0 && o->eps_depth >= 0 && o->max_mu > 0;
+           o->max_diag >= o->min_diag && o->pcg_rel_tol >= 0 && o->eps_depth >= 0 && o->max_mu > 0 &&
+           (o->rotation_update == 0 || o->rotation_update == 1);
 }
 
 // Launch of the solve: a captured graph (queue reset + persistent kernel), rebuilt

@@ -357,6 +357,7 @@ ba_status ba_options_default(ba_options* o) {
     o->eps_depth = 0.0;
     o->use_graph = 1;
     o->pcg_kernel = 0;
+    o->rotation_update = 0;
     return BA_OK;
 }
 
@@ -657,6 +658,9 @@ ba_status ba_evaluate(ba_problem* p, double* cost_out, void* residuals, void* ja
     ba_status st = check_bound(p, "ba_evaluate");
     if (st) return st;
     DevState* dst = dev_state(p);
+    // evaluation is always w.r.t. the angle-axis parameters (no retraction records)
+    const int32_t additive = 0;
+    GBBA_CUDA(cudaMemcpyAsync(&dst->opt.retract, &additive, sizeof(additive), cudaMemcpyHostToDevice, p->stream));
     if (p->precision == BA_PREC_MIXED) {
         launch_camera_precompute(p->vf, p->L, p->stream);
         launch_linearize(p->vf, p->L, p->stream, 2, (float*)residuals, (float*)jacobian, 0, 0);
@@ -682,7 +686,8 @@ static ba_status check_options(const ba_options* o) {
     }
     if (o->max_lm_iters < 0 || o->max_pcg_iters < 0 || !(o->pcg_rel_tol >= 0) || !(o->initial_trust_region > 0) ||
         !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0) ||
-        (o->pcg_kernel != 0 && o->pcg_kernel != 1) || o->use_graph < 0 || o->use_graph > 2) {
+        (o->pcg_kernel != 0 && o->pcg_kernel != 1) || o->use_graph < 0 || o->use_graph > 2 ||
+        (o->rotation_update != 0 && o->rotation_update != 1)) {
         set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive)");
         return BA_ERR_INVALID_ARG;
     }
@@ -699,6 +704,7 @@ static ba_status write_options(ba_problem* p, const ba_options* o) {
     d.max_diag = o->max_diag;
     d.max_mu = o->max_mu;
     d.eps = o->eps_depth;
+    d.retract = o->rotation_update;
     static_assert(offsetof(DevState, opt) == 0, "options first");
     GBBA_CUDA(cudaMemcpyAsync(p->ws + p->lay.state, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
     return BA_OK;

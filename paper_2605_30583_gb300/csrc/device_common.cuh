@@ -155,7 +155,9 @@ __device__ __forceinline__ void rodrigues_coeffs(double th2, double& A, double& 
 // R(w) = I + A [w]x + B [w]x^2 and J_l(w) = I + B [w]x + C [w]x^2, where J_l is the
 // left Jacobian of the rotation exponential: R(w + d) = Exp(J_l(w) d) R(w) + O(|d|^2),
 // so d(R(w) X)/dw . d = (J_l d) x (R X).
-__device__ __forceinline__ void camera_record(const double* c, float* out) {
+// With `retract` the record is for the tangent-space update R <- Exp(d) R(w): the
+// rotation Jacobian is then taken w.r.t. d at d = 0, i.e. J_l is replaced by I.
+__device__ __forceinline__ void camera_record(const double* c, float* out, bool retract = false) {
     const double w0 = c[0], w1 = c[1], w2 = c[2];
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
     double A, B, C;
@@ -169,7 +171,7 @@ __device__ __forceinline__ void camera_record(const double* c, float* out) {
     for (int i = 0; i < 9; ++i) {
         const double I = (i % 4 == 0) ? 1.0 : 0.0;
         out[CP_R + i] = (float)(I + A * K[i] + B * K2[i]);
-        out[CP_JL + i] = (float)(I + B * K[i] + C * K2[i]);
+        out[CP_JL + i] = retract ? (float)I : (float)(I + B * K[i] + C * K2[i]);
     }
     out[CP_T + 0] = (float)c[3];
     out[CP_T + 1] = (float)c[4];
@@ -178,6 +180,48 @@ __device__ __forceinline__ void camera_record(const double* c, float* out) {
     out[CP_K1] = (float)c[7];
     out[CP_K2] = (float)c[8];
     out[CP_PAD] = 0.0f;
+}
+
+// Unit quaternion (q0; q1 q2 q3) of the rotation vector v: (cos(t/2); sin(t/2) v / t),
+// t = |v|, with the Taylor series of both factors for t^2 < 1e-12.
+__device__ __forceinline__ void rotvec_quat(const double* v, double* q) {
+    const double t2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    double c, s_over_t;
+    if (t2 < 1e-12) {
+        c = 1.0 - t2 / 8.0 + t2 * t2 / 384.0;
+        s_over_t = 0.5 - t2 / 48.0 + t2 * t2 / 3840.0;
+    } else {
+        const double t = sqrt(t2);
+        double sn;
+        sincos(0.5 * t, &sn, &c);
+        s_over_t = sn / t;
+    }
+    q[0] = c;
+    q[1] = s_over_t * v[0];
+    q[2] = s_over_t * v[1];
+    q[3] = s_over_t * v[2];
+}
+
+// Rotation vector of Exp(h) Exp(w) (the retraction of a tangent step h at w), through
+// the Hamilton product of unit quaternions q(h) q(w), taken with q0 >= 0, and
+// w' = 2 atan2(|q_v|, q0) q_v / |q_v| (series 2 / q0 (1 - |q_v|^2 / (3 q0^2)) when
+// |q_v| < 1e-7).  FP64.
+__device__ __forceinline__ void compose_rotvec(const double* h, const double* w, double* out) {
+    double a[4], b[4];
+    rotvec_quat(h, a);
+    rotvec_quat(w, b);
+    double q0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    double q1 = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    double q2 = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    double q3 = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    if (q0 < 0.0) {
+        q0 = -q0; q1 = -q1; q2 = -q2; q3 = -q3;
+    }
+    const double n = sqrt(q1 * q1 + q2 * q2 + q3 * q3);
+    const double scale = n > 1e-7 ? 2.0 * atan2(n, q0) / n : (2.0 / q0) * (1.0 - n * n / (3.0 * q0 * q0));
+    out[0] = scale * q1;
+    out[1] = scale * q2;
+    out[2] = scale * q3;
 }
 
 // ------------------------------------------------------------- projection core ---

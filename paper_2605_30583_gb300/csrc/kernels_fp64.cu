@@ -18,7 +18,9 @@ using V64 = Views<double>;
 namespace {
 
 // Camera record in FP64, same field order as the FP32 record (CP_*).
-__device__ void camera_record64(const double* c, double* out) {
+// With `retract` the rotation Jacobian is taken w.r.t. the tangent step d of
+// R <- Exp(d) R(w) at d = 0: J_l is replaced by I.
+__device__ void camera_record64(const double* c, double* out, bool retract = false) {
     const double w0 = c[0], w1 = c[1], w2 = c[2];
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
     double A, B, C;
@@ -29,7 +31,7 @@ __device__ void camera_record64(const double* c, double* out) {
     for (int i = 0; i < 9; ++i) {
         const double I = (i % 4 == 0) ? 1.0 : 0.0;
         out[CP_R + i] = I + A * K[i] + B * K2[i];
-        out[CP_JL + i] = I + B * K[i] + C * K2[i];
+        out[CP_JL + i] = retract ? I : I + B * K[i] + C * K2[i];
     }
     for (int k = 0; k < 3; ++k) out[CP_T + k] = c[3 + k];
     out[CP_F] = c[6];
@@ -85,7 +87,7 @@ __device__ __forceinline__ int gtid() { return blockIdx.x * blockDim.x + threadI
 
 __global__ void k64_camera_precompute(V64 v) {
     for (int c = gtid(); c < v.n_cams; c += grid_threads()) {
-        camera_record64(v.x + 9 * (size_t)c, v.cam64 + (size_t)c * CP_STRIDE);
+        camera_record64(v.x + 9 * (size_t)c, v.cam64 + (size_t)c * CP_STRIDE, v.st->opt.retract != 0);
         for (int k = 0; k < CL_STRIDE; ++k) v.cam_lin[(size_t)c * CL_STRIDE + k] = 0.0;
         for (int k = 0; k < CH_STRIDE; ++k) v.cam_H64[(size_t)c * CH_STRIDE + k] = 0.0;
     }
@@ -371,17 +373,22 @@ __global__ void k64_update(V64 v, CondHandle pcg_cond, int use_cond) {
 __global__ void k64_candidate(V64 v) {
     DevState* st = v.st;
     if (st->lm_active == 0) return;
+    const bool retract = st->opt.retract != 0;
     double gh = 0.0;
     for (size_t e = gtid(); e < (size_t)v.n_vec; e += grid_threads()) {
-        v.x_new[e] = v.x[e] + v.h[e];
-        const double ge = e < 9 * (size_t)v.n_cams ? v.cam_lin[(e / 9) * CL_STRIDE + e % 9]
-                                                   : (e >= (size_t)v.pt_off ? v.g[e] : 0.0);
+        const bool cam = e < 9 * (size_t)v.n_cams;
+        if (!(retract && cam && e % 9 < 3)) v.x_new[e] = v.x[e] + v.h[e];   // rotations: below
+        const double ge = cam ? v.cam_lin[(e / 9) * CL_STRIDE + e % 9] : (e >= (size_t)v.pt_off ? v.g[e] : 0.0);
         gh += ge * v.h[e];
     }
     for (int c = gtid(); c < v.n_cams; c += grid_threads()) {
         double xn[9];
         for (int k = 0; k < 9; ++k) xn[k] = v.x[9 * (size_t)c + k] + v.h[9 * (size_t)c + k];
-        camera_record64(xn, v.cam64_new + (size_t)c * CP_STRIDE);
+        if (retract) {   // R' = Exp(h_w) R(w)
+            compose_rotvec(v.h + 9 * (size_t)c, v.x + 9 * (size_t)c, xn);
+            for (int k = 0; k < 3; ++k) v.x_new[9 * (size_t)c + k] = xn[k];
+        }
+        camera_record64(xn, v.cam64_new + (size_t)c * CP_STRIDE, retract);
     }
     double in[1] = {gh}, out[1];
     if (grid_reduce<1>(in, v.partials, &st->tickets[TK_CAND], out) && threadIdx.x == 0) st->gh = out[0];

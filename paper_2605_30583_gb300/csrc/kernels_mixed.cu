@@ -33,7 +33,7 @@ __global__ void k_camera_precompute(Views<float> v) {
         double p[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) p[k] = (double)v.x[9 * (size_t)c + k];
-        camera_record(p, v.cam_pre + (size_t)c * CP_STRIDE);
+        camera_record(p, v.cam_pre + (size_t)c * CP_STRIDE, v.st->opt.retract != 0);
         double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
 #pragma unroll
         for (int k = 0; k < CL_STRIDE; ++k) cl[k] = 0.0;
@@ -587,6 +587,7 @@ __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond) {
 __global__ void k_candidate(Views<float> v) {
     DevState* st = v.st;
     if (st->lm_active == 0) return;
+    const bool retract = st->opt.retract != 0;
     double gh = 0.0;
     FOR_CAMERAS(c, v) {
         {
@@ -602,7 +603,19 @@ __global__ void k_candidate(Views<float> v) {
                 xn[k] = (double)xk;
                 gh += cl[CL_G + k] * (double)hc[k];
             }
-            camera_record(xn, v.cam_pre_new + (size_t)c * CP_STRIDE);
+            if (retract) {   // R' = Exp(h_w) R(w)
+                const double w[3] = {v.x[e], v.x[e + 1], v.x[e + 2]};
+                const double hw[3] = {hc[0], hc[1], hc[2]};
+                double wn[3];
+                compose_rotvec(hw, w, wn);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float wk = (float)wn[k];
+                    v.x_new[e + k] = wk;
+                    xn[k] = (double)wk;
+                }
+            }
+            camera_record(xn, v.cam_pre_new + (size_t)c * CP_STRIDE, retract);
             const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
             float* d = v.cam_dir + (size_t)c * CD_STRIDE;
 #pragma unroll

@@ -47,6 +47,8 @@ __host__ __device__ constexpr int tri_index(int n, int i, int j) {
 struct DevOptions {
     int32_t max_lm, max_pcg;
     double tol, mu0, min_diag, max_diag, max_mu, eps;
+    int32_t retract;   // 1: rotations updated by retraction R <- Exp(d) R (J w.r.t. d)
+    int32_t pad;
 };
 
 // Layout-compatible with ba_iter_stat of the public header.

@@ -3,7 +3,8 @@ copy of the oracle (on the CPU, in a temporary tree) and the pin suite must fail
 
 The mutations are the mistakes a restatement of the method could make: a dropped
 Rodrigues or distortion term, a wrong sign or index, a wrong damping, gain-ratio or
-Madsen constant, a transposed block, an inverted CG coefficient.
+Madsen constant, a transposed block, an inverted CG coefficient, a retraction applied
+on the wrong side.
 """
 import os
 import shutil
@@ -26,6 +27,9 @@ MUTATIONS = {
     "point_columns_permuted": ("cols_p = 9 * n_cams + 3 * pi", "cols_p = 9 * n_cams + 3 * pi[::-1]"),
     "cg_beta_inverted": ("beta = rz_new / rz", "beta = rz / rz_new"),
     "depth_guard_sign": ("d_safe = P2 + eps_depth * _sign_no_zero(P2)", "d_safe = P2 - eps_depth * _sign_no_zero(P2)"),
+    "retraction_composed_on_the_right": ("(Rotation.from_rotvec(h[:, 0:3]) * Rotation.from_rotvec(cams[:, 0:3]))",
+                                         "(Rotation.from_rotvec(cams[:, 0:3]) * Rotation.from_rotvec(h[:, 0:3]))"),
+    "retraction_step_on_the_right": ("rotate(w, rotate(base_w, X))", "rotate(base_w, rotate(w, X))"),
 }
 
 

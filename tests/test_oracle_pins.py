@@ -313,3 +313,82 @@ def test_gradient_vanishes_at_solution():
     g0 = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels).g
     g1 = O.linearize(c, q, p.cam_idx, p.pt_idx, p.pixels).g
     assert np.linalg.norm(g1) < 1e-6 * np.linalg.norm(g0)
+
+
+# ---------------------------------------------------------------- retraction ------
+# The paper's Pose3 update (Sec. VI-A) as the oracle's rotation_update="retraction":
+# rotations step as R <- Exp(d) R(w), the Jacobian taken w.r.t. d at d = 0.
+
+
+def _skew(w):
+    return np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+
+
+def test_retraction_jacobian_matches_central_differences():
+    p = _small_problem(seed=41)
+    S = np.arange(min(40, p.n_obs))
+    cams, pts = p.cams_init, p.pts_init
+    _, Jc, Jp = O.jacobian_blocks(cams, pts, p.cam_idx[S], p.pt_idx[S], p.pixels[S], retraction=True)
+    _, Jc_add, Jp_add = O.jacobian_blocks(cams, pts, p.cam_idx[S], p.pt_idx[S], p.pixels[S])
+    eps = 1e-6
+    for i in range(3):
+        e = np.zeros((cams.shape[0], 3))
+        e[:, i] = eps
+        cp, cm = cams.copy(), cams.copy()
+        # perturbed rotations Exp(+-eps e_i) R(w), composed by scipy (independent of the oracle)
+        cp[:, 0:3] = (Rotation.from_rotvec(e) * Rotation.from_rotvec(cams[:, 0:3])).as_rotvec()
+        cm[:, 0:3] = (Rotation.from_rotvec(-e) * Rotation.from_rotvec(cams[:, 0:3])).as_rotvec()
+        rp = O.residuals(cp, pts, p.cam_idx[S], p.pt_idx[S], p.pixels[S])
+        rm = O.residuals(cm, pts, p.cam_idx[S], p.pt_idx[S], p.pixels[S])
+        fd = (rp - rm) / (2 * eps)
+        assert np.linalg.norm(fd - Jc[:, :, i]) <= 1e-6 * np.linalg.norm(fd)
+    # every other column is the additive Jacobian's
+    assert np.allclose(Jc[:, :, 3:], Jc_add[:, :, 3:], rtol=1e-13, atol=0)
+    assert np.allclose(Jp, Jp_add, rtol=1e-13, atol=0)
+
+
+def test_retraction_jacobian_maps_to_additive_through_left_jacobian():
+    """d r/d w = (d r/d d) J_l(w), with the closed-form left Jacobian of SO(3)
+    J_l(w) = I + (1 - cos t)/t^2 [w]x + (t - sin t)/t^3 [w]x^2."""
+    p = _small_problem(seed=42)
+    S = np.arange(min(40, p.n_obs))
+    _, Jd, _ = O.jacobian_blocks(p.cams_init, p.pts_init, p.cam_idx[S], p.pt_idx[S], p.pixels[S], retraction=True)
+    _, Jw, _ = O.jacobian_blocks(p.cams_init, p.pts_init, p.cam_idx[S], p.pt_idx[S], p.pixels[S])
+    for o in range(len(S)):
+        w = p.cams_init[p.cam_idx[S[o]], 0:3]
+        t = np.linalg.norm(w)
+        K = _skew(w)
+        Jl = np.eye(3) + (1 - np.cos(t)) / t**2 * K + (t - np.sin(t)) / t**3 * (K @ K)
+        assert np.allclose(Jd[o][:, 0:3] @ Jl, Jw[o][:, 0:3], rtol=1e-9, atol=1e-9 * np.abs(Jw[o]).max())
+
+
+def test_retraction_step_composes_on_the_left():
+    rng = np.random.default_rng(43)
+    cams = rng.standard_normal((6, 9))
+    h = 0.1 * rng.standard_normal((6, 9))
+    out = O.retract_cams(cams, h)
+    assert np.allclose(out[:, 3:], cams[:, 3:] + h[:, 3:], rtol=0, atol=1e-15)
+    assert np.allclose(O.retract_cams(cams, np.zeros_like(h))[:, 0:3],
+                       Rotation.from_rotvec(cams[:, 0:3]).as_rotvec(), atol=1e-14)
+    # R(w') X == R(h) (R(w) X), checked with the oracle's own Rodrigues rotation
+    X = list(rng.standard_normal((3, 6)))
+    lhs = O.rotate(list(out[:, 0:3].T), X)
+    rhs = O.rotate(list(h[:, 0:3].T), list(O.rotate(list(cams[:, 0:3].T), X)))
+    assert np.allclose(np.array(lhs), np.array(rhs), atol=1e-12)
+
+
+def test_lm_retraction_reaches_the_additive_optimum():
+    """The minimum of F does not depend on how rotations are parametrised: run to
+    convergence, both updates end at the same cost and a vanishing gradient."""
+    p = _small_problem(seed=44, n_cams=4, n_pts=40)
+    out = {}
+    for ru in ("additive", "retraction"):
+        opts = O.LMOptions(max_lm_iters=60, max_pcg_iters=400, pcg_rel_tol=1e-10, rotation_update=ru)
+        out[ru] = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, opts)
+    a, b = out["additive"].final_cost, out["retraction"].final_cost
+    assert abs(a - b) <= 1e-9 * a
+    for r in out.values():
+        c, q = O.unpack(r.x, p.n_cams)
+        lin = O.linearize(c, q, p.cam_idx, p.pt_idx, p.pixels)
+        lin0 = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+        assert np.linalg.norm(lin.g) <= 1e-6 * np.linalg.norm(lin0.g)
