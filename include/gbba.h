@@ -87,6 +87,13 @@ typedef struct {
                                      taken w.r.t. d at d = 0, and w <- Log(Exp(d) Exp(w))
                                      stored back in angle-axis form.  ba_evaluate, the
                                      autograd entries and ba_cost_noalloc always use w. */
+    int32_t loss;                 /* robust loss on s = |r_o|^2 of each observation, F =
+                                     1/2 sum rho(s): 0 squared (default, rho = s);
+                                     1 Huber (rho = s for s <= d^2, else 2 d sqrt(s) - d^2);
+                                     2 Cauchy (rho = d^2 log(1 + s/d^2)).  LM runs on the
+                                     IRLS-weighted system J^T W J + mu D, W = rho'(s) at
+                                     the linearisation point.  Not in the batched mode.  */
+    double loss_scale;            /* the loss's scale d in pixels, default 1              */
 } ba_options;
 
 /* One LM iteration (Sec. V): cost before the step, candidate cost, damping used,

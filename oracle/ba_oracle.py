@@ -23,6 +23,8 @@ the paper (arXiv 2605.30583, "Caspar"):
 * settings        -- Sec. VI: initial trust region 100, CG tolerance 0.001.
 * retraction      -- Sec. VI-A's Pose3 update as an option: rotations stepped by
                      R <- Exp(d) R (scipy's rotation composition), Jacobian w.r.t. d.
+* robust loss     -- robust factors (named in Sec. VI-A as an easy addition): Huber or
+                     Cauchy on |r_o|^2 with IRLS weights rho'(|r_o|^2).
 
 Readings where the paper is silent (all listed in the design notes): damping
 matrix D = diag(J^T J) clamped to [min_diag, max_diag]; mu_0 = 1 / trust region;
@@ -200,6 +202,12 @@ def cost(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0):
     return 0.5 * float(np.sum(r * r))
 
 
+def robust_cost(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, loss="squared", loss_scale=1.0):
+    """F = 1/2 sum_o rho(|r_o|^2)."""
+    r = residuals(cams, pts, cam_idx, pt_idx, pixels, eps_depth)
+    return 0.5 * float(np.sum(robust_rho(np.sum(r * r, axis=1), loss, loss_scale)))
+
+
 def jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, chunk=200_000, retraction=False):
     """Residuals r [n_obs,2] and Jacobian blocks J_c [n_obs,2,9], J_p [n_obs,2,3], by
     forward-mode dual numbers seeded with the 12 tangent directions of (camera, point).
@@ -266,9 +274,52 @@ def assemble_jacobian(Jc, Jp, cam_idx, pt_idx, n_cams, n_pts):
     return sp.csr_matrix((vals, (rows, cols)), shape=(2 * n_obs, n))
 
 
-def linearize(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, retraction=False) -> Linearization:
+# Robust losses on s = |r_o|^2 (Sec. VI-A names robust factors as an easy addition):
+# F = 1/2 sum_o rho(s_o).  Each is given with rho'(s), the IRLS weight of observation o.
+#   squared: rho(s) = s                                rho' = 1
+#   Huber:   rho(s) = s (s <= d^2), 2 d sqrt(s) - d^2    rho' = 1, d / sqrt(s)
+#   Cauchy:  rho(s) = d^2 log(1 + s / d^2)               rho' = 1 / (1 + s / d^2)
+LOSSES = ("squared", "huber", "cauchy")
+
+
+def robust_rho(s, loss="squared", scale=1.0):
+    s = np.asarray(s, np.float64)
+    if loss == "squared":
+        return s.copy()
+    d2 = scale * scale
+    if loss == "huber":
+        return np.where(s <= d2, s, 2.0 * scale * np.sqrt(s) - d2)
+    if loss == "cauchy":
+        return d2 * np.log1p(s / d2)
+    raise ValueError(loss)
+
+
+def robust_weight(s, loss="squared", scale=1.0):
+    s = np.asarray(s, np.float64)
+    if loss == "squared":
+        return np.ones_like(s)
+    d2 = scale * scale
+    if loss == "huber":
+        return np.where(s <= d2, 1.0, scale / np.sqrt(np.maximum(s, d2)))
+    if loss == "cauchy":
+        return 1.0 / (1.0 + s / d2)
+    raise ValueError(loss)
+
+
+def linearize(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, retraction=False, loss="squared",
+              loss_scale=1.0) -> Linearization:
+    """F, g = J^T W r and the node blocks of J^T W J, with W the IRLS weights
+    w_o = rho'(|r_o|^2) (all ones for the squared loss).  J and r are returned already
+    scaled by sqrt(w_o), so every later product (PCG, |J h|^2) is the weighted one;
+    F = 1/2 sum rho(|r_o|^2)."""
     n_cams, n_pts = cams.shape[0], pts.shape[0]
     r, Jc, Jp = jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth, retraction=retraction)
+    s = np.sum(r * r, axis=1)
+    F = 0.5 * float(np.sum(robust_rho(s, loss, loss_scale)))
+    sw = np.sqrt(robust_weight(s, loss, loss_scale))
+    r = r * sw[:, None]
+    Jc = Jc * sw[:, None, None]
+    Jp = Jp * sw[:, None, None]
     J = assemble_jacobian(Jc, Jp, cam_idx, pt_idx, n_cams, n_pts)
     rf = r.reshape(-1)
     g = J.T @ rf
@@ -276,7 +327,7 @@ def linearize(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, retraction=Fals
     Hp = np.zeros((n_pts, 3, 3))
     np.add.at(Hc, np.asarray(cam_idx, np.int64), np.einsum("oki,okj->oij", Jc, Jc))
     np.add.at(Hp, np.asarray(pt_idx, np.int64), np.einsum("oki,okj->oij", Jp, Jp))
-    return Linearization(F=0.5 * float(rf @ rf), r=rf, J=J, g=g, Hc=Hc, Hp=Hp)
+    return Linearization(F=F, r=rf, J=J, g=g, Hc=Hc, Hp=Hp)
 
 
 # --------------------------------------------------------------------------------------
@@ -365,6 +416,8 @@ class LMOptions:
     eps_depth: float = 0.0
     max_mu: float = 1e32
     rotation_update: str = "additive"   # or "retraction": R <- Exp(d) R, J w.r.t. d
+    loss: str = "squared"               # or "huber", "cauchy" (IRLS weights, see LOSSES)
+    loss_scale: float = 1.0             # the loss's scale d, in pixels
 
 
 @dataclasses.dataclass
@@ -465,11 +518,12 @@ def ba_solve(cams0, pts0, cam_idx, pt_idx, pixels, opts: LMOptions = LMOptions()
 
     def lin_fn(x):
         c, p = unpack(x, n_cams)
-        return linearize(c, p, cam_idx, pt_idx, pixels, opts.eps_depth, retraction=retraction)
+        return linearize(c, p, cam_idx, pt_idx, pixels, opts.eps_depth, retraction=retraction, loss=opts.loss,
+                         loss_scale=opts.loss_scale)
 
     def cost_fn(x):
         c, p = unpack(x, n_cams)
-        return cost(c, p, cam_idx, pt_idx, pixels, opts.eps_depth)
+        return robust_cost(c, p, cam_idx, pt_idx, pixels, opts.eps_depth, opts.loss, opts.loss_scale)
 
     def step_fn(x, h):
         c, p = unpack(x, n_cams)

@@ -94,6 +94,7 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     l.pt_H = s.take(T * PH_STRIDE * 4 * n_quads);
     l.Minv_c = s.take(T * MC_STRIDE * nc);
     l.Minv_p = s.take(T * MP_STRIDE * 4 * n_quads);
+    l.obs_w = s.take(4 * no);
     if (precision == BA_PREC_FP64) {
         l.jac = s.take(T * 24 * no);
         l.res = s.take(T * 2 * no);
@@ -156,6 +157,7 @@ Views<T> make_views(ba_problem* p) {
     v.cam_H64 = l.cam_H64 ? (double*)(w + l.cam_H64) : nullptr;
     v.jac = l.jac ? (T*)(w + l.jac) : nullptr;
     v.res = l.res ? (T*)(w + l.res) : nullptr;
+    v.obs_w = (float*)(w + l.obs_w);
     v.st = (DevState*)(w + l.state);
     v.partials = (double*)(w + l.partials);
     v.staging = w + l.staging;
@@ -358,6 +360,8 @@ ba_status ba_options_default(ba_options* o) {
     o->use_graph = 1;
     o->pcg_kernel = 0;
     o->rotation_update = 0;
+    o->loss = 0;
+    o->loss_scale = 1.0;
     return BA_OK;
 }
 
@@ -658,9 +662,11 @@ ba_status ba_evaluate(ba_problem* p, double* cost_out, void* residuals, void* ja
     ba_status st = check_bound(p, "ba_evaluate");
     if (st) return st;
     DevState* dst = dev_state(p);
-    // evaluation is always w.r.t. the angle-axis parameters (no retraction records)
-    const int32_t additive = 0;
-    GBBA_CUDA(cudaMemcpyAsync(&dst->opt.retract, &additive, sizeof(additive), cudaMemcpyHostToDevice, p->stream));
+    // evaluation (and ba_apply_normal after it) is always w.r.t. the angle-axis
+    // parameters and the squared loss
+    static_assert(offsetof(DevOptions, loss) == offsetof(DevOptions, retract) + sizeof(int32_t), "adjacent");
+    const int32_t plain[2] = {0, 0};   // retract, loss
+    GBBA_CUDA(cudaMemcpyAsync(&dst->opt.retract, plain, sizeof(plain), cudaMemcpyHostToDevice, p->stream));
     if (p->precision == BA_PREC_MIXED) {
         launch_camera_precompute(p->vf, p->L, p->stream);
         launch_linearize(p->vf, p->L, p->stream, 2, (float*)residuals, (float*)jacobian, 0, 0);
@@ -687,7 +693,8 @@ static ba_status check_options(const ba_options* o) {
     if (o->max_lm_iters < 0 || o->max_pcg_iters < 0 || !(o->pcg_rel_tol >= 0) || !(o->initial_trust_region > 0) ||
         !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0) ||
         (o->pcg_kernel != 0 && o->pcg_kernel != 1) || o->use_graph < 0 || o->use_graph > 2 ||
-        (o->rotation_update != 0 && o->rotation_update != 1)) {
+        (o->rotation_update != 0 && o->rotation_update != 1) || o->loss < 0 || o->loss > 2 ||
+        !(o->loss_scale > 0)) {
         set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive)");
         return BA_ERR_INVALID_ARG;
     }
@@ -705,6 +712,8 @@ static ba_status write_options(ba_problem* p, const ba_options* o) {
     d.max_mu = o->max_mu;
     d.eps = o->eps_depth;
     d.retract = o->rotation_update;
+    d.loss = o->loss;
+    d.loss_scale = o->loss_scale;
     static_assert(offsetof(DevState, opt) == 0, "options first");
     GBBA_CUDA(cudaMemcpyAsync(p->ws + p->lay.state, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
     return BA_OK;

@@ -224,6 +224,34 @@ __device__ __forceinline__ void compose_rotvec(const double* h, const double* w,
     out[2] = scale * q3;
 }
 
+// Robust loss on s = |r|^2 of one observation (0 squared, 1 Huber, 2 Cauchy; scale d):
+// rho(s) and the IRLS weight rho'(s).
+//   Huber:  rho = s (s <= d^2), 2 d sqrt(s) - d^2;   rho' = 1, d / sqrt(s)
+//   Cauchy: rho = d^2 log(1 + s / d^2);              rho' = 1 / (1 + s / d^2)
+__device__ __forceinline__ float loss_weight(float s, int loss, float d) {
+    if (loss == 1) return s <= d * d ? 1.0f : d * rsqrtf(s);
+    if (loss == 2) return 1.0f / (1.0f + s / (d * d));
+    return 1.0f;
+}
+
+__device__ __forceinline__ float loss_rho(float s, int loss, float d) {
+    if (loss == 1) return s <= d * d ? s : 2.0f * d * sqrtf(s) - d * d;
+    if (loss == 2) return d * d * log1pf(s / (d * d));
+    return s;
+}
+
+__device__ __forceinline__ double loss_weight64(double s, int loss, double d) {
+    if (loss == 1) return s <= d * d ? 1.0 : d / sqrt(s);
+    if (loss == 2) return 1.0 / (1.0 + s / (d * d));
+    return 1.0;
+}
+
+__device__ __forceinline__ double loss_rho64(double s, int loss, double d) {
+    if (loss == 1) return s <= d * d ? s : 2.0 * d * sqrt(s) - d * d;
+    if (loss == 2) return d * d * log1p(s / (d * d));
+    return s;
+}
+
 // ------------------------------------------------------------- projection core ---
 
 struct Cam {

@@ -98,6 +98,9 @@ __global__ void k64_camera_precompute(V64 v) {
 __global__ void k64_linearize(V64 v, int mode, double* res_out, double* jac_out, CondHandle lm_cond, int use_cond) {
     if (mode == 1 && v.st->relin == 0) return;
     const double eps = v.st->opt.eps;
+    // robust loss (evaluation, mode 2, is always the squared loss)
+    const int loss = mode == 2 ? 0 : v.st->opt.loss;
+    const double lscale = v.st->opt.loss_scale;
     double cost = 0.0;
     for (int ip = gtid(); ip < v.n_pts; ip += grid_threads()) {
         const double* X = v.x + v.pt_off + 3 * (size_t)ip;
@@ -108,10 +111,24 @@ __global__ void k64_linearize(V64 v, int mode, double* res_out, double* jac_out,
             double J[24], r0, r1;
             obs_jacobian64(v.cam64 + (size_t)c * CP_STRIDE, X[0], X[1], X[2], eps, v.obs_uv[2 * (size_t)j],
                            v.obs_uv[2 * (size_t)j + 1], r0, r1, J);
+            if (mode == 2) {   // evaluation output: the unweighted residual and Jacobian
+                const uint32_t o = v.obs_user[j];
+                if (res_out) { res_out[2 * (size_t)o] = r0; res_out[2 * (size_t)o + 1] = r1; }
+                if (jac_out) for (int q = 0; q < 24; ++q) jac_out[24 * (size_t)o + q] = J[q];
+            }
+            if (loss) {   // IRLS: the stored rows are scaled by sqrt(rho'(|r|^2))
+                const double s2 = r0 * r0 + r1 * r1;
+                cost += loss_rho64(s2, loss, lscale);
+                const double sw = sqrt(loss_weight64(s2, loss, lscale));
+                r0 *= sw;
+                r1 *= sw;
+                for (int q = 0; q < 24; ++q) J[q] *= sw;
+            } else {
+                cost += r0 * r0 + r1 * r1;
+            }
             for (int q = 0; q < 24; ++q) v.jac[24 * (size_t)j + q] = J[q];
             v.res[2 * (size_t)j] = r0;
             v.res[2 * (size_t)j + 1] = r1;
-            cost += r0 * r0 + r1 * r1;
             double* gc = v.cam_lin + (size_t)c * CL_STRIDE;
             double* hc = v.cam_H64 + (size_t)c * CH_STRIDE;
             for (int a = 0; a < 9; ++a) {
@@ -121,11 +138,6 @@ __global__ void k64_linearize(V64 v, int mode, double* res_out, double* jac_out,
             for (int a = 0; a < 3; ++a) {
                 gp[a] += J[9 + a] * r0 + J[21 + a] * r1;
                 for (int b = a; b < 3; ++b) hp[tri_index(3, a, b)] += J[9 + a] * J[9 + b] + J[21 + a] * J[21 + b];
-            }
-            if (mode == 2) {
-                const uint32_t o = v.obs_user[j];
-                if (res_out) { res_out[2 * (size_t)o] = r0; res_out[2 * (size_t)o + 1] = r1; }
-                if (jac_out) for (int q = 0; q < 24; ++q) jac_out[24 * (size_t)o + q] = J[q];
             }
         }
         for (int a = 0; a < 3; ++a) v.g[v.pt_off + 3 * (size_t)ip + a] = gp[a];
@@ -399,6 +411,8 @@ __global__ void k64_eval_candidate(V64 v, CondHandle lm_cond, int use_cond) {
     DevState* st = v.st;
     const int active = st->lm_active;
     const double eps = st->opt.eps;
+    const int loss = st->opt.loss;
+    const double lscale = st->opt.loss_scale;
     double fnew = 0.0, jh2 = 0.0;
     if (active) {
         for (int ip = gtid(); ip < v.n_pts; ip += grid_threads()) {
@@ -410,8 +424,8 @@ __global__ void k64_eval_candidate(V64 v, CondHandle lm_cond, int use_cond) {
                 double r0, r1;
                 obs_jacobian64(v.cam64_new + (size_t)c * CP_STRIDE, Xn[0], Xn[1], Xn[2], eps, v.obs_uv[2 * (size_t)j],
                                v.obs_uv[2 * (size_t)j + 1], r0, r1, nullptr);
-                fnew += r0 * r0 + r1 * r1;
-                const double* J = v.jac + 24 * (size_t)j;
+                fnew += loss ? loss_rho64(r0 * r0 + r1 * r1, loss, lscale) : r0 * r0 + r1 * r1;
+                const double* J = v.jac + 24 * (size_t)j;   // sqrt(w)-scaled: |J h|^2 is weighted
                 const double* hc = v.h + 9 * (size_t)c;
                 double t0 = J[9] * hp[0] + J[10] * hp[1] + J[11] * hp[2];
                 double t1 = J[21] * hp[0] + J[22] * hp[1] + J[23] * hp[2];

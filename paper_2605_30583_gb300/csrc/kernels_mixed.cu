@@ -73,6 +73,9 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
     if (mode == 1 && v.st->relin == 0) return;
     __shared__ float4 sx[TILE_PTS];
     const float eps = (float)v.st->opt.eps;
+    // robust loss (evaluation, mode 2, is always the squared loss)
+    const int loss = mode == 2 ? 0 : v.st->opt.loss;
+    const float lscale = (float)v.st->opt.loss_scale;
     float cost = 0.0f;
     for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
         const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
@@ -107,8 +110,8 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                 const float4 X = sx[slot];
                 const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
                 const float fs = cam.f * g.s;
-                const float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
-                const float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
+                float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
+                float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
                 // camera Jacobian rows: [J_w | J_t | J_intr], J_w[:,k] = A (J_l[:,k] x RX)
                 float j0[9], j1[9];
 #pragma unroll
@@ -125,6 +128,24 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                 const float fn2 = cam.f * g.n2;
                 j0[6] = g.s * g.p[0]; j0[7] = fn2 * g.p[0]; j0[8] = fn2 * g.n2 * g.p[0];
                 j1[6] = g.s * g.p[1]; j1[7] = fn2 * g.p[1]; j1[8] = fn2 * g.n2 * g.p[1];
+                if (mode == 2) {   // evaluation output: the unweighted residual and Jacobian
+                    const uint32_t o = v.obs_user[j];
+                    if (res_out) { res_out[2 * (size_t)o] = r0; res_out[2 * (size_t)o + 1] = r1; }
+                    if (jac_out) {
+                        float* Jo = jac_out + 24 * (size_t)o;
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) { Jo[k] = j0[k]; Jo[12 + k] = j1[k]; }
+                    }
+                }
+                if (loss) {   // IRLS weight w = rho'(|r|^2): rows scaled by sqrt(w)
+                    const float w = loss_weight(fmaf(r0, r0, r1 * r1), loss, lscale);
+                    if (mode != 2) v.obs_w[j] = w;
+                    const float sw = sqrtf(w);
+                    r0 *= sw;
+                    r1 *= sw;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) { j0[k] *= sw; j1[k] *= sw; }
+                }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) acc[CL_G + i] = fmaf(j0[i], r0, fmaf(j1[i], r1, acc[CL_G + i]));
 #pragma unroll
@@ -134,15 +155,6 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                         const int t = 9 + tri_index(9, i, k);
                         acc[t] = fmaf(j0[i], j0[k], fmaf(j1[i], j1[k], acc[t]));
                     }
-                if (mode == 2) {
-                    const uint32_t o = v.obs_user[j];
-                    if (res_out) { res_out[2 * (size_t)o] = r0; res_out[2 * (size_t)o + 1] = r1; }
-                    if (jac_out) {
-                        float* Jo = jac_out + 24 * (size_t)o;
-#pragma unroll
-                        for (int k = 0; k < 9; ++k) { Jo[k] = j0[k]; Jo[12 + k] = j1[k]; }
-                    }
-                }
             }
             // camera sums: combine lanes of the same camera, one set of atomics per run
             const bool head = seg_reduce<LIN_ACC>(cur, acc);
@@ -160,14 +172,29 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                 const Cam cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
                 const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
                 const float fs = cam.f * g.s;
-                const float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
-                const float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
-                cost = fmaf(r0, r0, fmaf(r1, r1, cost));
+                float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
+                float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
                 float jx0[3], jx1[3];   // J_X = A R
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     jx0[q] = fmaf(g.A[0], cam.R[q], fmaf(g.A[1], cam.R[3 + q], g.A[2] * cam.R[6 + q]));
                     jx1[q] = fmaf(g.A[3], cam.R[q], fmaf(g.A[4], cam.R[3 + q], g.A[5] * cam.R[6 + q]));
+                }
+                if (mode == 2 && jac_out) {
+                    float* Jo = jac_out + 24 * (size_t)v.obs_user[j];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) { Jo[9 + q] = jx0[q]; Jo[21 + q] = jx1[q]; }
+                }
+                if (loss) {
+                    const float s2 = fmaf(r0, r0, r1 * r1);
+                    cost += loss_rho(s2, loss, lscale);
+                    const float sw = sqrtf(loss_weight(s2, loss, lscale));
+                    r0 *= sw;
+                    r1 *= sw;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) { jx0[q] *= sw; jx1[q] *= sw; }
+                } else {
+                    cost = fmaf(r0, r0, fmaf(r1, r1, cost));
                 }
 #pragma unroll
                 for (int q = 0; q < 3; ++q) gp[q] = fmaf(jx0[q], r0, fmaf(jx1[q], r1, gp[q]));
@@ -178,11 +205,6 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                         const int t = tri_index(3, a2, b2);
                         hp[t] = fmaf(jx0[a2], jx0[b2], fmaf(jx1[a2], jx1[b2], hp[t]));
                     }
-                if (mode == 2 && jac_out) {
-                    float* Jo = jac_out + 24 * (size_t)v.obs_user[j];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) { Jo[9 + q] = jx0[q]; Jo[21 + q] = jx1[q]; }
-                }
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q) v.g[base + 3 * i + q] = gp[q];
@@ -354,6 +376,7 @@ __global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* ga
     float* pc_new = v.pc + (size_t)(par ^ 1) * v.pc_stride;
     const float mu = (float)st->mu;
     const float eps = (float)st->opt.eps;
+    const bool weighted = st->opt.loss != 0;
     float pdp = 0.0f, jp2 = 0.0f;
     // camera part of p owned by this CTA
     for (int c = blockIdx.x; c < v.n_cams; c += gridDim.x) {
@@ -396,6 +419,12 @@ __global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* ga
                 cur = c;
                 cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
                 camera_dir(v, c, zs, pc_old, beta, dir);
+            }
+            if (weighted) {   // robust loss: per-observation IRLS weights
+                jp2 += obs_normal<true>(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc, sq + 3 * slot,
+                                        __ldg(v.obs_w + j));
+                j += 1;
+                continue;
             }
             if (j + 1 < b) {
                 const uint32_t key1 = __ldg(v.obs_key + j + 1);
@@ -653,6 +682,8 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
     DevState* st = v.st;
     const int active = st->lm_active;
     const float eps = (float)st->opt.eps;
+    const int loss = st->opt.loss;
+    const float lscale = (float)st->opt.loss_scale;
     double fnew = 0.0, jh2 = 0.0;
     if (active) {
         for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
@@ -678,11 +709,16 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
                 float r0, r1;
                 project_residual(cn, v.x_new[xi], v.x_new[xi + 1], v.x_new[xi + 2], eps,
                                  v.obs_uv[2 * (size_t)j], v.obs_uv[2 * (size_t)j + 1], r0, r1);
-                fc = fmaf(r0, r0, fmaf(r1, r1, fc));
                 const Geo g = project_geo(co, v.x[xi], v.x[xi + 1], v.x[xi + 2], eps);
                 float t0, t1;
                 jdir(g, co, dir, v.h[xi], v.h[xi + 1], v.h[xi + 2], t0, t1);
-                jc = fmaf(t0, t0, fmaf(t1, t1, jc));
+                if (loss) {   // F' = 1/2 sum rho(|r'|^2); |J h|^2 weighted at x
+                    fc += loss_rho(fmaf(r0, r0, r1 * r1), loss, lscale);
+                    jc = fmaf(__ldg(v.obs_w + j), fmaf(t0, t0, t1 * t1), jc);
+                } else {
+                    fc = fmaf(r0, r0, fmaf(r1, r1, fc));
+                    jc = fmaf(t0, t0, fmaf(t1, t1, jc));
+                }
             }
             fnew += (double)fc;
             jh2 += (double)jc;

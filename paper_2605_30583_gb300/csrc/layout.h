@@ -48,7 +48,8 @@ struct DevOptions {
     int32_t max_lm, max_pcg;
     double tol, mu0, min_diag, max_diag, max_mu, eps;
     int32_t retract;   // 1: rotations updated by retraction R <- Exp(d) R (J w.r.t. d)
-    int32_t pad;
+    int32_t loss;      // robust loss: 0 squared, 1 Huber, 2 Cauchy
+    double loss_scale;
 };
 
 // Layout-compatible with ba_iter_stat of the public header.
@@ -106,6 +107,7 @@ struct Views {
     T* Minv_p;        // [4 n_quads][6]
     T* jac;           // plain form only: stored Jacobian [n_obs][2][12]
     T* res;           // plain form only: stored residuals [n_obs][2]
+    float* obs_w;     // IRLS weights of the robust loss, solver observation order [n_obs]
     DevState* st;
     double* partials; // [MAX_GRID][NPART]
     void* staging;    // user-layout parameter staging (FP64, 9 n_cams + 3 n_pts)

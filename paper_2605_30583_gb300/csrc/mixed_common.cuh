@@ -85,8 +85,12 @@ __device__ __forceinline__ void camera_dir(const Views<float>& v, uint32_t c, co
 
 // Contribution of one observation to the normal operator: t = J d (returns |t|^2),
 // camera sums (RX x u, u, intrinsic part) into acc, point part R^T u into qs (shared).
+// WEIGHTED: the robust loss's IRLS weight w scales the observation's rows of J^T J
+// (u = A^T (w t), returns w |t|^2).
+template <bool WEIGHTED = false>
 __device__ __forceinline__ float obs_normal(const Cam& cam, const float (&dir)[9], const float* xs,
-                                            const float* ds, float eps, float (&acc)[9], float* qs) {
+                                            const float* ds, float eps, float (&acc)[9], float* qs,
+                                            float w = 1.0f) {
     const GeoLite g = project_lite(cam, xs[0], xs[1], xs[2], eps);
     // J d = A (phi x RX + d_t + R d_X) + c_i p
     float dP0 = fmaf(dir[1], g.RX[2], -dir[2] * g.RX[1]) + dir[CD_T + 0];
@@ -101,6 +105,11 @@ __device__ __forceinline__ float obs_normal(const Cam& cam, const float (&dir)[9
     apply_A(g, dP0, dP1, dP2, t0, t1);
     t0 = fmaf(ci, g.p[0], t0);
     t1 = fmaf(ci, g.p[1], t1);
+    const float tt = fmaf(t0, t0, t1 * t1);
+    if (WEIGHTED) {
+        t0 *= w;
+        t1 *= w;
+    }
     // adjoint: u = A^T t
     float u0, u1, u2;
     apply_At(g, t0, t1, u0, u1, u2);
@@ -117,7 +126,7 @@ __device__ __forceinline__ float obs_normal(const Cam& cam, const float (&dir)[9
     atomicAdd(qs + 0, fmaf(cam.R[0], u0, fmaf(cam.R[3], u1, cam.R[6] * u2)));
     atomicAdd(qs + 1, fmaf(cam.R[1], u0, fmaf(cam.R[4], u1, cam.R[7] * u2)));
     atomicAdd(qs + 2, fmaf(cam.R[2], u0, fmaf(cam.R[5], u1, cam.R[8] * u2)));
-    return fmaf(t0, t0, t1 * t1);
+    return WEIGHTED ? w * tt : tt;
 }
 
 

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
     const double mu = st->mu;
     const float muf = (float)mu;
     const float eps = (float)st->opt.eps;
+    const bool weighted = st->opt.loss != 0;   // robust loss: IRLS weights per observation
     const double tol2 = st->opt.tol * st->opt.tol;
     const double rr0 = st->rr0;
     const int max_pcg = st->opt.max_pcg;
@@ -229,7 +230,8 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                     }
                     const float4 xp = sX4[lp], pp = sP4[lp];
                     const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
-                    jp2 += obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * lp);
+                    if (weighted) jp2 += obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * lp, __ldg(v.obs_w + ob + j));
+                    else jp2 += obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * lp);
                 }
             }
             // every lane of the warp reaches this one collective

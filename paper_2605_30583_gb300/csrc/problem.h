@@ -26,7 +26,8 @@ struct Layout {
     size_t state, partials, obs_key, obs_uv, obs_user, tile_off, pt_user, pt_internal, obs_pm, pt_obs_off;
     size_t vec[9];                       // x, x_new, h, r, z, p, q, g, D
     size_t blk_tile, blk_cam_off, blk_cams, pslots;
-    size_t cam_pre, cam_pre_new, cam_dir, cam_acc, pc, cam_lin, cam_H, cam64, cam64_new, cam_H64, pt_H, Minv_c, Minv_p, jac, res, staging;
+    size_t cam_pre, cam_pre_new, cam_dir, cam_acc, pc, cam_lin, cam_H, cam64, cam64_new, cam_H64, pt_H, Minv_c, Minv_p, jac, res, obs_w,
+        staging;
     size_t s_cam_idx, s_pt_idx, s_pixels, s_pt_key, s_tile_cnt, s_keys, s_vals, sort_cap;
     size_t total;
 };

@@ -30,6 +30,8 @@ MUTATIONS = {
     "retraction_composed_on_the_right": ("(Rotation.from_rotvec(h[:, 0:3]) * Rotation.from_rotvec(cams[:, 0:3]))",
                                          "(Rotation.from_rotvec(cams[:, 0:3]) * Rotation.from_rotvec(h[:, 0:3]))"),
     "retraction_step_on_the_right": ("rotate(w, rotate(base_w, X))", "rotate(base_w, rotate(w, X))"),
+    "huber_weight_power": ("scale / np.sqrt(np.maximum(s, d2))", "scale / np.maximum(s, d2)"),
+    "cauchy_weight_squared": ("return 1.0 / (1.0 + s / d2)", "return 1.0 / (1.0 + s / d2) ** 2"),
 }
 
 

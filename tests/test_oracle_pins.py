@@ -392,3 +392,71 @@ def test_lm_retraction_reaches_the_additive_optimum():
         lin = O.linearize(c, q, p.cam_idx, p.pt_idx, p.pixels)
         lin0 = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
         assert np.linalg.norm(lin.g) <= 1e-6 * np.linalg.norm(lin0.g)
+
+
+# ---------------------------------------------------------------- robust loss -----
+
+
+def _with_outliers(p, frac=0.05, size=40.0, seed=0):
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    px = p.pixels.copy()
+    idx = rng.choice(p.n_obs, max(1, int(frac * p.n_obs)), replace=False)
+    px[idx] += size * rng.choice([-1.0, 1.0], size=(len(idx), 2))
+    return dataclasses.replace(p, pixels=px)
+
+
+def test_robust_losses_closed_forms():
+    s = np.array([0.0, 0.25, 1.0, 4.0, 100.0])
+    assert np.array_equal(O.robust_rho(s, "squared"), s)
+    # Huber (d = 1): s below d^2, 2 sqrt(s) - 1 above; continuous with slope 1 at d^2
+    assert np.allclose(O.robust_rho(s, "huber", 1.0), [0.0, 0.25, 1.0, 3.0, 19.0])
+    assert np.allclose(O.robust_weight(s, "huber", 1.0), [1.0, 1.0, 1.0, 0.5, 0.1])
+    # Cauchy (d = 2): 4 log(1 + s/4); rho(d^2) = d^2 log 2
+    assert np.isclose(O.robust_rho(np.array([4.0]), "cauchy", 2.0)[0], 4.0 * np.log(2.0))
+    assert np.allclose(O.robust_weight(s, "cauchy", 2.0), 1.0 / (1.0 + s / 4.0))
+    # weights are the derivatives of rho: central differences
+    for loss, sc in (("huber", 1.0), ("cauchy", 2.0)):
+        t = np.array([0.3, 2.5, 9.0, 50.0])
+        fd = (O.robust_rho(t + 1e-6, loss, sc) - O.robust_rho(t - 1e-6, loss, sc)) / 2e-6
+        assert np.allclose(fd, O.robust_weight(t, loss, sc), rtol=1e-6)
+
+
+@pytest.mark.parametrize("loss", ["huber", "cauchy"])
+def test_robust_gradient_is_the_gradient_of_the_robust_cost(loss):
+    """g = sum_o rho'(s_o) J_o^T r_o is the exact gradient of 1/2 sum rho(s_o)."""
+    p = _with_outliers(_small_problem(seed=45))
+    lin = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, loss=loss, loss_scale=2.0)
+    x0 = O.pack(p.cams_init, p.pts_init)
+    rng = np.random.default_rng(1)
+    for k in rng.choice(x0.size, 12, replace=False):
+        e = np.zeros_like(x0)
+        h = 1e-6 * max(1.0, abs(x0[k]))
+        e[k] = h
+        Fp = O.robust_cost(*O.unpack(x0 + e, p.n_cams), p.cam_idx, p.pt_idx, p.pixels, loss=loss, loss_scale=2.0)
+        Fm = O.robust_cost(*O.unpack(x0 - e, p.n_cams), p.cam_idx, p.pt_idx, p.pixels, loss=loss, loss_scale=2.0)
+        fd = (Fp - Fm) / (2 * h)
+        assert abs(fd - lin.g[k]) <= 1e-5 * max(1.0, np.abs(lin.g).max() * 1e-3) + 1e-6 * abs(fd), (k, fd, lin.g[k])
+    assert np.isclose(lin.F, O.robust_cost(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, loss=loss,
+                                           loss_scale=2.0))
+
+
+def test_huber_with_a_huge_scale_is_the_squared_loss():
+    p = _small_problem(seed=46)
+    a = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, O.LMOptions(max_lm_iters=5))
+    b = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels,
+                   O.LMOptions(max_lm_iters=5, loss="huber", loss_scale=1e6))
+    assert a.final_cost == b.final_cost and a.pcg_iters_total == b.pcg_iters_total
+
+
+@pytest.mark.parametrize("loss", ["huber", "cauchy"])
+def test_robust_lm_is_monotone_and_reaches_a_stationary_point(loss):
+    p = _with_outliers(_small_problem(seed=47, n_cams=4, n_pts=40), frac=0.1)
+    opts = O.LMOptions(max_lm_iters=200, max_pcg_iters=400, pcg_rel_tol=1e-10, loss=loss, loss_scale=2.0)
+    r = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, opts)
+    costs = [h["cost"] for h in r.history] + [r.final_cost]
+    assert all(a >= b for a, b in zip(costs, costs[1:]))
+    c, q = O.unpack(r.x, p.n_cams)
+    g_end = O.linearize(c, q, p.cam_idx, p.pt_idx, p.pixels, loss=loss, loss_scale=2.0).g
+    g0 = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, loss=loss, loss_scale=2.0).g
+    assert np.linalg.norm(g_end) <= 1e-6 * np.linalg.norm(g0)
