@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-schur", action="store_true")
     ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1, 2],
                     help="1: conditional-loop graph; 2: unrolled predicated graph; 0: host-enqueued sequence")
     return ap.parse_args()
@@ -410,6 +411,30 @@ def run_ours(args, rank, world, local_rank):
         except binding.BAError as e:
             fp64 = {"unavailable": str(e)}
 
+    # ---- the Schur-complement solver on the same problem (PCG on the camera system)
+    schur = None
+    if not args.no_schur:
+        so = binding.default_options(use_graph=args.graph_mode, solver=1)
+        p.set_params(cams0, pts0)
+        p.solve(so, wait=False)
+        torch.cuda.synchronize()
+        ms, pc = [], 0
+        for _ in range(max(1, min(3, args.steps))):
+            flush.fill_(5)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.set_params(cams0, pts0)
+            p.solve(so, wait=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            sst = p.stats()
+            pc += sst.pcg_iters_total
+        schur = {"ms_per_solve": sum(ms) / len(ms), "pcg_iters_per_solve": pc / len(ms),
+                 "pcg_iters_per_s": pc / (sum(ms) / 1e3), "final_cost": sst.final_cost,
+                 "time_to_cost_ms": time_to_cost(sst.history, target * (1 + 1e-4) if target else None)}
+
     batched = None if args.no_batch else run_batched(args, binding, synth, torch, dev, stream, flush, rank)
 
     launches_per_step = 1 + 3 + 5 * last.lm_iters + 3 * last.pcg_iters_total + 1
@@ -425,7 +450,7 @@ def run_ours(args, rank, world, local_rank):
         "time_to_cost_ms": ttc, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
         "step_ms": step_ms,
         "roofline": roofline, "roofline_matvec": other,
-        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "batched": batched, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "schur": schur, "batched": batched, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob)

@@ -94,6 +94,13 @@ typedef struct {
                                      IRLS-weighted system J^T W J + mu D, W = rho'(s) at
                                      the linearisation point.  Not in the batched mode.  */
     double loss_scale;            /* the loss's scale d in pixels, default 1              */
+    int32_t solver;               /* 0 (default): PCGNR on the full damped normal
+                                     equations (Sec. V); 1: PCG on the camera Schur
+                                     complement S = H'cc - Hcp H'pp^-1 Hpc with the points
+                                     back-substituted (the alternative Sec. V sets aside),
+                                     block-Jacobi on the camera blocks.  Mixed precision
+                                     only (BA_ERR_NOT_IMPLEMENTED for the FP64 form and
+                                     the batched mode).                                 */
 } ba_options;
 
 /* One LM iteration (Sec. V): cost before the step, candidate cost, damping used,

@@ -25,6 +25,8 @@ the paper (arXiv 2605.30583, "Caspar"):
                      R <- Exp(d) R (scipy's rotation composition), Jacobian w.r.t. d.
 * robust loss     -- robust factors (named in Sec. VI-A as an easy addition): Huber or
                      Cauchy on |r_o|^2 with IRLS weights rho'(|r_o|^2).
+* Schur PCG       -- the alternative Sec. V sets aside: PCG on the camera Schur
+                     complement, points back-substituted (schur_pcg).
 
 Readings where the paper is silent (all listed in the design notes): damping
 matrix D = diag(J^T J) clamped to [min_diag, max_diag]; mu_0 = 1 / trust region;
@@ -400,6 +402,55 @@ def pcgnr(J, D, mu, b, precond, tol=1e-3, max_iters=50):
     return PCGResult(h=h, iters=k, r0_norm=r0, r_norm=rn)
 
 
+def schur_pcg(lin: Linearization, D, mu, n_cams, tol=1e-3, max_iters=50):
+    """The damped step by the Schur complement on the cameras (the comparison the paper
+    sets aside in Sec. V): with H' = J^T J + mu D split into camera and point blocks,
+
+        S = H'_cc - H_cp H'_pp^-1 H_pc,   b = -g_c + H_cp H'_pp^-1 g_p,
+
+    S h_c = b is solved by PCG (matrix-free S v = J_c^T (J_c v - J_p H'_pp^-1 J_p^T J_c v)
+    + mu D_c v; block-Jacobi on the camera blocks of H'_cc; from h_c = 0, stopping when
+    |r_k|_2 <= tol |r_0|_2 of the reduced system or after max_iters iterations), then
+    h_p = H'_pp^-1 (-g_p - H_pc h_c)."""
+    nc9 = 9 * n_cams
+    J = lin.J.tocsc()
+    Jc, Jp = J[:, :nc9].tocsr(), J[:, nc9:].tocsr()
+    Dc, Dp = D[:nc9], D[nc9:]
+    Mc, Mp = block_jacobi(lin, D, mu)          # inverses of the camera / point blocks of H'
+    hpp_inv = lambda v: np.einsum("pij,pj->pi", Mp, v.reshape(-1, 3)).reshape(-1)
+    mc_apply = lambda v: np.einsum("cij,cj->ci", Mc, v.reshape(-1, 9)).reshape(-1)
+
+    def S(v):
+        t = Jc @ v
+        return Jc.T @ (t - Jp @ hpp_inv(Jp.T @ t)) + mu * Dc * v
+
+    gc, gp = lin.g[:nc9], lin.g[nc9:]
+    b = -gc + Jc.T @ (Jp @ hpp_inv(gp))
+    hc = np.zeros(nc9)
+    r = b.copy()
+    z = mc_apply(r)
+    p = z.copy()
+    rz = float(r @ z)
+    r0 = float(np.sqrt(r @ r))
+    rn = r0
+    k = 0
+    while k < max_iters and rn > tol * r0:
+        q = S(p)
+        alpha = rz / float(p @ q)
+        hc = hc + alpha * p
+        r = r - alpha * q
+        k += 1
+        rn = float(np.sqrt(r @ r))
+        if rn <= tol * r0:
+            break
+        z = mc_apply(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    hp = hpp_inv(-gp - Jp.T @ (Jc @ hc))
+    return PCGResult(h=np.concatenate([hc, hp]), iters=k, r0_norm=r0, r_norm=rn)
+
+
 # --------------------------------------------------------------------------------------
 # Levenberg-Marquardt with Madsen's quality-based damping (Sec. V)
 # --------------------------------------------------------------------------------------
@@ -418,6 +469,7 @@ class LMOptions:
     rotation_update: str = "additive"   # or "retraction": R <- Exp(d) R, J w.r.t. d
     loss: str = "squared"               # or "huber", "cauchy" (IRLS weights, see LOSSES)
     loss_scale: float = 1.0             # the loss's scale d, in pixels
+    solver: str = "pcgnr"               # or "schur": PCG on the Schur complement (schur_pcg)
 
 
 @dataclasses.dataclass
@@ -431,10 +483,12 @@ class LMResult:
     pcg_iters_total: int
 
 
-def lm_solve(x0, linearize_fn, cost_fn, make_precond, opts: LMOptions = LMOptions(), step_fn=None) -> LMResult:
+def lm_solve(x0, linearize_fn, cost_fn, make_precond, opts: LMOptions = LMOptions(), step_fn=None,
+             solve_fn=None) -> LMResult:
     """Generic LM over x.  linearize_fn(x) -> object with F, J (sparse) and g = J^T r;
     cost_fn(x) -> F; make_precond(lin, D, mu) -> callable applying the preconditioner;
-    step_fn(x, h) -> x' applies a step (default x + h).
+    step_fn(x, h) -> x' applies a step (default x + h); solve_fn(lin, D, mu) -> PCGResult
+    replaces PCGNR on the damped system (default: pcgnr with make_precond).
 
     One iteration: solve (J^T J + mu D) h = -g by PCGNR; x' = x + h;
     rho = (F - F') / (-g^T h - 1/2 |J h|^2).  If rho > 0 the step is accepted,
@@ -451,8 +505,11 @@ def lm_solve(x0, linearize_fn, cost_fn, make_precond, opts: LMOptions = LMOption
     it = 0
     while it < opts.max_lm_iters and lin.F > 0.0 and mu <= opts.max_mu:
         D = damping_diag(lin.J, opts.min_diag, opts.max_diag)
-        precond = make_precond(lin, D, mu)
-        res = pcgnr(lin.J, D, mu, -lin.g, precond, opts.pcg_rel_tol, opts.max_pcg_iters)
+        if solve_fn is None:
+            precond = make_precond(lin, D, mu)
+            res = pcgnr(lin.J, D, mu, -lin.g, precond, opts.pcg_rel_tol, opts.max_pcg_iters)
+        else:
+            res = solve_fn(lin, D, mu)
         h = res.h
         pcg_total += res.iters
         Jh = lin.J @ h
@@ -530,7 +587,12 @@ def ba_solve(cams0, pts0, cam_idx, pt_idx, pixels, opts: LMOptions = LMOptions()
         hc, hp = unpack(h, n_cams)
         return pack(retract_cams(c, hc), p + hp)
 
-    return lm_solve(pack(cams0, pts0), lin_fn, cost_fn, _ba_precond, opts, step_fn if retraction else None)
+    if opts.solver not in ("pcgnr", "schur"):
+        raise ValueError(opts.solver)
+    solve_fn = None
+    if opts.solver == "schur":
+        solve_fn = lambda lin, D, mu: schur_pcg(lin, D, mu, n_cams, opts.pcg_rel_tol, opts.max_pcg_iters)
+    return lm_solve(pack(cams0, pts0), lin_fn, cost_fn, _ba_precond, opts, step_fn if retraction else None, solve_fn)
 
 
 def normal_matvec(lin: Linearization, D, mu, v):

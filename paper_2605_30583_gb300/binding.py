@@ -32,7 +32,8 @@ class Options(ctypes.Structure):
                 ("pcg_rel_tol", ctypes.c_double), ("initial_trust_region", ctypes.c_double),
                 ("min_diag", ctypes.c_double), ("max_diag", ctypes.c_double), ("max_mu", ctypes.c_double),
                 ("eps_depth", ctypes.c_double), ("use_graph", ctypes.c_int32), ("pcg_kernel", ctypes.c_int32),
-                ("rotation_update", ctypes.c_int32), ("loss", ctypes.c_int32), ("loss_scale", ctypes.c_double)]
+                ("rotation_update", ctypes.c_int32), ("loss", ctypes.c_int32), ("loss_scale", ctypes.c_double),
+                ("solver", ctypes.c_int32)]
 
 
 class IterStat(ctypes.Structure):

@@ -1009,7 +1009,7 @@ DevOptions dev_options(const ba_options* o) {
 bool options_ok(const ba_options* o) {
     return o && o->max_lm_iters >= 0 && o->max_pcg_iters >= 0 && o->initial_trust_region > 0 && o->min_diag > 0 &&
            o->max_diag >= o->min_diag && o->pcg_rel_tol >= 0 && o->eps_depth >= 0 && o->max_mu > 0 &&
-           (o->rotation_update == 0 || o->rotation_update == 1) && o->loss == 0;
+           (o->rotation_update == 0 || o->rotation_update == 1) && o->loss == 0 && o->solver == 0;
 }
 
 // Launch of the solve: a captured graph (queue reset + persistent kernel), rebuilt
@@ -1321,8 +1321,8 @@ ba_status ba_batch_solve(ba_batch* B, const ba_options* o, ba_stats* stats) {
         set_error("ba_batch_solve: no workspace bound");
         return BA_ERR_STATE;
     }
-    if (o && o->loss != 0) {
-        set_error("ba_batch_solve: robust losses are not available in the batched mode");
+    if (o && (o->loss != 0 || o->solver != 0)) {
+        set_error("ba_batch_solve: robust losses and the Schur-complement solver are not available in the batched mode");
         return BA_ERR_NOT_IMPLEMENTED;
     }
     if (!options_ok(o)) {

@@ -174,7 +174,9 @@ template Views<double> make_views<double>(ba_problem*);
 //   pcg_iter  one PCG iteration (multi-kernel PCG only);
 //   lm_tail   candidate step, its evaluation and the LM decision, commit, relinearise.
 
-static bool inner_pcg(const ba_problem* p) { return !(p->precision == BA_PREC_MIXED && p->use_persistent); }
+static bool inner_pcg(const ba_problem* p) {
+    return !(p->precision == BA_PREC_MIXED && p->use_persistent) || p->use_schur;
+}
 
 static void step_init(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use) {
     if (p->precision == BA_PREC_MIXED) {
@@ -189,7 +191,11 @@ static void step_init(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use) {
 }
 
 static void step_pcg_iter(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int use) {
-    if (p->precision == BA_PREC_MIXED) {
+    if (p->precision == BA_PREC_MIXED && p->use_schur) {   // reduced camera system
+        const Views<float>& v = p->vf;
+        launch_schur(v, s, 1, &v.st->pcg_active);
+        launch_update(v, p->L, s, pcg_c, use, 1);
+    } else if (p->precision == BA_PREC_MIXED) {
         const Views<float>& v = p->vf;
         launch_matvec(v, p->L, s, &v.st->pcg_active, v.z, 1);
         launch_update(v, p->L, s, pcg_c, use);
@@ -202,7 +208,13 @@ static void step_pcg_iter(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int u
 }
 
 static void step_lm_head(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int use, bool inline_pcg, int max_pcg) {
-    if (p->precision == BA_PREC_MIXED) {
+    if (p->precision == BA_PREC_MIXED && p->use_schur) {
+        // blocks of H' (camera and point inverses, D), then the reduced right-hand side
+        const Views<float>& v = p->vf;
+        launch_precond(v, p->L, s, pcg_c, 0, nullptr);
+        launch_schur(v, s, 0, &v.st->lm_active);
+        launch_schur_start(v, p->L, s, pcg_c, use);
+    } else if (p->precision == BA_PREC_MIXED) {
         const Views<float>& v = p->vf;
         launch_precond(v, p->L, s, pcg_c, use, p->use_persistent ? p->pslots : nullptr);
         if (p->use_persistent)
@@ -217,6 +229,7 @@ static void step_lm_head(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int us
 static void step_lm_tail(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use) {
     if (p->precision == BA_PREC_MIXED) {
         const Views<float>& v = p->vf;
+        if (p->use_schur) launch_schur(v, s, 2, &v.st->lm_active);   // points back-substituted
         launch_candidate(v, p->L, s);
         launch_eval_candidate(v, p->L, s, lm_c, use);
         launch_commit(v, p->L, s);
@@ -362,6 +375,7 @@ ba_status ba_options_default(ba_options* o) {
     o->rotation_update = 0;
     o->loss = 0;
     o->loss_scale = 1.0;
+    o->solver = 0;
     return BA_OK;
 }
 
@@ -694,7 +708,7 @@ static ba_status check_options(const ba_options* o) {
         !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0) ||
         (o->pcg_kernel != 0 && o->pcg_kernel != 1) || o->use_graph < 0 || o->use_graph > 2 ||
         (o->rotation_update != 0 && o->rotation_update != 1) || o->loss < 0 || o->loss > 2 ||
-        !(o->loss_scale > 0)) {
+        !(o->loss_scale > 0) || (o->solver != 0 && o->solver != 1)) {
         set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive)");
         return BA_ERR_INVALID_ARG;
     }
@@ -752,11 +766,17 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
     ba_status st = check_bound(p, "ba_solve");
     if (st) return st;
     if ((st = check_options(o))) return st;
+    if (o->solver == 1 && p->precision != BA_PREC_MIXED) {
+        set_error("ba_solve: the Schur-complement solver is available for the mixed-precision form only");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
     if ((st = write_options(p, o))) return st;
-    const bool want_persistent = p->persistent && o->pcg_kernel == 0;
-    if (want_persistent != p->use_persistent) {   // cached graphs were built for the other PCG form
-        release_graph(p);
+    const bool want_schur = o->solver == 1;
+    const bool want_persistent = p->persistent && o->pcg_kernel == 0 && !want_schur;
+    if (want_persistent != p->use_persistent || want_schur != p->use_schur) {
+        release_graph(p);   // cached graphs were built for the other PCG form
         p->use_persistent = want_persistent;
+        p->use_schur = want_schur;
     }
     // A cooperative kernel cannot sit inside a conditional node, so with the persistent
     // PCG kernel the default graph is the fixed LM sequence (six kernels per LM step).

@@ -42,7 +42,11 @@ void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, C
                     double* pslots);
 void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                    const float* zs, int use_beta);
-void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
+void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
+                   int cameras_only = 0);
+// Schur-complement PCG (kernels_mixed.cu): mode 0 right-hand side, 1 operator, 2 back-substitution
+void launch_schur(const Views<float>& v, cudaStream_t s, int mode, const int32_t* gate);
+void launch_schur_start(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
 void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
 void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
 void launch_commit(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);

@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* ga
 // q = (J_l^T sum RX x u, sum u, intrinsic part) + mu D p from the K4 accumulators.
 // Points run four at a time with float4 accesses.  Never gated: its last block
 // decides whether PCG continues, sets the loop flag and clears the accumulators.
-__global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond) {
+__global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond, int cameras_only) {
     DevState* st = v.st;
     __shared__ double red[32];
     __shared__ double sh_mv[2];
@@ -516,7 +516,8 @@ __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond) {
                 rr = fmaf(rn[i], rn[i], rr);
             }
         }
-        for (int qd = blockIdx.x * blockDim.x + threadIdx.x; qd < v.n_quads; qd += gridDim.x * blockDim.x) {
+        for (int qd = blockIdx.x * blockDim.x + threadIdx.x; !cameras_only && qd < v.n_quads;
+             qd += gridDim.x * blockDim.x) {
             const size_t e = v.pt_off + 12 * (size_t)qd;
             float4* p4 = reinterpret_cast<float4*>(v.p + e);
             float4* h4 = reinterpret_cast<float4*>(v.h + e);
@@ -760,6 +761,248 @@ __global__ void k_commit(Views<float> v) {
     }
 }
 
+// ------------------------------------------------------------ Schur complement ---
+// PCG on the camera Schur complement (the alternative Sec. V sets aside):
+// S = H'cc - Hcp H'pp^-1 Hpc with H' = J^T W J + mu D (W the robust-loss weights, all
+// ones for the squared loss).  A tile holds every observation of its points, so the
+// point elimination is local to one tile CTA: pass 1 sums y_p = J_p^T W J_c d over the
+// tile (shared memory), z_p = H'pp^-1 y_p per point, pass 2 sums the camera parts
+// J_c^T W (J_c d - J_p z).  The camera PCG vectors use the camera segments of r z p h
+// and k_update in its cameras-only form.
+
+enum : int { SCHUR_RHS = 0, SCHUR_MV = 1, SCHUR_BACK = 2 };
+
+// t = J_c d for a camera direction record d (no point part)
+__device__ __forceinline__ void jc_apply(const GeoLite& g, const Cam& c, const float (&dir)[9], float& t0, float& t1) {
+    const float dP0 = fmaf(dir[1], g.RX[2], -dir[2] * g.RX[1]) + dir[CD_T + 0];
+    const float dP1 = fmaf(dir[2], g.RX[0], -dir[0] * g.RX[2]) + dir[CD_T + 1];
+    const float dP2 = fmaf(dir[0], g.RX[1], -dir[1] * g.RX[0]) + dir[CD_T + 2];
+    apply_A(g, dP0, dP1, dP2, t0, t1);
+    const float fn2 = c.f * g.n2;
+    const float ci = fmaf(g.s, dir[CD_I + 0], fmaf(fn2, dir[CD_I + 1], fn2 * g.n2 * dir[CD_I + 2]));
+    t0 = fmaf(ci, g.p[0], t0);
+    t1 = fmaf(ci, g.p[1], t1);
+}
+
+// t = J_p z = A R z
+__device__ __forceinline__ void jp_apply(const GeoLite& g, const Cam& c, const float* z, float& t0, float& t1) {
+    const float d0 = fmaf(c.R[0], z[0], fmaf(c.R[1], z[1], c.R[2] * z[2]));
+    const float d1 = fmaf(c.R[3], z[0], fmaf(c.R[4], z[1], c.R[5] * z[2]));
+    const float d2 = fmaf(c.R[6], z[0], fmaf(c.R[7], z[1], c.R[8] * z[2]));
+    apply_A(g, d0, d1, d2, t0, t1);
+}
+
+// y += J_p^T t = R^T A^T t (shared-memory atomics)
+__device__ __forceinline__ void jp_adjoint(const GeoLite& g, const Cam& c, float t0, float t1, float* y) {
+    float u0, u1, u2;
+    apply_At(g, t0, t1, u0, u1, u2);
+    atomicAdd(y + 0, fmaf(c.R[0], u0, fmaf(c.R[3], u1, c.R[6] * u2)));
+    atomicAdd(y + 1, fmaf(c.R[1], u0, fmaf(c.R[4], u1, c.R[7] * u2)));
+    atomicAdd(y + 2, fmaf(c.R[2], u0, fmaf(c.R[5], u1, c.R[8] * u2)));
+}
+
+// acc += J_c^T t, its rotation part w.r.t. phi (k_update and k_schur_start apply J_l^T)
+__device__ __forceinline__ void jc_adjoint(const GeoLite& g, const Cam& c, float t0, float t1, float (&acc)[9]) {
+    float u0, u1, u2;
+    apply_At(g, t0, t1, u0, u1, u2);
+    acc[0] += fmaf(g.RX[1], u2, -g.RX[2] * u1);
+    acc[1] += fmaf(g.RX[2], u0, -g.RX[0] * u2);
+    acc[2] += fmaf(g.RX[0], u1, -g.RX[1] * u0);
+    acc[3] += u0;
+    acc[4] += u1;
+    acc[5] += u2;
+    const float pt = fmaf(g.p[0], t0, g.p[1] * t1);
+    const float fn2 = c.f * g.n2;
+    acc[6] = fmaf(g.s, pt, acc[6]);
+    acc[7] = fmaf(fn2, pt, acc[7]);
+    acc[8] = fmaf(fn2 * g.n2, pt, acc[8]);
+}
+
+// MODE SCHUR_RHS:  camera sums of J_c^T W J_p (H'pp^-1 g_p)      -> cam_acc
+//      SCHUR_MV:   camera sums of J_c^T W (J_c p - J_p z)         -> cam_acc, and the
+//                  slot sums sum w |J_c p|^2 - sum y^T z, p_c^T D_c p_c (alpha's denominator)
+//      SCHUR_BACK: h_p = H'pp^-1 (-g_p - J_p^T W J_c h_c)
+template <int TB, int MODE>
+__global__ void __launch_bounds__(TB) k_schur(Views<float> v, const int32_t* gate) {
+    if (gated_off(gate)) return;
+    __shared__ float sx[3 * TILE_PTS], sy[3 * TILE_PTS];
+    __shared__ double red[32];
+    DevState* st = v.st;
+    const float eps = (float)st->opt.eps;
+    const bool weighted = st->opt.loss != 0;
+    const int par = st->pcg_iter & 1;
+    const float beta = MODE == SCHUR_MV ? (float)st->beta : 0.0f;
+    const float* pc_old = v.pc + (size_t)par * v.pc_stride;
+    float* pc_new = v.pc + (size_t)(par ^ 1) * v.pc_stride;
+    const float* dsrc = MODE == SCHUR_MV ? v.z : v.h;   // camera direction source (with beta, pc_old)
+    float tt = 0.0f, yz = 0.0f, pdp = 0.0f;
+    if (MODE == SCHUR_MV)   // camera part of p owned by this CTA
+        for (int c = blockIdx.x; c < v.n_cams; c += gridDim.x)
+            if (threadIdx.x < 9) {
+                const size_t e = 9 * (size_t)c + threadIdx.x;
+                const float pk = beta != 0.0f ? fmaf(beta, pc_old[e], v.z[e]) : v.z[e];
+                pc_new[e] = pk;
+                pdp = fmaf(v.D[e] * pk, pk, pdp);
+            }
+    for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
+        const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
+        const int pt0 = tile * TILE_PTS;
+        const int npt = min(TILE_PTS, v.n_pts - pt0);
+        const size_t base = v.pt_off + 3 * (size_t)pt0;
+        for (int i = threadIdx.x; i < 3 * npt; i += TB) {
+            sx[i] = v.x[base + i];
+            sy[i] = 0.0f;
+        }
+        if (MODE == SCHUR_RHS)   // z_p = H'pp^-1 g_p
+            for (int i = threadIdx.x; i < npt; i += TB) {
+                const float* m = v.Minv_p + 6 * (size_t)(pt0 + i);
+                const float g0 = v.g[base + 3 * i], g1 = v.g[base + 3 * i + 1], g2 = v.g[base + 3 * i + 2];
+                sy[3 * i] = fmaf(m[0], g0, fmaf(m[1], g1, m[2] * g2));
+                sy[3 * i + 1] = fmaf(m[1], g0, fmaf(m[3], g1, m[4] * g2));
+                sy[3 * i + 2] = fmaf(m[2], g0, fmaf(m[4], g1, m[5] * g2));
+            }
+        __syncthreads();
+        const uint32_t n = hi - lo;
+        const uint32_t chunk = (n + TB - 1) / TB;
+        const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
+        if (MODE != SCHUR_RHS) {
+            // pass 1: y_p = sum J_p^T W J_c d
+            uint32_t cur = NO_CAM;
+            Cam cam;
+            float dir[9];
+            for (uint32_t j = a; j < b; ++j) {
+                const uint32_t key = __ldg(v.obs_key + j);
+                const uint32_t c = key >> 8, slot = key & 0xffu;
+                if (c != cur) {
+                    cur = c;
+                    cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+                    camera_dir(v, c, dsrc, pc_old, beta, dir);
+                }
+                const GeoLite g = project_lite(cam, sx[3 * slot], sx[3 * slot + 1], sx[3 * slot + 2], eps);
+                float t0, t1;
+                jc_apply(g, cam, dir, t0, t1);
+                const float w = weighted ? __ldg(v.obs_w + j) : 1.0f;
+                tt = fmaf(w, fmaf(t0, t0, t1 * t1), tt);
+                jp_adjoint(g, cam, w * t0, w * t1, sy + 3 * slot);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < npt; i += TB) {
+                const float* m = v.Minv_p + 6 * (size_t)(pt0 + i);
+                const float y0 = sy[3 * i], y1 = sy[3 * i + 1], y2 = sy[3 * i + 2];
+                if (MODE == SCHUR_MV) {   // z_p = H'pp^-1 y_p
+                    const float z0 = fmaf(m[0], y0, fmaf(m[1], y1, m[2] * y2));
+                    const float z1 = fmaf(m[1], y0, fmaf(m[3], y1, m[4] * y2));
+                    const float z2 = fmaf(m[2], y0, fmaf(m[4], y1, m[5] * y2));
+                    yz = fmaf(y0, z0, fmaf(y1, z1, fmaf(y2, z2, yz)));
+                    sy[3 * i] = z0;
+                    sy[3 * i + 1] = z1;
+                    sy[3 * i + 2] = z2;
+                } else {                  // h_p = H'pp^-1 (-g_p - y_p)
+                    const float b0 = -v.g[base + 3 * i] - y0, b1 = -v.g[base + 3 * i + 1] - y1;
+                    const float b2 = -v.g[base + 3 * i + 2] - y2;
+                    v.h[base + 3 * i] = fmaf(m[0], b0, fmaf(m[1], b1, m[2] * b2));
+                    v.h[base + 3 * i + 1] = fmaf(m[1], b0, fmaf(m[3], b1, m[4] * b2));
+                    v.h[base + 3 * i + 2] = fmaf(m[2], b0, fmaf(m[4], b1, m[5] * b2));
+                }
+            }
+            __syncthreads();
+        }
+        if (MODE != SCHUR_BACK) {
+            // pass 2: camera sums of J_c^T W s, s = J_c d - J_p z (operator) or J_p z (RHS)
+            uint32_t cur = NO_CAM;
+            float acc[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+            Cam cam;
+            float dir[9];
+            for (uint32_t j = a; j < b; ++j) {
+                const uint32_t key = __ldg(v.obs_key + j);
+                const uint32_t c = key >> 8, slot = key & 0xffu;
+                if (c != cur) {
+                    if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
+                    cur = c;
+                    cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+                    if (MODE == SCHUR_MV) camera_dir(v, c, dsrc, pc_old, beta, dir);
+                }
+                const GeoLite g = project_lite(cam, sx[3 * slot], sx[3 * slot + 1], sx[3 * slot + 2], eps);
+                float s0, s1;
+                jp_apply(g, cam, sy + 3 * slot, s0, s1);
+                if (MODE == SCHUR_MV) {
+                    float t0, t1;
+                    jc_apply(g, cam, dir, t0, t1);
+                    s0 = t0 - s0;
+                    s1 = t1 - s1;
+                }
+                const float w = weighted ? __ldg(v.obs_w + j) : 1.0f;
+                jc_adjoint(g, cam, w * s0, w * s1, acc);
+            }
+            const bool head = seg_reduce<9>(cur, acc);
+            if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
+        }
+        __syncthreads();
+    }
+    if (MODE == SCHUR_MV) {
+        const double bj = block_sum((double)tt - (double)yz, red);
+        const double bp = block_sum((double)pdp, red);
+        if (threadIdx.x == 0) {
+            slot_add(st->acc_mv, 0, bj);
+            slot_add(st->acc_mv, 1, bp);
+        }
+    }
+}
+
+// Start of the reduced PCG: r_c = -g_c + (camera sums of the right-hand-side pass),
+// z = M_c^-1 r (the camera blocks of H'), p = h_c = 0; scalars as k_precond sets them.
+__global__ void k_schur_start(Views<float> v, CondHandle pcg_cond, int use_cond) {
+    DevState* st = v.st;
+    if (st->lm_active == 0) {
+        if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(pcg_cond, 0u);
+        return;
+    }
+    double rz = 0.0, rr = 0.0;
+    FOR_CAMERAS(c, v) {
+        const size_t e = 9 * (size_t)c;
+        float* ca = v.cam_acc + (size_t)c * CA_STRIDE;
+        const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
+        const double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
+        float q[9], rn[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) q[k] = fmaf(JL[k], ca[0], fmaf(JL[3 + k], ca[1], JL[6 + k] * ca[2]));
+#pragma unroll
+        for (int k = 3; k < 9; ++k) q[k] = ca[k];
+#pragma unroll
+        for (int k = 0; k < CA_STRIDE; ++k) ca[k] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            rn[k] = (float)(-cl[CL_G + k]) + q[k];
+            v.r[e + k] = rn[k];
+            v.p[e + k] = 0.0f;
+            v.h[e + k] = 0.0f;
+        }
+        const float* M = v.Minv_c + (size_t)c * MC_STRIDE;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float z = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) z = fmaf(M[9 * i + k], rn[k], z);
+            v.z[e + i] = z;
+            rz += (double)rn[i] * (double)z;
+            rr += (double)rn[i] * (double)rn[i];
+        }
+    }
+    double in[2] = {rz, rr}, out[2];
+    if (grid_reduce<2>(in, v.partials, &st->tickets[TK_PRE], out) && threadIdx.x == 0) {
+        st->rz = out[0];
+        st->rr0 = out[1];
+        st->rr = out[1];
+        st->beta = 0.0;
+        st->pcg_iter = 0;
+        for (int k = 0; k < NSLOT * SLOT_STRIDE; ++k) st->acc_mv[k] = st->acc_up[k] = 0.0;
+        st->pcg_active = (out[1] > 0.0 && isfinite(out[0]) && st->opt.max_pcg > 0) ? 1 : 0;
+        if (use_cond) cudaGraphSetConditional(pcg_cond, st->pcg_active ? 1u : 0u);
+    }
+}
+
 // ------------------------------------------------------------- state / misc ---
 
 __global__ void k_init_state(DevState* st) {
@@ -873,8 +1116,18 @@ void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, co
     (void)L;
     k_matvec<MV_TB><<<v.n_tiles > 0 ? v.n_tiles : 1, MV_TB, 0, s>>>(v, gate, zs, use_beta);
 }
-void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
-    k_update<<<grid_items(L, v.n_quads), L.item_block, 0, s>>>(v, c, use);
+void launch_schur(const Views<float>& v, cudaStream_t s, int mode, const int32_t* gate) {
+    const int grid = v.n_tiles > 0 ? v.n_tiles : 1;
+    if (mode == SCHUR_RHS) k_schur<MV_TB, SCHUR_RHS><<<grid, MV_TB, 0, s>>>(v, gate);
+    else if (mode == SCHUR_MV) k_schur<MV_TB, SCHUR_MV><<<grid, MV_TB, 0, s>>>(v, gate);
+    else k_schur<MV_TB, SCHUR_BACK><<<grid, MV_TB, 0, s>>>(v, gate);
+}
+void launch_schur_start(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
+    k_schur_start<<<grid_items(L, v.n_cams), L.item_block, 0, s>>>(v, c, use);
+}
+void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
+                   int cameras_only) {
+    k_update<<<grid_items(L, cameras_only ? v.n_cams : v.n_quads), L.item_block, 0, s>>>(v, c, use, cameras_only);
 }
 void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s) {
     k_candidate<<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v);

@@ -64,6 +64,7 @@ struct ba_problem {
     // persistent PCG plan (mixed precision, problems whose tiles fit in shared memory)
     bool persistent = false;        // the plan fits
     bool use_persistent = false;    // the plan is used by the current solve sequences
+    bool use_schur = false;         // the current solve sequences use the Schur-complement PCG
     int p_grid = 0, p_smem = 0;
     uint32_t* blk_tile = nullptr;   // device, [p_grid + 1]
     uint32_t* blk_cam_off = nullptr;   // device, [p_grid + 1]: per-CTA camera list offsets

@@ -32,6 +32,8 @@ MUTATIONS = {
     "retraction_step_on_the_right": ("rotate(w, rotate(base_w, X))", "rotate(base_w, rotate(w, X))"),
     "huber_weight_power": ("scale / np.sqrt(np.maximum(s, d2))", "scale / np.maximum(s, d2)"),
     "cauchy_weight_squared": ("return 1.0 / (1.0 + s / d2)", "return 1.0 / (1.0 + s / d2) ** 2"),
+    "schur_rhs_sign": ("b = -gc + Jc.T @ (Jp @ hpp_inv(gp))", "b = -gc - Jc.T @ (Jp @ hpp_inv(gp))"),
+    "schur_backsub_sign": ("hp = hpp_inv(-gp - Jp.T @ (Jc @ hc))", "hp = hpp_inv(-gp + Jp.T @ (Jc @ hc))"),
 }
 
 

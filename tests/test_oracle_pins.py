@@ -460,3 +460,47 @@ def test_robust_lm_is_monotone_and_reaches_a_stationary_point(loss):
     g_end = O.linearize(c, q, p.cam_idx, p.pt_idx, p.pixels, loss=loss, loss_scale=2.0).g
     g0 = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, loss=loss, loss_scale=2.0).g
     assert np.linalg.norm(g_end) <= 1e-6 * np.linalg.norm(g0)
+
+
+# ---------------------------------------------------------------- Schur PCG -------
+
+
+def _dense_damped(lin, D, mu):
+    H = (lin.J.T @ lin.J).toarray()
+    return H + mu * np.diag(D)
+
+
+def test_schur_operator_is_the_dense_schur_complement():
+    p = _small_problem(seed=48, n_cams=3, n_pts=15)
+    lin = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+    D = O.damping_diag(lin.J)
+    mu = 0.05
+    A = _dense_damped(lin, D, mu)
+    nc9 = 9 * p.n_cams
+    S_dense = A[:nc9, :nc9] - A[:nc9, nc9:] @ np.linalg.solve(A[nc9:, nc9:], A[nc9:, :nc9])
+    # the reduced solve equals the dense Schur system's solution
+    res = O.schur_pcg(lin, D, mu, p.n_cams, tol=1e-14, max_iters=500)
+    b = -lin.g[:nc9] + A[:nc9, nc9:] @ np.linalg.solve(A[nc9:, nc9:], lin.g[nc9:])
+    hc = np.linalg.solve(S_dense, b)
+    assert np.allclose(res.h[:nc9], hc, rtol=1e-9, atol=1e-12 * np.abs(hc).max())
+
+
+def test_schur_solve_equals_the_dense_direct_solve_of_the_damped_system():
+    p = _small_problem(seed=49, n_cams=3, n_pts=20)
+    lin = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+    D = O.damping_diag(lin.J)
+    for mu in (1e-3, 0.3):
+        A = _dense_damped(lin, D, mu)
+        h = np.linalg.solve(A, -lin.g)
+        res = O.schur_pcg(lin, D, mu, p.n_cams, tol=1e-14, max_iters=500)
+        assert np.linalg.norm(res.h - h) <= 1e-9 * np.linalg.norm(h)
+
+
+def test_lm_schur_reaches_the_pcgnr_optimum():
+    p = _small_problem(seed=50, n_cams=4, n_pts=40)
+    out = {}
+    for sv in ("pcgnr", "schur"):
+        opts = O.LMOptions(max_lm_iters=60, max_pcg_iters=400, pcg_rel_tol=1e-10, solver=sv)
+        out[sv] = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, opts)
+    a, b = out["pcgnr"].final_cost, out["schur"].final_cost
+    assert abs(a - b) <= 1e-9 * a
