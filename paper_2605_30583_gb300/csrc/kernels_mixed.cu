@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                                                   CondHandle lm_cond, int use_cond) {
     if (mode == 1 && v.st->relin == 0) return;
     __shared__ float4 sx[TILE_PTS];
+    __shared__ float sg[3 * TILE_PTS], sh[6 * TILE_PTS];   // the tile's points: J_p^T r, J_p^T J_p
     const float eps = (float)v.st->opt.eps;
     // robust loss (evaluation, mode 2, is always the squared loss)
     const int loss = mode == 2 ? 0 : v.st->opt.loss;
@@ -83,10 +84,16 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
         const int npt = min(TILE_PTS, v.n_pts - pt0);
         const size_t base = v.pt_off + 3 * (size_t)pt0;
         __syncthreads();
-        for (int i = threadIdx.x; i < npt; i += TB)
+        for (int i = threadIdx.x; i < npt; i += TB) {
             sx[i] = make_float4(v.x[base + 3 * i], v.x[base + 3 * i + 1], v.x[base + 3 * i + 2], 0.0f);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) sg[3 * i + q] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) sh[6 * i + q] = 0.0f;
+        }
         __syncthreads();
-        // ---- camera pass
+        // one pass over the tile's camera-sorted observations: camera sums in registers
+        // (one flush per camera run), the tile's point sums in shared memory
         {
             const uint32_t n = hi - lo;
             const uint32_t chunk = (n + TB - 1) / TB;
@@ -128,6 +135,12 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                 const float fn2 = cam.f * g.n2;
                 j0[6] = g.s * g.p[0]; j0[7] = fn2 * g.p[0]; j0[8] = fn2 * g.n2 * g.p[0];
                 j1[6] = g.s * g.p[1]; j1[7] = fn2 * g.p[1]; j1[8] = fn2 * g.n2 * g.p[1];
+                float jx0[3], jx1[3];   // point Jacobian rows J_X = A R
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    jx0[q] = fmaf(g.A[0], cam.R[q], fmaf(g.A[1], cam.R[3 + q], g.A[2] * cam.R[6 + q]));
+                    jx1[q] = fmaf(g.A[3], cam.R[q], fmaf(g.A[4], cam.R[3 + q], g.A[5] * cam.R[6 + q]));
+                }
                 if (mode == 2) {   // evaluation output: the unweighted residual and Jacobian
                     const uint32_t o = v.obs_user[j];
                     if (res_out) { res_out[2 * (size_t)o] = r0; res_out[2 * (size_t)o + 1] = r1; }
@@ -135,16 +148,24 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                         float* Jo = jac_out + 24 * (size_t)o;
 #pragma unroll
                         for (int k = 0; k < 9; ++k) { Jo[k] = j0[k]; Jo[12 + k] = j1[k]; }
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) { Jo[9 + q] = jx0[q]; Jo[21 + q] = jx1[q]; }
                     }
                 }
+                const float s2 = fmaf(r0, r0, r1 * r1);
                 if (loss) {   // IRLS weight w = rho'(|r|^2): rows scaled by sqrt(w)
-                    const float w = loss_weight(fmaf(r0, r0, r1 * r1), loss, lscale);
+                    const float w = loss_weight(s2, loss, lscale);
                     if (mode != 2) v.obs_w[j] = w;
+                    cost += loss_rho(s2, loss, lscale);
                     const float sw = sqrtf(w);
                     r0 *= sw;
                     r1 *= sw;
 #pragma unroll
                     for (int k = 0; k < 9; ++k) { j0[k] *= sw; j1[k] *= sw; }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) { jx0[q] *= sw; jx1[q] *= sw; }
+                } else {
+                    cost += s2;
                 }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) acc[CL_G + i] = fmaf(j0[i], r0, fmaf(j1[i], r1, acc[CL_G + i]));
@@ -155,61 +176,26 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
                         const int t = 9 + tri_index(9, i, k);
                         acc[t] = fmaf(j0[i], j0[k], fmaf(j1[i], j1[k], acc[t]));
                     }
+                float* gq = sg + 3 * slot;
+                float* hq = sh + 6 * slot;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) atomicAdd(gq + q, fmaf(jx0[q], r0, jx1[q] * r1));
+#pragma unroll
+                for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+                    for (int b2 = a2; b2 < 3; ++b2)
+                        atomicAdd(hq + tri_index(3, a2, b2), fmaf(jx0[a2], jx0[b2], jx1[a2] * jx1[b2]));
             }
             // camera sums: combine lanes of the same camera, one set of atomics per run
             const bool head = seg_reduce<LIN_ACC>(cur, acc);
             if (head && cur != NO_CAM) flush_lin(v, cur, acc);
         }
-        // ---- point pass: one thread per point, its observations in point-major order
+        __syncthreads();
         for (int i = threadIdx.x; i < npt; i += TB) {
-            const int ip = pt0 + i;
-            const float4 X = sx[i];
-            float gp[3] = {0.0f, 0.0f, 0.0f}, hp[6] = {0, 0, 0, 0, 0, 0};
-            const uint32_t k0 = __ldg(v.pt_obs_off + ip), k1 = __ldg(v.pt_obs_off + ip + 1);
-            for (uint32_t k = k0; k < k1; ++k) {
-                const uint32_t j = __ldg(v.obs_pm + k);
-                const uint32_t c = __ldg(v.obs_key + j) >> 8;
-                const Cam cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
-                const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
-                const float fs = cam.f * g.s;
-                float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
-                float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
-                float jx0[3], jx1[3];   // J_X = A R
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    jx0[q] = fmaf(g.A[0], cam.R[q], fmaf(g.A[1], cam.R[3 + q], g.A[2] * cam.R[6 + q]));
-                    jx1[q] = fmaf(g.A[3], cam.R[q], fmaf(g.A[4], cam.R[3 + q], g.A[5] * cam.R[6 + q]));
-                }
-                if (mode == 2 && jac_out) {
-                    float* Jo = jac_out + 24 * (size_t)v.obs_user[j];
+            for (int q = 0; q < 3; ++q) v.g[base + 3 * i + q] = sg[3 * i + q];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) { Jo[9 + q] = jx0[q]; Jo[21 + q] = jx1[q]; }
-                }
-                if (loss) {
-                    const float s2 = fmaf(r0, r0, r1 * r1);
-                    cost += loss_rho(s2, loss, lscale);
-                    const float sw = sqrtf(loss_weight(s2, loss, lscale));
-                    r0 *= sw;
-                    r1 *= sw;
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) { jx0[q] *= sw; jx1[q] *= sw; }
-                } else {
-                    cost = fmaf(r0, r0, fmaf(r1, r1, cost));
-                }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) gp[q] = fmaf(jx0[q], r0, fmaf(jx1[q], r1, gp[q]));
-#pragma unroll
-                for (int a2 = 0; a2 < 3; ++a2)
-#pragma unroll
-                    for (int b2 = a2; b2 < 3; ++b2) {
-                        const int t = tri_index(3, a2, b2);
-                        hp[t] = fmaf(jx0[a2], jx0[b2], fmaf(jx1[a2], jx1[b2], hp[t]));
-                    }
-            }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) v.g[base + 3 * i + q] = gp[q];
-#pragma unroll
-            for (int q = 0; q < PH_STRIDE; ++q) v.pt_H[(size_t)ip * PH_STRIDE + q] = hp[q];
+            for (int q = 0; q < PH_STRIDE; ++q) v.pt_H[(size_t)(pt0 + i) * PH_STRIDE + q] = sh[6 * i + q];
         }
     }
     double in[1] = {(double)cost}, out[1];
