@@ -75,9 +75,15 @@ typedef struct {
                                      2: one graph of the fixed sequence of max_lm_iters x
                                      max_pcg_iters slots, idle slots return at once;
                                      0: the same sequence launched from the host    */
-    int32_t pcg_kernel;           /* 0: one persistent cooperative kernel per PCG solve when
-                                     every CTA's tiles fit in shared memory (default);
-                                     1: separate kernels per PCG iteration           */
+    int32_t pcg_kernel;           /* 0 (default): one persistent cooperative kernel per PCG
+                                     solve when every CTA's tiles fit in shared memory,
+                                     with two grid-wide exchanges per iteration;
+                                     1: separate kernels per PCG iteration (also used
+                                     when the persistent plan does not fit);
+                                     2: the persistent kernel with the recurrences
+                                     arranged so that one exchange per iteration carries
+                                     both inner products (same iterates in exact
+                                     arithmetic; its updated residual drifts sooner)  */
     int32_t rotation_update;      /* how a step updates each camera's rotation:
                                      0 (default): additive angle-axis, w <- w + dw, the
                                      Jacobian taken w.r.t. w (through the left Jacobian

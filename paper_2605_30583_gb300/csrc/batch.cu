@@ -156,7 +156,7 @@ __device__ __forceinline__ void b_flush_lin(const BatchView& b, int gc, float (&
 // thread.
 __device__ double b_linearize(const BatchView& b, const Prob& P, float eps, double* sh) {
     {
-        const int64_t chunk = (P.no + blockDim.x - 1) / blockDim.x;
+        const int64_t chunk = odd_chunk<int64_t>(P.no, (int64_t)blockDim.x);
         const int64_t a = min(P.o0 + (int64_t)threadIdx.x * chunk, P.o0 + P.no), e = min(a + chunk, P.o0 + P.no);
         uint32_t cur = NO_CAM;
         float acc[BLIN];
@@ -438,7 +438,7 @@ __device__ int b_pcg(const BatchView& b, const Prob& P, double mu, double rz, do
         // other lanes'), keys fetched one group of four ahead
         float jp2 = 0.0f;
         {
-            const int64_t chunk = (P.no + TB - 1) / TB;
+            const int64_t chunk = odd_chunk<int64_t>(P.no, (int64_t)TB);
             const int64_t a = min(P.o0 + (int64_t)tid * chunk, P.o0 + P.no), e = min(a + chunk, P.o0 + P.no);
             uint32_t cur = NO_CAM;
             float acc[9];

@@ -74,11 +74,12 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     l.staging = b.take(8 * (9 * nc + 3 * np));
     l.blk_tile = b.take(4 * (MAX_PBLOCKS + 1));
     l.blk_cam_off = b.take(4 * (MAX_PBLOCKS + 1));
-    // per-CTA camera lists of the persistent PCG kernel: each CTA lists at most the
-    // cameras of its observations, so n_obs + MAX_PBLOCKS entries always suffice; the
-    // plan is only used when they fit in shared memory, so cap the region
-    l.blk_cams = b.take(4 * std::min(no + MAX_PBLOCKS, (size_t)(MAX_PBLOCKS * 4096)));
-    l.pslots = b.take(8 * PSLOT_DOUBLES);
+    // per-CTA camera lists of the persistent PCG kernel: each CTA lists the cameras of
+    // its observations, and every camera no observation sees is listed once, so
+    // n_obs + n_cams + MAX_PBLOCKS entries always suffice; the plan is only used when
+    // they fit in shared memory, so cap the region
+    l.blk_cams = b.take(4 * std::min(no + nc + MAX_PBLOCKS, (size_t)(MAX_PBLOCKS * 4096)));
+    l.pslots = b.take(8 * PSLOT_TOTAL);
     const size_t union_base = align_up(b.off, 256);
     // solver arrays
     Bump s;
@@ -87,7 +88,7 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     l.cam_pre = s.take(4 * CP_STRIDE * nc);
     l.cam_pre_new = s.take(4 * CP_STRIDE * nc);
     l.cam_dir = s.take(4 * CD_STRIDE * nc);
-    l.cam_acc = s.take(4 * CA_STRIDE * nc);
+    l.cam_acc = s.take(4 * CA_STRIDE * nc * CA_SETS);
     l.pc = s.take(4 * 2 * pc_stride);
     l.cam_lin = s.take(8 * CL_STRIDE * nc);
     l.cam_H = s.take(4 * CH_STRIDE * nc);
@@ -218,7 +219,8 @@ static void step_lm_head(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int us
         const Views<float>& v = p->vf;
         launch_precond(v, p->L, s, pcg_c, use, p->use_persistent ? p->pslots : nullptr);
         if (p->use_persistent)
-            launch_pcg_persistent(v, p->blk_tile, p->blk_cam_off, p->blk_cams, p->pslots, p->p_grid, p->p_smem, s);
+            launch_pcg_persistent(v, p->blk_tile, p->blk_cam_off, p->blk_cams, p->pslots, p->p_grid,
+                                  p->p_form == PCG_TWO_EXCHANGE ? p->p_smem_two : p->p_smem_one, p->p_form, s);
     } else {
         launch64_precond(p->vd, p->L, s, pcg_c, use);
     }
@@ -474,7 +476,9 @@ static ba_status check_bound(const ba_problem* p, const char* who) {
 static ba_status write_options(ba_problem* p, const ba_options* o);
 
 // Persistent PCG plan: one CTA per SM, contiguous tile runs balanced by observation
-// count; used only when every CTA's keys and point state fit in its shared memory.
+// count; a form is used only when every CTA's keys and point state fit in its shared
+// memory.  Each CTA lists the cameras of its observations; a camera that no
+// observation sees is listed by CTA c % G, and the first list holding a camera owns it.
 static ba_status plan_persistent(ba_problem* p, int sms) {
     const int nt = p->n_tiles;
     std::vector<uint32_t> off((size_t)nt + 1);
@@ -502,34 +506,61 @@ static ba_status plan_persistent(ba_problem* p, int sms) {
     size_t worst = 0;
     for (int b = 0; b < G; ++b) worst = std::max(worst, point_bytes(b));
     if (worst > limit) return BA_OK;   // too large: the multi-kernel PCG path is used
-    // distinct cameras of each CTA's observations (sorted)
+    // distinct cameras of each CTA's observations (sorted), then the unseen ones
     std::vector<uint32_t> keys((size_t)p->n_obs);
     GBBA_CUDA(cudaMemcpy(keys.data(), p->vf.obs_key, 4 * keys.size(), cudaMemcpyDeviceToHost));
-    std::vector<uint32_t> coff((size_t)G + 1, 0), cams;
+    std::vector<std::vector<uint32_t>> lists((size_t)G);
+    std::vector<char> seen((size_t)p->n_cams, 0);
     for (int b = 0; b < G; ++b) {
-        std::vector<uint32_t> cb;
+        std::vector<uint32_t>& cb = lists[b];
         for (uint32_t j = off[bt[b]]; j < off[bt[b + 1]]; ++j) cb.push_back(keys[j] >> 8);
         std::sort(cb.begin(), cb.end());
         cb.erase(std::unique(cb.begin(), cb.end()), cb.end());
-        cams.insert(cams.end(), cb.begin(), cb.end());
-        coff[b + 1] = (uint32_t)cams.size();
-        const size_t bytes = point_bytes(b) + 4 * ((cb.size() + 3) & ~(size_t)3) + 4 * 28 * cb.size();
-        worst = std::max(worst, bytes);
+        for (uint32_t c : cb) seen[c] = 1;
     }
-    if (worst > limit) return BA_OK;
+    for (int c = 0; c < p->n_cams; ++c)
+        if (!seen[c]) {
+            std::vector<uint32_t>& cb = lists[c % G];
+            cb.insert(std::upper_bound(cb.begin(), cb.end(), (uint32_t)c), (uint32_t)c);
+        }
+    std::fill(seen.begin(), seen.end(), 0);
+    std::vector<uint32_t> coff((size_t)G + 1, 0), cams;
+    size_t worst_one = 0, worst_two = 0;
+    for (int b = 0; b < G; ++b) {
+        for (uint32_t c : lists[b]) {
+            cams.push_back(seen[c] ? c : (c | BLK_CAM_OWNER));
+            seen[c] = 1;
+        }
+        coff[b + 1] = (uint32_t)cams.size();
+        const size_t ncb = lists[b].size();
+        const size_t no = off[bt[b + 1]] - off[bt[b]];
+        const long pb = (long)bt[b] * TILE_PTS, pe = std::min((long)bt[b + 1] * TILE_PTS, (long)p->n_pts);
+        const size_t np = pe > pb ? (size_t)(pe - pb) : 0;
+        worst_two = std::max(worst_two, point_bytes(b) + 4 * ((ncb + 3) & ~(size_t)3) + 4 * 28 * ncb);
+        worst_one = std::max(worst_one, pcg1_smem_bytes(no, np, ncb));
+    }
     const size_t cap = (p->lay.pslots - p->lay.blk_cams) / 4;
     if (cams.size() > cap) return BA_OK;
-    int bps = 0;
-    if (persistent_prepare((int)worst, &bps) != cudaSuccess || bps < 1) {
-        cudaGetLastError();
-        return BA_OK;
-    }
+    auto fits = [&](int form, size_t bytes) {
+        int bps = 0;
+        if (bytes > limit) return false;
+        if (persistent_prepare(form, (int)bytes, &bps) != cudaSuccess || bps < 1) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    };
+    p->fits_one = fits(PCG_ONE_EXCHANGE, worst_one);
+    p->fits_two = fits(PCG_TWO_EXCHANGE, worst_two);
+    if (!p->fits_one && !p->fits_two) return BA_OK;
     GBBA_CUDA(cudaMemcpy(p->blk_tile, bt.data(), 4 * bt.size(), cudaMemcpyHostToDevice));
     GBBA_CUDA(cudaMemcpy(p->blk_cam_off, coff.data(), 4 * coff.size(), cudaMemcpyHostToDevice));
     GBBA_CUDA(cudaMemcpy(p->blk_cams, cams.data(), 4 * cams.size(), cudaMemcpyHostToDevice));
     p->persistent = true;
     p->p_grid = G;
-    p->p_smem = (int)worst;
+    p->p_smem_one = (int)worst_one;
+    p->p_smem_two = (int)worst_two;
+    p->p_form = p->fits_two ? PCG_TWO_EXCHANGE : PCG_ONE_EXCHANGE;
     return BA_OK;
 }
 
@@ -601,7 +632,7 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
     p->blk_cam_off = (uint32_t*)(w + l.blk_cam_off);
     p->blk_cams = (uint32_t*)(w + l.blk_cams);
     p->pslots = (double*)(w + l.pslots);
-    p->persistent = false;
+    p->persistent = p->fits_one = p->fits_two = false;
     if (p->precision == BA_PREC_MIXED) {
         ba_status pst = plan_persistent(p, sms);
         if (pst) return pst;
@@ -706,7 +737,7 @@ static ba_status check_options(const ba_options* o) {
     }
     if (o->max_lm_iters < 0 || o->max_pcg_iters < 0 || !(o->pcg_rel_tol >= 0) || !(o->initial_trust_region > 0) ||
         !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0) ||
-        (o->pcg_kernel != 0 && o->pcg_kernel != 1) || o->use_graph < 0 || o->use_graph > 2 ||
+        (o->pcg_kernel < 0 || o->pcg_kernel > 2) || o->use_graph < 0 || o->use_graph > 2 ||
         (o->rotation_update != 0 && o->rotation_update != 1) || o->loss < 0 || o->loss > 2 ||
         !(o->loss_scale > 0) || (o->solver != 0 && o->solver != 1)) {
         set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive)");
@@ -772,11 +803,17 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
     }
     if ((st = write_options(p, o))) return st;
     const bool want_schur = o->solver == 1;
-    const bool want_persistent = p->persistent && o->pcg_kernel == 0 && !want_schur;
-    if (want_persistent != p->use_persistent || want_schur != p->use_schur) {
+    // pcg_kernel 0: the persistent kernel's two-exchange form, 2: its one-exchange
+    // form, each when the plan fits in that form; otherwise separate kernels
+    const int want_form = o->pcg_kernel == 2 ? PCG_ONE_EXCHANGE : PCG_TWO_EXCHANGE;
+    const bool want_persistent = !want_schur && o->pcg_kernel != 1 &&
+                                 (want_form == PCG_ONE_EXCHANGE ? p->fits_one : p->fits_two);
+    if (want_persistent != p->use_persistent || want_schur != p->use_schur ||
+        (want_persistent && want_form != p->p_form)) {
         release_graph(p);   // cached graphs were built for the other PCG form
         p->use_persistent = want_persistent;
         p->use_schur = want_schur;
+        if (want_persistent) p->p_form = want_form;
     }
     // A cooperative kernel cannot sit inside a conditional node, so with the persistent
     // PCG kernel the default graph is the fixed LM sequence (six kernels per LM step).
@@ -957,7 +994,8 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
             launch_precond(v, p->L, s, 0, 0, p->pslots);
             cudaEventRecord(e0, s);
             GBBA_CUDA(launch_pcg_persistent(v, p->blk_tile, p->blk_cam_off, p->blk_cams, p->pslots, p->p_grid,
-                                            p->p_smem, s));
+                                            p->p_form == PCG_TWO_EXCHANGE ? p->p_smem_two : p->p_smem_one,
+                                            p->p_form, s));
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             float ms = 0;

@@ -59,11 +59,31 @@ void launch_unpack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, co
 void launch_set_direction(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const float* src);
 void launch_normal_out(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, float* out);
 // persistent PCG (pcg_persistent.cu)
+// Two forms, numbered like ba_options.pcg_kernel: PCG_TWO_EXCHANGE (0) runs the
+// textbook recurrences with two grid-wide exchanges per iteration; PCG_ONE_EXCHANGE
+// (2) rearranges them so that one exchange per iteration carries both inner products.
+enum : int { PCG_TWO_EXCHANGE = 0, PCG_ONE_EXCHANGE = 2 };
+// Entries of blk_cams: camera id, bit 31 set in the one list that owns the camera.
+constexpr uint32_t BLK_CAM_OWNER = 0x80000000u;
 int persistent_max_smem();
-cudaError_t persistent_prepare(int smem_bytes, int* blocks_per_sm);
+cudaError_t persistent_prepare(int form, int smem_bytes, int* blocks_per_sm);
 cudaError_t launch_pcg_persistent(const Views<float>& v, const uint32_t* blk_tile, const uint32_t* blk_cam_off,
-                                  const uint32_t* blk_cams, double* pslots, int grid, int smem_bytes,
+                                  const uint32_t* blk_cams, double* pslots, int grid, int smem_bytes, int form,
                                   cudaStream_t s);
+// Dynamic shared memory of the one-exchange kernel for a CTA with `no` observations,
+// `np` points and `ncb` listed cameras, in the order the kernel carves it.
+__host__ __device__ inline size_t pcg1_smem_bytes(size_t no, size_t np, size_t ncb) {
+    const size_t n3p = (3 * np + 3) & ~(size_t)3;
+    size_t b = (4 * no + 15) & ~(size_t)15;          // observation keys
+    b += 32 * np;                                     // (X, D_0) and (u, D_1) as float4
+    b += 4 * ((np + 3) & ~(size_t)3);                 // D_2
+    b += 4 * 5 * n3p;                                 // p, s, r, h, q
+    b += 4 * ((6 * np + 3) & ~(size_t)3);             // M^-1 blocks
+    b += 4 * ((ncb + 3) & ~(size_t)3);                // camera ids
+    b += 4 * ((((ncb + 31) >> 5) + 3) & ~(size_t)3);  // owner bits
+    b += 4 * (16 + 12 + 5 * 9) * ncb;                 // records, directions, u p s r h
+    return b;
+}
 int occupancy_blocks_linearize();
 int occupancy_blocks_matvec();
 int occupancy_blocks_eval();

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
         // (one flush per camera run), the tile's point sums in shared memory
         {
             const uint32_t n = hi - lo;
-            const uint32_t chunk = (n + TB - 1) / TB;
+            const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
             const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
             uint32_t cur = NO_CAM;
             float acc[LIN_ACC];
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
 __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, double* pslots) {
     DevState* st = v.st;
     if (pslots != nullptr && blockIdx.x == 0) {   // state of the persistent PCG kernel
-        for (int i = threadIdx.x; i < PSLOT_DOUBLES; i += blockDim.x) pslots[i] = 0.0;
+        for (int i = threadIdx.x; i < PSLOT_TOTAL; i += blockDim.x) pslots[i] = 0.0;
         if (threadIdx.x == 0) {
             st->bar_count = 0u;
             st->bar_err = 0;
@@ -291,7 +291,12 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
             rz += (double)ri * (double)z;
             rr += (double)ri * (double)ri;
         }
-        if (lane < CA_STRIDE) v.cam_acc[(size_t)c * CA_STRIDE + lane] = 0.0f;
+        if (lane < CA_STRIDE) {
+            v.cam_acc[(size_t)c * CA_STRIDE + lane] = 0.0f;
+            if (pslots != nullptr)   // the persistent kernel rotates over all the sets
+                for (int set = 1; set < CA_SETS; ++set)
+                    v.cam_acc[((size_t)set * v.n_cams + c) * CA_STRIDE + lane] = 0.0f;
+        }
     }
     FOR_POINTS(i, v) {
         const float* H = v.pt_H + (size_t)i * PH_STRIDE;
@@ -388,7 +393,7 @@ __global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* ga
         }
         __syncthreads();
         const uint32_t n = hi - lo;
-        const uint32_t chunk = (n + TB - 1) / TB;
+        const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
         const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
         uint32_t cur = NO_CAM;
         float acc[9];
@@ -677,7 +682,7 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
             const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
             const int pt0 = tile * TILE_PTS;
             const uint32_t n = hi - lo;
-            const uint32_t chunk = (n + TB - 1) / TB;
+            const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
             const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
             uint32_t cur = NO_CAM;
             Cam cn, co;
@@ -849,7 +854,7 @@ __global__ void __launch_bounds__(TB) k_schur(Views<float> v, const int32_t* gat
             }
         __syncthreads();
         const uint32_t n = hi - lo;
-        const uint32_t chunk = (n + TB - 1) / TB;
+        const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
         const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
         if (MODE != SCHUR_RHS) {
             // pass 1: y_p = sum J_p^T W J_c d
@@ -1213,7 +1218,7 @@ __global__ void __launch_bounds__(TB) k_cost_grad(Views<float> v, const float* _
         __syncthreads();
         if (want_grad) {
             const uint32_t n = hi - lo;
-            const uint32_t chunk = (n + TB - 1) / TB;
+            const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
             const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
             uint32_t cur = NO_CAM;
             float acc[9];

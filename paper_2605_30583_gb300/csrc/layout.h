@@ -21,7 +21,13 @@ constexpr int NPART = 4;            // doubles of partial sums per block
 constexpr int NSLOT = 32;           // atomic accumulator slots per scalar sum
 constexpr int SLOT_STRIDE = 16;     // doubles between slots (one 128-byte line)
 constexpr int MAX_PBLOCKS = 1024;   // CTAs of the persistent PCG kernel
-constexpr int PSLOT_DOUBLES = 6 * NSLOT * SLOT_STRIDE;   // 3 rotating sets x (matvec, update)
+// Exchange area of the persistent PCG kernels: three rotating slot sets of NSLOT
+// slots, each slot XCH_NV sums (doubles), cleared before every launch.
+constexpr int XCH_NV = 4;
+constexpr int PSLOT_TOTAL = 3 * NSLOT * SLOT_STRIDE;
+static_assert(XCH_NV <= SLOT_STRIDE, "a slot holds every sum of one exchange");
+// Camera accumulator sets of the one-exchange kernel (rotating over iterations).
+constexpr int CA_SETS = 3;
 
 // Camera record (floats), written once per parameter change (FP64 math, FP32 store).
 enum : int { CP_R = 0, CP_T = 9, CP_F = 12, CP_K1 = 13, CP_K2 = 14, CP_PAD = 15,

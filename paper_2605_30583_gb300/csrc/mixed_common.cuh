@@ -62,6 +62,17 @@ __device__ __forceinline__ void jdir(const Geo& g, const Cam& c, const float (&d
     t1 = fmaf(g.A[3], dP0, fmaf(g.A[4], dP1, fmaf(g.A[5], dP2, ci * g.p[1])));
 }
 
+// Observations per thread when a CTA of `threads` threads splits `n` of them into
+// contiguous chunks, rounded up to an odd count.  A camera's run covers consecutive
+// tile slots, so lanes inside one run sit `chunk` slots apart: an odd stride sends
+// their float4 point loads to distinct bank groups and their three-float point
+// accumulations to distinct banks, where an even one (16 is the worst) serialises
+// up to 16 of them.
+template <typename T>
+__host__ __device__ __forceinline__ T odd_chunk(T n, T threads) {
+    return ((n + threads - 1) / threads) | (T)1;
+}
+
 __device__ __forceinline__ bool gated_off(const int32_t* gate) { return gate != nullptr && *gate == 0; }
 
 

@@ -3,17 +3,38 @@
 //
 // One cooperative launch runs every PCG iteration of one LM step.  The grid is one
 // CTA per SM; CTA b owns a contiguous run of tiles (balanced by observation count)
-// and keeps, for the whole solve, its observation keys and its points' X, D, M^-1,
-// r, z, h, p and q in shared memory.  Per iteration only the camera-side data
-// (directions, accumulators, the camera part of the vectors) goes through global
-// memory.  Two grid-wide barriers separate the phases:
+// and keeps, for the whole solve, its observation keys and its points' X, D, M^-1
+// and PCG vectors in shared memory.  Grid-wide sums travel through an exchange:
+// slot-spread atomic sums followed by a grid barrier, after which every CTA reads the
+// same totals and so takes the same stop decision.  Every wait is time-bounded: on a
+// time-out the CTA sets an error flag, every CTA leaves, and the solve reports
+// BA_ERR_TIMEOUT.
+//
+// Two forms of the same Krylov iteration:
+//
+// k_pcg_persistent_twosync (the default form): the textbook recurrences, two
+// exchanges per iteration:
 //   A  p = z + beta p (points in smem; cameras double-buffered in global), then
-//      q = J^T J p + mu D p with |J p|^2 and p^T D p;
+//      q = J^T J p + mu D p with |J p|^2 and p^T D p;            -> exchange
 //   B  alpha = r^T z / (|J p|^2 + mu p^T D p); h += alpha p; r -= alpha q; z = M^-1 r;
-//   C  r^T z, |r|^2 -> stop test (|r| <= tol |r_0| or the iteration cap), beta.
-// Every CTA takes the stop decision from the same global sums, so all leave the
-// loop together.  The barrier spins are time-bounded: on a time-out the CTA sets an
-// error flag, every CTA leaves, and the solve reports BA_ERR_TIMEOUT.
+//      r^T z, |r|^2                                              -> exchange
+//   C  stop test (|r| <= tol |r_0| or the iteration cap), beta.
+//
+// k_pcg_persistent: one exchange per iteration.  The recurrences are arranged as in
+// the CG of Chronopoulos and Gear (J. Comput. Appl. Math. 25, 1989): with u = M^-1 r,
+// w = A u and s = A p carried by s = w + beta s,
+//   gamma = r^T u,  delta = u^T A u = |J u|^2 + mu u^T D u,
+//   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev),
+// so both inner products of an iteration come out of the one exchange that follows
+// the operator.  Each CTA keeps its own copy of the camera vectors it touches and
+// updates them from the assembled camera sums of the operator, so no second exchange
+// publishes them; the one CTA that owns a camera adds it to the inner products and
+// writes its step.  Same iterates in exact arithmetic; in FP32 the recurrence for s
+// lets the updated residual drift from the true one sooner.
+//   M  w = J^T W J u: point part in shared memory, camera part into one of three
+//      rotating accumulator sets; |J u|^2 with the partials of the previous update;
+//   X  exchange: gamma, |r|^2, u^T D u, |J u|^2 over the grid; stop test, alpha, beta;
+//   U  p = u + beta p, s = w + beta s, h += alpha p, r -= alpha s, u = M^-1 r.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -60,22 +81,44 @@ __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int nblocks) {
     return s_ok != 0;
 }
 
-// Sum over slots of component k of one slot set, broadcast to the whole CTA.
-__device__ __forceinline__ void slot_pair(const double* set, double* sh, double& a, double& b) {
-    __syncthreads();
+// Grid-wide sums of XCH_NV per-CTA values, then the grid barrier.  Exchange e adds
+// into slot set e % 3 (CTA b into slot b % NSLOT, so concurrent atomics spread over
+// NSLOT lines); every CTA then reads the same totals.  Block 0 clears set (e + 1) % 3
+// before it arrives: that set was last read right after exchange e - 2, which every
+// CTA has left, and is next filled after exchange e.  `mine` is read in thread 0;
+// `sh` holds XCH_NV doubles.  False on time-out.
+__device__ bool exchange(DevState* st, double* pslots, unsigned long long epoch, const double (&mine)[XCH_NV],
+                         double (&tot)[XCH_NV], double* sh) {
+    double* cur = pslots + (size_t)(epoch % 3ull) * NSLOT * SLOT_STRIDE;
+    if (blockIdx.x == 0) {
+        double* nx = pslots + (size_t)((epoch + 1ull) % 3ull) * NSLOT * SLOT_STRIDE;
+        for (int i = threadIdx.x; i < NSLOT * SLOT_STRIDE; i += blockDim.x) nx[i] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < XCH_NV; ++k)
+            if (mine[k] != 0.0) slot_add(cur, k, mine[k]);
+    }
+    if (!grid_sync(st, gridDim.x)) return false;
     if (threadIdx.x < 32) {
-        const double x = slot_sum_warp(set, 0), y = slot_sum_warp(set, 1);
-        if (threadIdx.x == 0) { sh[0] = x; sh[1] = y; }
+        double x[XCH_NV];
+#pragma unroll
+        for (int k = 0; k < XCH_NV; ++k) x[k] = slot_sum_warp(cur, k);
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < XCH_NV; ++k) sh[k] = x[k];
+        }
     }
     __syncthreads();
-    a = sh[0];
-    b = sh[1];
+#pragma unroll
+    for (int k = 0; k < XCH_NV; ++k) tot[k] = sh[k];
+    return true;
 }
 
 }  // namespace
 
 template <int TB>
-__global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const uint32_t* __restrict__ blk_tile,
+__global__ void __launch_bounds__(TB, 1) k_pcg_persistent_twosync(Views<float> v, const uint32_t* __restrict__ blk_tile,
                                                          const uint32_t* __restrict__ blk_cam_off,
                                                          const uint32_t* __restrict__ blk_cams,
                                                          double* __restrict__ pslots) {
@@ -84,7 +127,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int CAMS_PER_PASS = TB / 9;
     __shared__ double red[64];
-    __shared__ double sh2[2];
+    __shared__ double shx[XCH_NV + 1];
     __shared__ float s_cam_r[9 * CAMS_PER_PASS];
     const int tid = threadIdx.x;
     // cameras owned by this CTA: blockIdx.x + gridDim.x * j, j < n_own
@@ -113,9 +156,9 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
     float* sCam = reinterpret_cast<float*>(sCid + ((ncb + 3) & ~3u));   // 16 per camera
     float* sDir = sCam + 16 * (size_t)ncb;                              // 12 per camera
     const size_t g0 = v.pt_off + 3 * (size_t)pb;
-    for (uint32_t i = tid; i < ncb; i += TB) sCid[i] = __ldg(blk_cams + cb + i);
+    for (uint32_t i = tid; i < ncb; i += TB) sCid[i] = __ldg(blk_cams + cb + i) & ~BLK_CAM_OWNER;
     for (uint32_t i = tid; i < 16 * ncb; i += TB)
-        sCam[i] = __ldg(v.cam_pre + (size_t)__ldg(blk_cams + cb + i / 16) * CP_STRIDE + i % 16);
+        sCam[i] = __ldg(v.cam_pre + (size_t)(__ldg(blk_cams + cb + i / 16) & ~BLK_CAM_OWNER) * CP_STRIDE + i % 16);
     for (uint32_t i = tid; i < no; i += TB) skey[i] = __ldg(v.obs_key + ob + i);
     for (int i = tid; i < n3; i += TB) {
         sD[i] = v.D[g0 + i];
@@ -139,10 +182,11 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
     const int max_pcg = st->opt.max_pcg;
     double rz = st->rz, rr = rr0, alpha = 0.0;
     float beta = 0.0f;
+    unsigned long long epoch = 0ull;
     int k = 0;
     bool ok = true, numeric_fail = false;
     // this thread's observation chunk (block-local indices) and its first tile
-    const uint32_t chunk = (no + TB - 1) / TB;
+    const uint32_t chunk = odd_chunk<uint32_t>(no, TB);
     const uint32_t ja = min(tid * chunk, no), jb = min(ja + chunk, no);
     uint32_t tfirst = t0;
     {
@@ -155,9 +199,6 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
     }
 
     while (k < max_pcg) {
-        const int set = k % 3;
-        double* mv = pslots + (size_t)set * NSLOT * SLOT_STRIDE;
-        double* up = pslots + (size_t)(3 + set) * NSLOT * SLOT_STRIDE;
         const float* pc_old = v.pc + (size_t)(k & 1) * v.pc_stride;
         float* pc_new = v.pc + (size_t)((k & 1) ^ 1) * v.pc_stride;
         // ------------------------------------------------------------ phase A
@@ -238,18 +279,15 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
             const bool head = seg_reduce<9>(cur, acc);
             if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
         }
-        {
-            double bj, bp;
-            block_sum2(jp2, pdp, red, bj, bp);
-            if (tid == 0) {
-                slot_add(mv, 0, bj);
-                slot_add(mv, 1, bp);
-            }
-        }
-        if (!grid_sync(st, gridDim.x)) { ok = false; break; }
-        // ------------------------------------------------------------ phase B
         double sj, sp;
-        slot_pair(mv, sh2, sj, sp);
+        {
+            double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
+            block_sum2(jp2, pdp, red, mine[0], mine[1]);
+            if (!exchange(st, pslots, ++epoch, mine, tot, shx)) { ok = false; break; }
+            sj = tot[0];
+            sp = tot[1];
+        }
+        // ------------------------------------------------------------ phase B
         const double denom = sj + mu * sp;
         if (!(denom > 0.0) || !isfinite(denom)) {
             numeric_fail = !isfinite(denom);
@@ -317,24 +355,15 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
             lrz = fmaf(r3[0], z0, fmaf(r3[1], z1, fmaf(r3[2], z2, lrz)));
             lrr = fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], fmaf(r3[2], r3[2], lrr)));
         }
-        if (blockIdx.x == 0) {   // the slot sets of the next iteration start from zero
-            const int nx = (k + 1) % 3;
-            double* a0 = pslots + (size_t)nx * NSLOT * SLOT_STRIDE;
-            double* a1 = pslots + (size_t)(3 + nx) * NSLOT * SLOT_STRIDE;
-            for (int i = tid; i < NSLOT * SLOT_STRIDE; i += TB) { a0[i] = 0.0; a1[i] = 0.0; }
-        }
-        {
-            double brz, brr;
-            block_sum2(lrz, lrr, red, brz, brr);
-            if (tid == 0) {
-                slot_add(up, 0, brz);
-                slot_add(up, 1, brr);
-            }
-        }
-        if (!grid_sync(st, gridDim.x)) { ok = false; break; }
-        // ------------------------------------------------------------ phase C
         double rzn, rrn;
-        slot_pair(up, sh2, rzn, rrn);
+        {
+            double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
+            block_sum2(lrz, lrr, red, mine[0], mine[1]);
+            if (!exchange(st, pslots, ++epoch, mine, tot, shx)) { ok = false; break; }
+            rzn = tot[0];
+            rrn = tot[1];
+        }
+        // ------------------------------------------------------------ phase C
         ++k;
         rr = rrn;
         if (!isfinite(rzn) || !isfinite(rrn)) { numeric_fail = true; break; }
@@ -357,6 +386,360 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
     }
 }
 
+
+// ------------------------------------------------------------ one-exchange form ---
+
+namespace {
+
+
+__device__ __forceinline__ bool owns(const uint32_t* sOwn, int lc) { return (sOwn[lc >> 5] >> (lc & 31)) & 1u; }
+
+// Camera direction records (phi = J_l u_w, u_t, u_intr) of the CTA's cameras from u.
+template <int TB>
+__device__ __forceinline__ void camera_dirs(const Views<float>& v, const uint32_t* sCid, const float* sCu,
+                                            float* sDir, int ne) {
+    for (int e = threadIdx.x; e < ne; e += TB) {
+        const int lc = e / 9, i = e - 9 * lc;
+        float d;
+        if (i < 3) {
+            const float* JL = v.cam_pre + (size_t)sCid[lc] * CP_STRIDE + CP_JL + 3 * i;
+            const float* u = sCu + 9 * lc;
+            d = fmaf(__ldg(JL), u[0], fmaf(__ldg(JL + 1), u[1], __ldg(JL + 2) * u[2]));
+        } else {
+            d = sCu[e];
+        }
+        sDir[12 * lc + i] = d;
+    }
+}
+
+// Warp sums of the update's three partials into red[3 * warp + k] (FP32 in the warp).
+__device__ __forceinline__ void warp_partials3(float a, float b, float c, double* red) {
+    a = warp_sumf(a);
+    b = warp_sumf(b);
+    c = warp_sumf(c);
+    if ((threadIdx.x & 31) == 0) {
+        const int w = threadIdx.x >> 5;
+        red[3 * w] = (double)a;
+        red[3 * w + 1] = (double)b;
+        red[3 * w + 2] = (double)c;
+    }
+}
+
+}  // namespace
+
+template <int TB>
+__global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const uint32_t* __restrict__ blk_tile,
+                                                         const uint32_t* __restrict__ blk_cam_off,
+                                                         const uint32_t* __restrict__ blk_cams,
+                                                         double* __restrict__ pslots) {
+    DevState* st = v.st;
+    if (st->pcg_active == 0) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int NW = TB / 32;
+    __shared__ double red_u[3 * NW], red_m[NW], shx[XCH_NV + 1];
+    const int tid = threadIdx.x;
+    const uint32_t t0 = blk_tile[blockIdx.x], t1 = blk_tile[blockIdx.x + 1];
+    const uint32_t ob = v.tile_off[t0], oe = v.tile_off[t1];
+    const uint32_t no = oe - ob;
+    const int pb = (int)(t0 * TILE_PTS);
+    const int pe = min((int)(t1 * TILE_PTS), v.n_pts);
+    const int np = pe > pb ? pe - pb : 0;
+    const int n3p = (3 * np + 3) & ~3;
+    const uint32_t cb = blk_cam_off[blockIdx.x], ncb = blk_cam_off[blockIdx.x + 1] - cb;
+    const int ne = 9 * (int)ncb;   // camera vector entries of this CTA
+    // shared memory, carved in the order pcg1_smem_bytes counts it
+    uint32_t* skey = reinterpret_cast<uint32_t*>(smem);
+    float4* sX4 = reinterpret_cast<float4*>(smem + (((size_t)no * 4 + 15) & ~(size_t)15));   // (X, D_0)
+    float4* sU4 = sX4 + np;                                                                  // (u, D_1)
+    float* sD2 = reinterpret_cast<float*>(sU4 + np);
+    float* sP = sD2 + ((np + 3) & ~3);
+    float* sS = sP + n3p;
+    float* sR = sS + n3p;
+    float* sH = sR + n3p;
+    float* sQ = sH + n3p;
+    float* sM = sQ + n3p;
+    uint32_t* sCid = reinterpret_cast<uint32_t*>(sM + ((6 * np + 3) & ~3));
+    uint32_t* sOwn = sCid + ((ncb + 3) & ~3u);
+    float* sCam = reinterpret_cast<float*>(sOwn + ((((ncb + 31) >> 5) + 3) & ~3u));
+    float* sDir = sCam + 16 * (size_t)ncb;
+    float* sCu = sDir + 12 * (size_t)ncb;
+    float* sCp = sCu + ne;
+    float* sCs = sCp + ne;
+    float* sCr = sCs + ne;
+    float* sCh = sCr + ne;
+    const size_t g0 = v.pt_off + 3 * (size_t)pb;
+    const size_t cas = (size_t)CA_STRIDE * v.n_cams;   // floats between accumulator sets
+
+    for (uint32_t i = tid; i < ncb; i += TB) sCid[i] = __ldg(blk_cams + cb + i) & ~BLK_CAM_OWNER;
+    for (uint32_t w = tid; w < (ncb + 31) / 32; w += TB) {
+        uint32_t m = 0u;
+        for (uint32_t j = 0; j < 32u && 32u * w + j < ncb; ++j)
+            if (__ldg(blk_cams + cb + 32u * w + j) & BLK_CAM_OWNER) m |= 1u << j;
+        sOwn[w] = m;
+    }
+    for (uint32_t i = tid; i < no; i += TB) skey[i] = __ldg(v.obs_key + ob + i);
+    float lg = 0.0f, lr = 0.0f, lu = 0.0f;   // partials of r^T u, |r|^2, u^T D u
+    for (int i = tid; i < np; i += TB) {
+        const size_t e = g0 + 3 * (size_t)i;
+        const float D0 = v.D[e], D1 = v.D[e + 1], D2 = v.D[e + 2];
+        const float u0 = v.z[e], u1 = v.z[e + 1], u2 = v.z[e + 2];
+        const float r0 = v.r[e], r1 = v.r[e + 1], r2 = v.r[e + 2];
+        sX4[i] = make_float4(v.x[e], v.x[e + 1], v.x[e + 2], D0);
+        sU4[i] = make_float4(u0, u1, u2, D1);
+        sD2[i] = D2;
+        sR[3 * i] = r0; sR[3 * i + 1] = r1; sR[3 * i + 2] = r2;
+        lg = fmaf(r0, u0, fmaf(r1, u1, fmaf(r2, u2, lg)));
+        lr = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, lr)));
+        lu = fmaf(D0 * u0, u0, fmaf(D1 * u1, u1, fmaf(D2 * u2, u2, lu)));
+    }
+    for (int i = tid; i < n3p; i += TB) {
+        sP[i] = 0.0f;
+        sS[i] = 0.0f;
+        sH[i] = 0.0f;
+        sQ[i] = 0.0f;
+    }
+    for (int i = tid; i < 6 * np; i += TB) sM[i] = v.Minv_p[6 * (size_t)pb + i];
+    __syncthreads();   // camera ids and owner bits
+    for (uint32_t i = tid; i < 16 * ncb; i += TB)
+        sCam[i] = __ldg(v.cam_pre + (size_t)sCid[i / 16] * CP_STRIDE + i % 16);
+    for (int e = tid; e < ne; e += TB) {
+        const int lc = e / 9, i = e - 9 * lc;
+        const size_t ge = 9 * (size_t)sCid[lc] + i;
+        const float u = v.z[ge], r = v.r[ge];
+        sCu[e] = u;
+        sCr[e] = r;
+        sCp[e] = 0.0f;
+        sCs[e] = 0.0f;
+        sCh[e] = 0.0f;
+        if (owns(sOwn, lc)) {
+            lg = fmaf(r, u, lg);
+            lr = fmaf(r, r, lr);
+            lu = fmaf(__ldg(v.D + ge) * u, u, lu);
+        }
+    }
+    warp_partials3(lg, lr, lu, red_u);
+    __syncthreads();   // camera u
+    camera_dirs<TB>(v, sCid, sCu, sDir, ne);
+    __syncthreads();
+
+    const double mu = st->mu;
+    const float muf = (float)mu;
+    const float eps = (float)st->opt.eps;
+    const bool weighted = st->opt.loss != 0;   // robust loss: IRLS weights per observation
+    const double tol2 = st->opt.tol * st->opt.tol;
+    const double rr0 = st->rr0;
+    const int max_pcg = st->opt.max_pcg;
+    double gam = st->rz, gam_prev = 1.0, alpha = 0.0, alpha_prev = 1.0, rr = rr0;
+    float beta = 0.0f;
+    unsigned long long epoch = 0ull;
+    int k = 0;
+    bool ok = true, numeric_fail = false;
+    // this thread's observation chunk (block-local indices) and its first tile
+    const uint32_t chunk = odd_chunk<uint32_t>(no, TB);
+    const uint32_t ja = min(tid * chunk, no), jb = min(ja + chunk, no);
+    uint32_t tfirst = t0;
+    {
+        uint32_t lo = t0, hi = t1;   // largest t in [t0, t1) with tile_off[t] - ob <= ja
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(v.tile_off + mid) - ob <= ja) lo = mid; else hi = mid;
+        }
+        tfirst = lo;
+    }
+
+    while (k < max_pcg) {
+        float* cacc = v.cam_acc + (size_t)(k % CA_SETS) * cas;
+        // ------------------------------------------------------------ M: w = A u
+        float jj = 0.0f;
+        {
+            uint32_t cur = NO_CAM;
+            float acc[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) acc[q] = 0.0f;
+            if (ja < jb) {
+                uint32_t tcur = tfirst;
+                uint32_t tend = __ldg(v.tile_off + tcur + 1) - ob;
+                int tpt = (int)(tcur * TILE_PTS) - pb;
+                Cam cam;
+                float dir[9];
+                for (uint32_t j = ja; j < jb; ++j) {
+                    while (j >= tend) {
+                        ++tcur;
+                        tend = __ldg(v.tile_off + tcur + 1) - ob;
+                        tpt = (int)(tcur * TILE_PTS) - pb;
+                    }
+                    const uint32_t key = skey[j];
+                    const uint32_t c = key >> 8;
+                    const int lp = tpt + (int)(key & 0xffu);
+                    if (c != cur) {
+                        if (cur != NO_CAM) flush_matvec(cacc + (size_t)cur * CA_STRIDE, acc);
+                        cur = c;
+                        uint32_t lo = 0, hi = ncb;   // local index of camera c
+                        while (hi - lo > 1) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (sCid[mid] <= c) lo = mid; else hi = mid;
+                        }
+                        const float* rec = sCam + 16 * lo;
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) cam.R[q] = rec[q];
+                        cam.t[0] = rec[9]; cam.t[1] = rec[10]; cam.t[2] = rec[11];
+                        cam.f = rec[12]; cam.k1 = rec[13]; cam.k2 = rec[14];
+                        const float* dr = sDir + 12 * lo;
+#pragma unroll
+                        for (int q = 0; q < 9; ++q) dir[q] = dr[q];
+                    }
+                    const float4 xp = sX4[lp], up = sU4[lp];
+                    const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {up.x, up.y, up.z};
+                    if (weighted) jj += obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * lp, __ldg(v.obs_w + ob + j));
+                    else jj += obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * lp);
+                }
+            }
+            // every lane of the warp reaches this one collective
+            const bool head = seg_reduce<9>(cur, acc);
+            if (head && cur != NO_CAM) flush_matvec(cacc + (size_t)cur * CA_STRIDE, acc);
+        }
+        jj = warp_sumf(jj);
+        if ((tid & 31) == 0) red_m[tid >> 5] = (double)jj;
+        __syncthreads();
+        // ------------------------------------------------------------ X: exchange
+        double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
+        if (tid == 0) {
+            for (int w = 0; w < NW; ++w) {
+                mine[0] += red_u[3 * w];
+                mine[1] += red_u[3 * w + 1];
+                mine[2] += red_u[3 * w + 2];
+                mine[3] += red_m[w];
+            }
+        }
+        if (!exchange(st, pslots, ++epoch, mine, tot, shx)) { ok = false; break; }
+        const double g_k = tot[0], rr_k = tot[1], udu = tot[2], jju = tot[3];
+        if (!isfinite(g_k) || !isfinite(rr_k)) { numeric_fail = true; break; }
+        rr = rr_k;
+        if (k > 0 && rr_k <= tol2 * rr0) break;
+        const double b_k = k > 0 ? g_k / gam_prev : 0.0;
+        const double delta = jju + mu * udu;                                  // u^T A u
+        const double denom = k > 0 ? delta - b_k * g_k / alpha_prev : delta;   // p^T A p
+        if (!(denom > 0.0) || !isfinite(denom)) {
+            numeric_fail = !isfinite(denom);
+            break;   // every CTA sees the same sums and leaves here
+        }
+        gam = g_k;
+        alpha = g_k / denom;
+        beta = (float)b_k;
+        const float af = (float)alpha;
+        // ------------------------------------------------------------ U: update
+        lg = lr = lu = 0.0f;
+        // cameras, step 1: w from the assembled sums, then p, s, h, r
+        for (int e = tid; e < ne; e += TB) {
+            const int lc = e / 9, i = e - 9 * lc;
+            const uint32_t c = sCid[lc];
+            const float* ca = cacc + (size_t)c * CA_STRIDE;
+            float q;
+            if (i < 3) {
+                const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
+                q = fmaf(__ldg(JL + i), __ldcg(ca + 0), fmaf(__ldg(JL + 3 + i), __ldcg(ca + 1),
+                                                           __ldg(JL + 6 + i) * __ldcg(ca + 2)));
+            } else {
+                q = __ldcg(ca + i);
+            }
+            const float u = sCu[e];
+            const float w = fmaf(muf * __ldg(v.D + 9 * (size_t)c + i), u, q);
+            const float pk = fmaf(beta, sCp[e], u);
+            const float sk = fmaf(beta, sCs[e], w);
+            sCp[e] = pk;
+            sCs[e] = sk;
+            sCh[e] = fmaf(af, pk, sCh[e]);
+            sCr[e] = fmaf(-af, sk, sCr[e]);
+        }
+        // points: all of it in shared memory
+        for (int i = tid; i < np; i += TB) {
+            const float4 x4 = sX4[i], u4 = sU4[i];
+            const float Dq[3] = {x4.w, u4.w, sD2[i]};
+            const float uq[3] = {u4.x, u4.y, u4.z};
+            float r3[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int e = 3 * i + q;
+                const float w = fmaf(muf * Dq[q], uq[q], sQ[e]);
+                const float pk = fmaf(beta, sP[e], uq[q]);
+                const float sk = fmaf(beta, sS[e], w);
+                sP[e] = pk;
+                sS[e] = sk;
+                sQ[e] = 0.0f;
+                sH[e] = fmaf(af, pk, sH[e]);
+                r3[q] = fmaf(-af, sk, sR[e]);
+                sR[e] = r3[q];
+            }
+            const float* m = sM + 6 * i;
+            const float z0 = fmaf(m[0], r3[0], fmaf(m[1], r3[1], m[2] * r3[2]));
+            const float z1 = fmaf(m[1], r3[0], fmaf(m[3], r3[1], m[4] * r3[2]));
+            const float z2 = fmaf(m[2], r3[0], fmaf(m[4], r3[1], m[5] * r3[2]));
+            sU4[i] = make_float4(z0, z1, z2, u4.w);
+            lg = fmaf(r3[0], z0, fmaf(r3[1], z1, fmaf(r3[2], z2, lg)));
+            lr = fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], fmaf(r3[2], r3[2], lr)));
+            lu = fmaf(Dq[0] * z0, z0, fmaf(Dq[1] * z1, z1, fmaf(Dq[2] * z2, z2, lu)));
+        }
+        __syncthreads();   // camera r
+        // cameras, step 2: u = M^-1 r; the owner adds the partials and clears the
+        // accumulator set that the iteration after next fills (its last readers are
+        // past the exchange above)
+        {
+            float* clear = v.cam_acc + (size_t)((k + 2) % CA_SETS) * cas;
+            for (int e = tid; e < ne; e += TB) {
+                const int lc = e / 9, i = e - 9 * lc;
+                const uint32_t c = sCid[lc];
+                const float* M = v.Minv_c + (size_t)c * MC_STRIDE + 9 * i;
+                const float* r9 = sCr + 9 * lc;
+                float z = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) z = fmaf(__ldg(M + q), r9[q], z);
+                sCu[e] = z;
+                if (owns(sOwn, lc)) {
+                    const float ri = r9[i];
+                    lg = fmaf(ri, z, lg);
+                    lr = fmaf(ri, ri, lr);
+                    lu = fmaf(__ldg(v.D + 9 * (size_t)c + i) * z, z, lu);
+                    clear[(size_t)c * CA_STRIDE + i] = 0.0f;
+                }
+            }
+        }
+        warp_partials3(lg, lr, lu, red_u);
+        __syncthreads();   // camera u
+        camera_dirs<TB>(v, sCid, sCu, sDir, ne);
+        __syncthreads();
+        gam_prev = g_k;
+        alpha_prev = alpha;
+        ++k;
+    }
+    // closing exchange: past it no CTA reads an accumulator set any more, so the
+    // owners leave all of them cleared
+    if (ok) {
+        double z4[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, t4[XCH_NV];
+        __syncthreads();
+        ok = exchange(st, pslots, ++epoch, z4, t4, shx);
+    }
+    for (int e = tid; e < ne; e += TB) {
+        const int lc = e / 9, i = e - 9 * lc;
+        if (!owns(sOwn, lc)) continue;
+        const uint32_t c = sCid[lc];
+        v.h[9 * (size_t)c + i] = sCh[e];
+        if (ok)
+            for (int set = 0; set < CA_SETS; ++set) v.cam_acc[set * cas + (size_t)c * CA_STRIDE + i] = 0.0f;
+    }
+    for (int i = tid; i < 3 * np; i += TB) v.h[g0 + i] = sH[i];
+    if (blockIdx.x == 0 && tid == 0) {
+        st->pcg_iter = k;
+        st->pcg_total += k;
+        st->rz = gam;
+        st->rr = rr;
+        st->alpha = alpha;
+        st->beta = beta;
+        st->pcg_active = 0;
+        if (!ok) st->status = 5;
+        else if (numeric_fail) st->status = 4;
+    }
+}
+
 // ------------------------------------------------------------------ host ----------
 
 int persistent_max_smem() {
@@ -366,15 +749,16 @@ int persistent_max_smem() {
     return v;
 }
 
-cudaError_t persistent_prepare(int smem_bytes, int* blocks_per_sm) {
-    cudaError_t e = ensure_dynamic_smem((const void*)k_pcg_persistent<PCG_TB>, smem_bytes);
+cudaError_t persistent_prepare(int form, int smem_bytes, int* blocks_per_sm) {
+    const void* f = form == PCG_TWO_EXCHANGE ? (const void*)k_pcg_persistent_twosync<PCG_TB>
+                                            : (const void*)k_pcg_persistent<PCG_TB>;
+    cudaError_t e = ensure_dynamic_smem(f, smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_pcg_persistent<PCG_TB>, PCG_TB,
-                                                         smem_bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, PCG_TB, smem_bytes);
 }
 
 cudaError_t launch_pcg_persistent(const Views<float>& v, const uint32_t* blk_tile, const uint32_t* blk_cam_off,
-                                  const uint32_t* blk_cams, double* pslots, int grid, int smem_bytes,
+                                  const uint32_t* blk_cams, double* pslots, int grid, int smem_bytes, int form,
                                   cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -386,6 +770,8 @@ cudaError_t launch_pcg_persistent(const Views<float>& v, const uint32_t* blk_til
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (form == PCG_TWO_EXCHANGE)
+        return cudaLaunchKernelEx(&cfg, k_pcg_persistent_twosync<PCG_TB>, v, blk_tile, blk_cam_off, blk_cams, pslots);
     return cudaLaunchKernelEx(&cfg, k_pcg_persistent<PCG_TB>, v, blk_tile, blk_cam_off, blk_cams, pslots);
 }
 

@@ -62,14 +62,16 @@ struct ba_problem {
     int32_t unrolled_lm = -1, unrolled_pcg = -1;
     int device = 0;
     // persistent PCG plan (mixed precision, problems whose tiles fit in shared memory)
-    bool persistent = false;        // the plan fits
+    bool persistent = false;        // the plan fits, in at least one form
+    bool fits_one = false, fits_two = false;   // ... in the one-exchange / two-exchange form
     bool use_persistent = false;    // the plan is used by the current solve sequences
     bool use_schur = false;         // the current solve sequences use the Schur-complement PCG
-    int p_grid = 0, p_smem = 0;
+    int p_grid = 0, p_smem_one = 0, p_smem_two = 0;
+    int p_form = 0;                 // form of the current solve sequences (gbba::PCG_*)
     uint32_t* blk_tile = nullptr;   // device, [p_grid + 1]
     uint32_t* blk_cam_off = nullptr;   // device, [p_grid + 1]: per-CTA camera list offsets
     uint32_t* blk_cams = nullptr;      // device, the lists (inside the ordering region of the workspace)
-    double* pslots = nullptr;       // device, [PSLOT_DOUBLES]
+    double* pslots = nullptr;       // device, [PSLOT_TOTAL]
 };
 
 namespace gbba {

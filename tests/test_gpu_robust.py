@@ -38,7 +38,7 @@ def _outliers(p, seed, frac=0.05, size=40.0):
 
 
 @pytest.mark.parametrize("loss", ["huber", "cauchy"])
-@pytest.mark.parametrize("pcg_kernel", [0, 1])
+@pytest.mark.parametrize("pcg_kernel", [0, 1, 2])
 def test_robust_solve_matches_oracle(B, loss, pcg_kernel):
     prob = synth.round_to_f32(_outliers(synth.make_config("tiny", seed=61), 1))
     p = B.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels)
