@@ -231,7 +231,7 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
     if (pslots != nullptr && blockIdx.x == 0) {   // state of the persistent PCG kernel
         for (int i = threadIdx.x; i < PSLOT_TOTAL; i += blockDim.x) pslots[i] = 0.0;
         if (threadIdx.x == 0) {
-            st->bar_count = 0u;
+            st->bar_count = 0ull;
             st->bar_err = 0;
         }
     }

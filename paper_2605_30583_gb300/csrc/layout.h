@@ -79,7 +79,7 @@ struct DevState {
     int32_t pcg_iter, pcg_active, pcg_total, pad0;
     int64_t t_start, t_end;
     uint32_t tickets[TK_COUNT];
-    uint32_t bar_count, bar_gen;   // grid barrier of the persistent PCG kernel
+    unsigned long long bar_count;   // arrivals at the grid barriers of the persistent PCG kernel
     int32_t bar_err, pad1;
     IterRec hist[HIST_CAP];
 };

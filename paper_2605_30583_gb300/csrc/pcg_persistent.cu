@@ -47,34 +47,37 @@ namespace {
 
 constexpr long long BARRIER_TIMEOUT_NS = 2000000000LL;   // 2 s
 
-// Grid-wide barrier for a co-resident (cooperative) grid; false on time-out or when
-// another CTA has already reported one.
-__device__ __forceinline__ bool grid_sync(DevState* st, unsigned int nblocks) {
+// Grid-wide barrier number `epoch` (1, 2, ... within a launch) for a co-resident
+// (cooperative) grid.  Each CTA adds one to a counter, cleared before the launch, with
+// release semantics, and waits until it reaches epoch * nblocks: the count can only
+// get there once every CTA has arrived, and a CTA that has already moved on to the
+// next barrier only raises it further.  False on time-out or when another CTA has
+// already reported one.
+__device__ __forceinline__ bool grid_sync(DevState* st, unsigned int nblocks, unsigned long long epoch) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int* gen = &st->bar_gen;
-        volatile int* err = &st->bar_err;
-        const unsigned int g = *gen;
-        __threadfence();
-        if (atomicAdd(&st->bar_count, 1u) == nblocks - 1) {
-            st->bar_count = 0u;
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
-            const long long t0 = global_ns();
-            while (*gen == g) {
-                if (*err) { ok = 0; break; }
+        unsigned long long* cnt = &st->bar_count;
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(cnt), "l"(1ull) : "memory");
+        const unsigned long long target = epoch * nblocks;
+        const long long t0 = global_ns();
+        unsigned spins = 0;
+        for (;;) {
+            unsigned long long c;
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(cnt) : "memory");
+            if (c >= target) break;
+            if ((++spins & 15u) == 0u) {
+                if (*reinterpret_cast<volatile int*>(&st->bar_err)) { ok = 0; break; }
                 if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
                     atomicExch(&st->bar_err, 1);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
             }
+            __nanosleep(32);
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         s_ok = ok;
     }
     __syncthreads();
@@ -99,7 +102,7 @@ __device__ bool exchange(DevState* st, double* pslots, unsigned long long epoch,
         for (int k = 0; k < XCH_NV; ++k)
             if (mine[k] != 0.0) slot_add(cur, k, mine[k]);
     }
-    if (!grid_sync(st, gridDim.x)) return false;
+    if (!grid_sync(st, gridDim.x, epoch)) return false;
     if (threadIdx.x < 32) {
         double x[XCH_NV];
 #pragma unroll
