@@ -130,7 +130,7 @@ def matvec_model(prob):
 # DRAM bytes (read + write) per 50-iteration launch of k_pcg_persistent, from one ncu
 # capture of the same workload and launch (profiles/k_pcg_persistent_medium.md).  Set to
 # None whenever the kernel changes until it is captured again.
-PCG_TRAFFIC = {"medium": 19975680}
+PCG_TRAFFIC = {}
 
 
 def pcg_iter_model(prob):

@@ -158,6 +158,31 @@ void ba_problem_destroy(ba_problem* problem);
 /* Bytes of device workspace the problem needs (any options). */
 ba_status ba_workspace_size(const ba_problem* problem, size_t* bytes);
 
+/* Pose factors: generic node-to-node factors next to the reprojection factors
+ * (Sec. IV of the paper: factors between nodes such as odometry / pose-graph
+ * constraints).  Factor k ties cameras a = cam_a[k] and b = cam_b[k] (a != b) by a
+ * measured relative pose: with world-to-camera maps x = R_c X + t_c,
+ *   R_ba = R_b R_a^T,  t_ba = t_b - R_ba t_a,
+ *   r_k = s_k * [ Log(Exp(w_m)^T R_ba) ; t_ba - t_m ]      (6 rows, elementwise s_k),
+ * and the objective gains 1/2 sum_k |r_k|^2 (squared loss; a robust loss applies to
+ * the observations only).  LM and PCG treat the factor rows like any other rows of J:
+ * they enter g, the camera blocks of the preconditioner, D, the normal operator and
+ * the model decrease.
+ *   n_factors      >= 0; 0 removes every factor.
+ *   cam_a, cam_b   host, [n_factors] camera indices < n_cams, cam_a[k] != cam_b[k].
+ *   meas           host, [n_factors][6] FP64: w_m (rotation vector), t_m.
+ *   sqrt_info      host, [n_factors][6] FP64 >= 0, the square root of a diagonal
+ *                  information matrix; NULL = all ones.
+ * The arrays are copied; the caller keeps ownership.  Call before ba_workspace_size
+ * and ba_bind_workspace (the workspace holds the factors); a bound problem returns
+ * BA_ERR_INVALID_ARG.  The mixed-precision form only (BA_ERR_NOT_IMPLEMENTED for
+ * BA_PREC_FP64); ba_solve with solver = 1 (Schur complement) returns
+ * BA_ERR_NOT_IMPLEMENTED when factors are present.  ba_evaluate's cost includes the
+ * factors; its residual and Jacobian outputs, ba_cost_noalloc and the autograd entries
+ * cover the observations only.  Invalid indices or non-finite values: INVALID_ARG. */
+ba_status ba_set_pose_factors(ba_problem* problem, int32_t n_factors, const uint32_t* cam_a, const uint32_t* cam_b,
+                              const double* meas, const double* sqrt_info);
+
 /* Binds caller-owned device memory (>= ba_workspace_size bytes, 256-byte aligned)
  * and a CUDA stream (cudaStream_t, may be 0 for the legacy stream).  Uploads the
  * observations and builds the locality ordering on the device: points sorted by

@@ -27,6 +27,9 @@ the paper (arXiv 2605.30583, "Caspar"):
                      Cauchy on |r_o|^2 with IRLS weights rho'(|r_o|^2).
 * Schur PCG       -- the alternative Sec. V sets aside: PCG on the camera Schur
                      complement, points back-substituted (schur_pcg).
+* pose factors    -- generic node-to-node factors (Sec. IV): a relative-pose factor on
+                     two cameras, Log(R_m^T R_b R_a^T) and t_b - R_b R_a^T t_a - t_m,
+                     differentiated by the same dual numbers (PoseFactors).
 
 Readings where the paper is silent (all listed in the design notes): damping
 matrix D = diag(J^T J) clamped to [min_diag, max_diag]; mu_0 = 1 / trust region;
@@ -115,6 +118,21 @@ def _cos(x):
     if isinstance(x, Dual):
         return Dual(np.cos(x.v), -x.d * np.sin(x.v)[..., None])
     return np.cos(x)
+
+
+def _atan2(y, x):
+    """atan2 with its derivative (x dy - y dx) / (x^2 + y^2)."""
+    if isinstance(y, Dual) or isinstance(x, Dual):
+        yv, yd = (y.v, y.d) if isinstance(y, Dual) else (np.asarray(y, np.float64), None)
+        xv, xd = (x.v, x.d) if isinstance(x, Dual) else (np.asarray(x, np.float64), None)
+        den = (xv * xv + yv * yv)[..., None]
+        d = 0.0
+        if yd is not None:
+            d = d + yd * xv[..., None] / den
+        if xd is not None:
+            d = d - xd * yv[..., None] / den
+        return Dual(np.arctan2(yv, xv), d)
+    return np.arctan2(y, x)
 
 
 def _where(mask, a, b):
@@ -247,6 +265,106 @@ def jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, chunk=200
 
 
 # --------------------------------------------------------------------------------------
+# Pose factors: the generic, non-reprojection factors of Sec. IV (node-to-node factors
+# such as odometry / pose-graph constraints, Sec. I and IV-C), here a relative-pose
+# ("between") factor on two cameras.  Camera c maps world points by x = R_c X + t_c.
+# The pose of camera b relative to camera a is R_ba = R_b R_a^T, t_ba = t_b - R_ba t_a;
+# with a measurement (R_m = Exp(w_m), t_m) and a diagonal square-root information s,
+#     r = s * [ Log(R_m^T R_ba) ; t_ba - t_m ]           (6 rows),
+# and the factor adds 1/2 |r|^2 to the cost.  Its Jacobian comes from dual numbers
+# carried through this residual, like the reprojection factor's.
+# --------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class PoseFactors:
+    cam_a: np.ndarray        # [nf] camera indices
+    cam_b: np.ndarray        # [nf]
+    meas: np.ndarray         # [nf, 6]: w_m (rotation vector of R_m), t_m
+    sqrt_info: np.ndarray    # [nf, 6]: s, the square root of the diagonal information
+
+
+def log_rotation(M):
+    """Rotation vector of a rotation matrix given as M[i][j] (arrays or duals):
+    sin(theta) n = (M21 - M12, M02 - M20, M10 - M01) / 2, cos(theta) = (trace - 1) / 2,
+    theta = atan2(|sin(theta) n|, cos(theta)), w = theta n.  For |sin(theta)|^2 < 1e-8
+    the factor theta / sin(theta) is its series 1 + y^2/6 + 3 y^4/40 in y = sin(theta)
+    (valid while theta < pi / 2 there, i.e. near the identity)."""
+    v0 = 0.5 * (M[2][1] - M[1][2])
+    v1 = 0.5 * (M[0][2] - M[2][0])
+    v2 = 0.5 * (M[1][0] - M[0][1])
+    c = 0.5 * (M[0][0] + M[1][1] + M[2][2] - 1.0)
+    y2 = v0 * v0 + v1 * v1 + v2 * v2
+    small = _value(y2) < SMALL_ANGLE_SQ
+    y2_safe = _where(small, 1.0, y2)
+    y = _sqrt(y2_safe)
+    k_big = _atan2(y, c) / y
+    k_small = 1.0 + y2 / 6.0 + 3.0 * y2 * y2 / 40.0
+    k = _where(small, k_small, k_big)
+    return (k * v0, k * v1, k * v2)
+
+
+def _pose_residual(wa, ta, wb, tb, wm, tm, s, base_a=None, base_b=None):
+    """The six rows of one factor (lists of arrays or duals).  With base_a / base_b
+    given, wa / wb are left steps: R_a = Exp(wa) R(base_a)."""
+    if base_a is None:
+        rot_a_t = lambda X: rotate([-wa[0], -wa[1], -wa[2]], X)
+    else:
+        rot_a_t = lambda X: rotate([-base_a[0], -base_a[1], -base_a[2]], rotate([-wa[0], -wa[1], -wa[2]], X))
+    rot_b = (lambda X: rotate(wb, X)) if base_b is None else (lambda X: rotate(wb, rotate(base_b, X)))
+    rot_ba = lambda X: rot_b(rot_a_t(X))
+    one, zero = np.ones_like(_value(tm[0])), np.zeros_like(_value(tm[0]))
+    cols = [rotate([-wm[0], -wm[1], -wm[2]], rot_ba(e)) for e in
+            ([one, zero, zero], [zero, one, zero], [zero, zero, one])]
+    E = [[cols[j][i] for j in range(3)] for i in range(3)]      # E[i][j] = column j, entry i
+    rr = log_rotation(E)
+    Rt = rot_ba(ta)
+    rt = [tb[i] - Rt[i] - tm[i] for i in range(3)]
+    return [s[:, i] * (list(rr) + rt)[i] for i in range(6)]
+
+
+def pose_factor_residuals(cams, f: PoseFactors):
+    """r [nf, 6] of every factor at the cameras `cams`."""
+    cams = np.asarray(cams, np.float64)
+    A, Bc = cams[f.cam_a], cams[f.cam_b]
+    r = _pose_residual(list(A[:, 0:3].T), list(A[:, 3:6].T), list(Bc[:, 0:3].T), list(Bc[:, 3:6].T),
+                       list(f.meas[:, 0:3].T), list(f.meas[:, 3:6].T), f.sqrt_info)
+    return np.stack([_value(x) for x in r], axis=1)
+
+
+def pose_factor_cost(cams, f: PoseFactors):
+    """1/2 sum of |r|^2 over the factors."""
+    r = pose_factor_residuals(cams, f)
+    return 0.5 * float(np.sum(r * r))
+
+
+def pose_factor_blocks(cams, f: PoseFactors, retraction=False):
+    """r [nf, 6] and the Jacobian blocks J_a, J_b [nf, 6, 9] (w, t columns filled; the
+    intrinsic columns are zero), by dual numbers seeded with the 12 tangent directions
+    (w_a, t_a, w_b, t_b).  retraction=True: rotation columns w.r.t. the left steps."""
+    cams = np.asarray(cams, np.float64)
+    A, Bc = cams[f.cam_a], cams[f.cam_b]
+    m = A.shape[0]
+    eye = np.eye(12)
+    seed = lambda vals, k0: [Dual(vals[:, k], np.broadcast_to(eye[k0 + k], (m, 12))) for k in range(3)]
+    ta, tb = seed(A[:, 3:6], 3), seed(Bc[:, 3:6], 9)
+    if retraction:
+        wa, wb = seed(np.zeros((m, 3)), 0), seed(np.zeros((m, 3)), 6)
+        rows = _pose_residual(wa, ta, wb, tb, list(f.meas[:, 0:3].T), list(f.meas[:, 3:6].T), f.sqrt_info,
+                              base_a=list(A[:, 0:3].T), base_b=list(Bc[:, 0:3].T))
+    else:
+        wa, wb = seed(A[:, 0:3], 0), seed(Bc[:, 0:3], 6)
+        rows = _pose_residual(wa, ta, wb, tb, list(f.meas[:, 0:3].T), list(f.meas[:, 3:6].T), f.sqrt_info)
+    r = np.stack([x.v for x in rows], axis=1)
+    D = np.stack([x.d for x in rows], axis=1)                  # [nf, 6, 12]
+    Ja = np.zeros((m, 6, 9))
+    Jb = np.zeros((m, 6, 9))
+    Ja[:, :, 0:6] = D[:, :, 0:6]
+    Jb[:, :, 0:6] = D[:, :, 6:12]
+    return r, Ja, Jb
+
+
+# --------------------------------------------------------------------------------------
 # Problem layout: x = [cams (9 per camera) | points (3 per point)], n = 9 Nc + 3 Np
 # --------------------------------------------------------------------------------------
 
@@ -309,11 +427,12 @@ def robust_weight(s, loss="squared", scale=1.0):
 
 
 def linearize(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, retraction=False, loss="squared",
-              loss_scale=1.0) -> Linearization:
+              loss_scale=1.0, factors: PoseFactors | None = None) -> Linearization:
     """F, g = J^T W r and the node blocks of J^T W J, with W the IRLS weights
     w_o = rho'(|r_o|^2) (all ones for the squared loss).  J and r are returned already
     scaled by sqrt(w_o), so every later product (PCG, |J h|^2) is the weighted one;
-    F = 1/2 sum rho(|r_o|^2)."""
+    F = 1/2 sum rho(|r_o|^2).  Pose factors, if given, append their six rows per factor
+    (squared loss) after the observations' rows."""
     n_cams, n_pts = cams.shape[0], pts.shape[0]
     r, Jc, Jp = jacobian_blocks(cams, pts, cam_idx, pt_idx, pixels, eps_depth, retraction=retraction)
     s = np.sum(r * r, axis=1)
@@ -324,11 +443,25 @@ def linearize(cams, pts, cam_idx, pt_idx, pixels, eps_depth=0.0, retraction=Fals
     Jp = Jp * sw[:, None, None]
     J = assemble_jacobian(Jc, Jp, cam_idx, pt_idx, n_cams, n_pts)
     rf = r.reshape(-1)
-    g = J.T @ rf
     Hc = np.zeros((n_cams, 9, 9))
     Hp = np.zeros((n_pts, 3, 3))
     np.add.at(Hc, np.asarray(cam_idx, np.int64), np.einsum("oki,okj->oij", Jc, Jc))
     np.add.at(Hp, np.asarray(pt_idx, np.int64), np.einsum("oki,okj->oij", Jp, Jp))
+    if factors is not None and len(factors.cam_a) > 0:
+        r_f, Ja, Jb = pose_factor_blocks(cams, factors, retraction)
+        F += 0.5 * float(np.sum(r_f * r_f))
+        nf = r_f.shape[0]
+        rows = np.repeat(np.arange(6 * nf), 18)
+        ca = 9 * np.asarray(factors.cam_a, np.int64)[:, None] + np.arange(9)[None, :]
+        cb = 9 * np.asarray(factors.cam_b, np.int64)[:, None] + np.arange(9)[None, :]
+        cols = np.repeat(np.concatenate([ca, cb], axis=1), 6, axis=0).reshape(-1)
+        vals = np.concatenate([Ja, Jb], axis=2).reshape(-1)
+        J_f = sp.csr_matrix((vals, (rows, cols)), shape=(6 * nf, J.shape[1]))
+        J = sp.vstack([J, J_f]).tocsr()
+        rf = np.concatenate([rf, r_f.reshape(-1)])
+        np.add.at(Hc, np.asarray(factors.cam_a, np.int64), np.einsum("oki,okj->oij", Ja, Ja))
+        np.add.at(Hc, np.asarray(factors.cam_b, np.int64), np.einsum("oki,okj->oij", Jb, Jb))
+    g = J.T @ rf
     return Linearization(F=F, r=rf, J=J, g=g, Hc=Hc, Hp=Hp)
 
 
@@ -564,10 +697,12 @@ def retract_cams(cams, h_cams):
     return out
 
 
-def ba_solve(cams0, pts0, cam_idx, pt_idx, pixels, opts: LMOptions = LMOptions()) -> LMResult:
+def ba_solve(cams0, pts0, cam_idx, pt_idx, pixels, opts: LMOptions = LMOptions(),
+             factors: PoseFactors | None = None) -> LMResult:
     """Bundle adjustment by LM + PCGNR over all camera and point parameters.  With
     opts.rotation_update == "retraction" each step updates the rotations by
-    R <- Exp(d) R (Jacobian w.r.t. d), the rest additively."""
+    R <- Exp(d) R (Jacobian w.r.t. d), the rest additively.  Pose factors, if given,
+    join the reprojection factors in the cost and the normal equations."""
     n_cams = cams0.shape[0]
     retraction = opts.rotation_update == "retraction"
     if opts.rotation_update not in ("additive", "retraction"):
@@ -576,11 +711,12 @@ def ba_solve(cams0, pts0, cam_idx, pt_idx, pixels, opts: LMOptions = LMOptions()
     def lin_fn(x):
         c, p = unpack(x, n_cams)
         return linearize(c, p, cam_idx, pt_idx, pixels, opts.eps_depth, retraction=retraction, loss=opts.loss,
-                         loss_scale=opts.loss_scale)
+                         loss_scale=opts.loss_scale, factors=factors)
 
     def cost_fn(x):
         c, p = unpack(x, n_cams)
-        return robust_cost(c, p, cam_idx, pt_idx, pixels, opts.eps_depth, opts.loss, opts.loss_scale)
+        F = robust_cost(c, p, cam_idx, pt_idx, pixels, opts.eps_depth, opts.loss, opts.loss_scale)
+        return F if factors is None else F + pose_factor_cost(c, factors)
 
     def step_fn(x, h):
         c, p = unpack(x, n_cams)

@@ -68,6 +68,7 @@ SIGNATURES = {
     "ba_problem_create": (I32, [I32, I32, I64, P, P, P, I32, ctypes.POINTER(P)]),
     "ba_problem_destroy": (None, [P]),
     "ba_workspace_size": (I32, [P, ctypes.POINTER(SZ)]),
+    "ba_set_pose_factors": (I32, [P, I32, P, P, P, P]),
     "ba_bind_workspace": (I32, [P, P, SZ, P]),
     "ba_set_params": (I32, [P, P, P]),
     "ba_get_params": (I32, [P, P, P]),
@@ -156,9 +157,11 @@ class Problem:
     """One bundle-adjustment problem bound to a device workspace.
 
     cam_idx, pt_idx: integer arrays [n_obs]; pixels: float64 [n_obs, 2] (host arrays).
-    precision: "mixed" (FP32 bulk, FP64 sums) or "fp64" (plain all-FP64 form)."""
+    precision: "mixed" (FP32 bulk, FP64 sums) or "fp64" (plain all-FP64 form).
+    pose_factors: optional (cam_a, cam_b, meas [nf, 6], sqrt_info [nf, 6] or None), the
+    relative-pose factors of ba_set_pose_factors (mixed form only)."""
 
-    def __init__(self, n_cams, n_pts, cam_idx, pt_idx, pixels, precision="mixed", stream=None):
+    def __init__(self, n_cams, n_pts, cam_idx, pt_idx, pixels, precision="mixed", stream=None, pose_factors=None):
         torch = _torch()
         self.n_cams, self.n_pts = int(n_cams), int(n_pts)
         ci = np.ascontiguousarray(cam_idx, dtype=np.uint32)
@@ -171,6 +174,20 @@ class Problem:
         check(lib().ba_problem_create(self.n_cams, self.n_pts, self.n_obs, _ptr(ci), _ptr(pi), _ptr(px),
                                       self.precision, ctypes.byref(h)))
         self._h = h
+        self.n_factors = 0
+        if pose_factors is not None:
+            fa, fb, meas, sq = pose_factors
+            fa = np.ascontiguousarray(fa, dtype=np.uint32)
+            fb = np.ascontiguousarray(fb, dtype=np.uint32)
+            meas = np.ascontiguousarray(meas, dtype=np.float64).reshape(-1, 6)
+            sq = None if sq is None else np.ascontiguousarray(sq, dtype=np.float64).reshape(-1, 6)
+            self.n_factors = int(fa.shape[0])
+            st = lib().ba_set_pose_factors(h, self.n_factors, _ptr(fa), _ptr(fb), _ptr(meas),
+                                           _ptr(sq) if sq is not None else None)
+            if st != 0:
+                self._h = None   # destroyed here; close() must not destroy it again
+                lib().ba_problem_destroy(h)
+                check(st)
         nbytes = ctypes.c_size_t()
         check(lib().ba_workspace_size(h, ctypes.byref(nbytes)))
         self.workspace_bytes = int(nbytes.value)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -51,7 +52,7 @@ inline size_t pow2_at_least(size_t n) {
 
 }  // namespace
 
-Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t precision) {
+Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t precision, int32_t n_fac) {
     Layout l{};
     const size_t T = precision == BA_PREC_FP64 ? 8 : 4;
     const size_t nc = (size_t)n_cams, np = (size_t)n_pts, no = (size_t)n_obs;
@@ -75,10 +76,11 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     l.blk_tile = b.take(4 * (MAX_PBLOCKS + 1));
     l.blk_cam_off = b.take(4 * (MAX_PBLOCKS + 1));
     // per-CTA camera lists of the persistent PCG kernel: each CTA lists the cameras of
-    // its observations, and every camera no observation sees is listed once, so
-    // n_obs + n_cams + MAX_PBLOCKS entries always suffice; the plan is only used when
-    // they fit in shared memory, so cap the region
-    l.blk_cams = b.take(4 * std::min(no + nc + MAX_PBLOCKS, (size_t)(MAX_PBLOCKS * 4096)));
+    // its observations and pose factors, and every other camera is listed once, so
+    // n_obs + 2 n_fac + n_cams + MAX_PBLOCKS entries always suffice; the plan is only
+    // used when they fit in shared memory, so cap the region
+    const size_t nfc = 2 * (size_t)std::max(0, n_fac);
+    l.blk_cams = b.take(4 * std::min(no + nfc + nc + MAX_PBLOCKS, (size_t)(MAX_PBLOCKS * 4096)));
     l.pslots = b.take(8 * PSLOT_TOTAL);
     const size_t union_base = align_up(b.off, 256);
     // solver arrays
@@ -96,6 +98,11 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     l.Minv_c = s.take(T * MC_STRIDE * nc);
     l.Minv_p = s.take(T * MP_STRIDE * 4 * n_quads);
     l.obs_w = s.take(4 * no);
+    const size_t nf = (size_t)std::max(0, n_fac);
+    l.fac_cam = s.take(4 * 2 * nf);
+    l.fac_meas = s.take(8 * 6 * nf);
+    l.fac_sqrt = s.take(8 * 6 * nf);
+    l.fac_J = s.take(4 * 72 * nf);
     if (precision == BA_PREC_FP64) {
         l.jac = s.take(T * 24 * no);
         l.res = s.take(T * 2 * no);
@@ -159,6 +166,11 @@ Views<T> make_views(ba_problem* p) {
     v.jac = l.jac ? (T*)(w + l.jac) : nullptr;
     v.res = l.res ? (T*)(w + l.res) : nullptr;
     v.obs_w = (float*)(w + l.obs_w);
+    v.n_fac = p->n_fac;
+    v.fac_cam = (const uint32_t*)(w + l.fac_cam);
+    v.fac_meas = (const double*)(w + l.fac_meas);
+    v.fac_sqrt = (const double*)(w + l.fac_sqrt);
+    v.fac_J = (float*)(w + l.fac_J);
     v.st = (DevState*)(w + l.state);
     v.partials = (double*)(w + l.partials);
     v.staging = w + l.staging;
@@ -461,6 +473,51 @@ ba_status ba_workspace_size(const ba_problem* p, size_t* bytes) {
     return BA_OK;
 }
 
+ba_status ba_set_pose_factors(ba_problem* p, int32_t n, const uint32_t* cam_a, const uint32_t* cam_b,
+                              const double* meas, const double* sqrt_info) {
+    if (!p) {
+        set_error("ba_set_pose_factors: null problem");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->bound) {
+        set_error("ba_set_pose_factors: the problem is bound; set factors before ba_bind_workspace");
+        return BA_ERR_INVALID_ARG;
+    }
+    if (p->precision != BA_PREC_MIXED) {
+        set_error("ba_set_pose_factors: pose factors are available for the mixed-precision form only");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    if (n < 0 || (n > 0 && (!cam_a || !cam_b || !meas))) {
+        set_error("ba_set_pose_factors: bad count or null array");
+        return BA_ERR_INVALID_ARG;
+    }
+    for (int32_t k = 0; k < n; ++k) {
+        if (cam_a[k] >= (uint32_t)p->n_cams || cam_b[k] >= (uint32_t)p->n_cams || cam_a[k] == cam_b[k]) {
+            set_error("ba_set_pose_factors: factor %d ties cameras %u and %u", k, cam_a[k], cam_b[k]);
+            return BA_ERR_INVALID_ARG;
+        }
+        for (int i = 0; i < 6; ++i) {
+            const double m = meas[6 * (size_t)k + i];
+            const double w = sqrt_info ? sqrt_info[6 * (size_t)k + i] : 1.0;
+            if (!std::isfinite(m) || !std::isfinite(w) || w < 0.0) {
+                set_error("ba_set_pose_factors: factor %d has a non-finite value or a negative weight", k);
+                return BA_ERR_INVALID_ARG;
+            }
+        }
+    }
+    p->n_fac = n;
+    p->fac_cam.resize(2 * (size_t)n);
+    p->fac_meas.assign(meas, meas + 6 * (size_t)n);
+    p->fac_sqrt.assign(6 * (size_t)n, 1.0);
+    for (int32_t k = 0; k < n; ++k) {
+        p->fac_cam[2 * (size_t)k] = cam_a[k];
+        p->fac_cam[2 * (size_t)k + 1] = cam_b[k];
+    }
+    if (sqrt_info) p->fac_sqrt.assign(sqrt_info, sqrt_info + 6 * (size_t)n);
+    p->lay = compute_layout(p->n_cams, p->n_pts, p->n_obs, p->precision, n);
+    return BA_OK;
+}
+
 static ba_status check_bound(const ba_problem* p, const char* who) {
     if (!p) {
         set_error("%s: null problem", who);
@@ -477,8 +534,9 @@ static ba_status write_options(ba_problem* p, const ba_options* o);
 
 // Persistent PCG plan: one CTA per SM, contiguous tile runs balanced by observation
 // count; a form is used only when every CTA's keys and point state fit in its shared
-// memory.  Each CTA lists the cameras of its observations; a camera that no
-// observation sees is listed by CTA c % G, and the first list holding a camera owns it.
+// memory.  Each CTA lists the cameras of its observations and of its pose factors
+// (factor k runs in CTA k % G); a camera that neither sees is listed by CTA c % G, and
+// the first list holding a camera owns it.
 static ba_status plan_persistent(ba_problem* p, int sms) {
     const int nt = p->n_tiles;
     std::vector<uint32_t> off((size_t)nt + 1);
@@ -518,6 +576,15 @@ static ba_status plan_persistent(ba_problem* p, int sms) {
         cb.erase(std::unique(cb.begin(), cb.end()), cb.end());
         for (uint32_t c : cb) seen[c] = 1;
     }
+    // pose factor k runs in CTA k % G, which lists both of its cameras
+    for (int32_t k = 0; k < p->n_fac; ++k)
+        for (int e = 0; e < 2; ++e) {
+            const uint32_t c = p->fac_cam[2 * (size_t)k + e];
+            std::vector<uint32_t>& cb = lists[k % G];
+            auto it = std::lower_bound(cb.begin(), cb.end(), c);
+            if (it == cb.end() || *it != c) cb.insert(it, c);
+            seen[c] = 1;
+        }
     for (int c = 0; c < p->n_cams; ++c)
         if (!seen[c]) {
             std::vector<uint32_t>& cb = lists[c % G];
@@ -627,6 +694,11 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
     // the scratch overlapped the solver arrays: clear them before first use
     const size_t ub = l.vec[0];
     GBBA_CUDA(cudaMemsetAsync(w + ub, 0, l.total - ub, s));
+    if (p->n_fac > 0) {   // pose factors live among the solver arrays
+        GBBA_CUDA(cudaMemcpyAsync(w + l.fac_cam, p->fac_cam.data(), 4 * p->fac_cam.size(), cudaMemcpyHostToDevice, s));
+        GBBA_CUDA(cudaMemcpyAsync(w + l.fac_meas, p->fac_meas.data(), 8 * p->fac_meas.size(), cudaMemcpyHostToDevice, s));
+        GBBA_CUDA(cudaMemcpyAsync(w + l.fac_sqrt, p->fac_sqrt.data(), 8 * p->fac_sqrt.size(), cudaMemcpyHostToDevice, s));
+    }
     GBBA_CUDA(cudaStreamSynchronize(s));
     p->blk_tile = (uint32_t*)(w + l.blk_tile);
     p->blk_cam_off = (uint32_t*)(w + l.blk_cam_off);
@@ -799,6 +871,10 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
     if ((st = check_options(o))) return st;
     if (o->solver == 1 && p->precision != BA_PREC_MIXED) {
         set_error("ba_solve: the Schur-complement solver is available for the mixed-precision form only");
+        return BA_ERR_NOT_IMPLEMENTED;
+    }
+    if (o->solver == 1 && p->n_fac > 0) {
+        set_error("ba_solve: the Schur-complement solver does not take pose factors");
         return BA_ERR_NOT_IMPLEMENTED;
     }
     if ((st = write_options(p, o))) return st;

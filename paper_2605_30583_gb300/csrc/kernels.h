@@ -47,6 +47,9 @@ void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, Co
 // Schur-complement PCG (kernels_mixed.cu): mode 0 right-hand side, 1 operator, 2 back-substitution
 void launch_schur(const Views<float>& v, cudaStream_t s, int mode, const int32_t* gate);
 void launch_schur_start(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
+// pose factors (pose_factor.cu); no-ops without factors
+void launch_factor_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode);
+void launch_factor_eval(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
 void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
 void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
 void launch_commit(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);

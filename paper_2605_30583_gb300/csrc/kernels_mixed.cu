@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(TB) k_linearize(Views<float> v, int mode, floa
     double in[1] = {(double)cost}, out[1];
     if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_LIN], out) && threadIdx.x == 0) {
         DevState* st = v.st;
-        const double F = 0.5 * out[0];
+        const double F = 0.5 * out[0] + (v.n_fac > 0 ? st->fac_cost : 0.0);   // pose factors: k_factor_linearize
         st->cost_out = F;
         if (mode == 0) {
             st->F = F;
@@ -437,6 +437,15 @@ __global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* ga
         __syncthreads();
         for (int i = threadIdx.x; i < 3 * npt; i += TB) v.q[base + i] = fmaf(mu * v.D[base + i], sd[i], sq[i]);
         __syncthreads();
+    }
+    // pose factors: camera-only rows of J
+    for (int k = blockIdx.x * TB + threadIdx.x; k < v.n_fac; k += gridDim.x * TB) {
+        const uint32_t ca = v.fac_cam[2 * (size_t)k], cb = v.fac_cam[2 * (size_t)k + 1];
+        float da[9], db[9];
+        camera_dir(v, ca, zs, pc_old, beta, da);
+        camera_dir(v, cb, zs, pc_old, beta, db);
+        jp2 += factor_normal(v.fac_J + 72 * (size_t)k, da, db, v.cam_acc + (size_t)ca * CA_STRIDE,
+                             v.cam_acc + (size_t)cb * CA_STRIDE);
     }
     const double bj = block_sum((double)jp2, red);
     const double bp = block_sum((double)pdp, red);
@@ -718,7 +727,9 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
     }
     double in[2] = {fnew, jh2}, out[2];
     if (grid_reduce<2>(in, v.partials, &st->tickets[TK_COST], out) && threadIdx.x == 0) {
-        lm_decide(st, active, 0.5 * out[0], out[1]);
+        // pose factors: k_factor_eval ran just before
+        const bool fac = v.n_fac > 0;
+        lm_decide(st, active, 0.5 * out[0] + (fac ? st->fac_cost_new : 0.0), out[1] + (fac ? st->fac_jh2 : 0.0));
         if (use_cond) cudaGraphSetConditional(lm_cond, st->lm_active ? 1u : 0u);
     }
 }
@@ -1095,6 +1106,7 @@ void launch_camera_precompute(const Views<float>& v, const LaunchCfg& L, cudaStr
 }
 void launch_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode,
                       float* res_out, float* jac_out, CondHandle lm_cond, int use_cond) {
+    launch_factor_linearize(v, L, s, mode);   // its cost is added by k_linearize
     k_linearize<LIN_TB><<<grid_tiles(L.lin_grid, v.n_tiles), LIN_TB, 0, s>>>(v, mode, res_out, jac_out,
                                                                              lm_cond, use_cond);
 }
@@ -1124,6 +1136,7 @@ void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s)
     k_candidate<<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v);
 }
 void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
+    launch_factor_eval(v, L, s);
     k_eval_candidate<EV_TB><<<grid_tiles(L.ev_grid, v.n_tiles), EV_TB, 0, s>>>(v, c, use);
 }
 void launch_commit(const Views<float>& v, const LaunchCfg& L, cudaStream_t s) {

@@ -65,12 +65,15 @@ struct IterRec {
     int64_t t_ns;
 };
 
-enum : int { TK_LIN = 0, TK_COST, TK_PRE, TK_DIR, TK_MV, TK_UPD, TK_CAND, TK_MISC, TK_COUNT = 16 };
+enum : int { TK_LIN = 0, TK_COST, TK_PRE, TK_DIR, TK_MV, TK_UPD, TK_CAND, TK_MISC, TK_FAC, TK_FACEV, TK_COUNT = 16 };
 
 struct DevState {
     DevOptions opt;
     double mu, nu, F, F_new, F0, rho, L, gh, jh2;
     double rz, rr0, rr, alpha, beta, pDp, jp2, cost_out;
+    // pose factors: 1/2 sum |r_f|^2 at the linearisation point and at the candidate,
+    // and |J_f h|^2 (written by the factor kernels, added by the observation kernels)
+    double fac_cost, fac_cost_new, fac_jh2;
     // Per-iteration sums, spread over NSLOT slots (block b adds into slot b % NSLOT,
     // one 128-byte line each) so concurrent atomics do not queue on one address.
     double acc_mv[NSLOT * SLOT_STRIDE];   // k = 0: |J p|^2, k = 1: p^T D p
@@ -114,6 +117,12 @@ struct Views {
     T* jac;           // plain form only: stored Jacobian [n_obs][2][12]
     T* res;           // plain form only: stored residuals [n_obs][2]
     float* obs_w;     // IRLS weights of the robust loss, solver observation order [n_obs]
+    // pose factors (relative pose of two cameras), n_fac of them
+    int32_t n_fac;
+    const uint32_t* fac_cam;   // [n_fac][2]: cameras a, b
+    const double* fac_meas;    // [n_fac][6]: rotation vector and translation of the measurement
+    const double* fac_sqrt;    // [n_fac][6]: square root of the diagonal information
+    float* fac_J;              // [n_fac][6][12]: Jacobian over (phi_a, t_a, phi_b, t_b), scaled
     DevState* st;
     double* partials; // [MAX_GRID][NPART]
     void* staging;    // user-layout parameter staging (FP64, 9 n_cams + 3 n_pts)

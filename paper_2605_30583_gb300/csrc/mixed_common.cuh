@@ -140,5 +140,34 @@ __device__ __forceinline__ float obs_normal(const Cam& cam, const float (&dir)[9
     return WEIGHTED ? w * tt : tt;
 }
 
+// One pose factor in the normal operator: t = J_f (d_a; d_b) over the (phi, t) parts of
+// the two cameras' direction records, J_f^T t added to their camera sums (phi part to
+// entries 0-2, translation part to 3-5, as the observations' sums); returns |t|^2.
+__device__ __forceinline__ float factor_normal(const float* __restrict__ Jf, const float* da, const float* db,
+                                               float* acc_a, float* acc_b) {
+    const float x[12] = {da[CD_PHI], da[CD_PHI + 1], da[CD_PHI + 2], da[CD_T], da[CD_T + 1], da[CD_T + 2],
+                         db[CD_PHI], db[CD_PHI + 1], db[CD_PHI + 2], db[CD_T], db[CD_T + 1], db[CD_T + 2]};
+    float t[6], tt = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        float ti = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 12; ++j) ti = fmaf(__ldg(Jf + 12 * i + j), x[j], ti);
+        t[i] = ti;
+        tt = fmaf(ti, ti, tt);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float ga = 0.0f, gb = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            ga = fmaf(__ldg(Jf + 12 * i + j), t[i], ga);
+            gb = fmaf(__ldg(Jf + 12 * i + 6 + j), t[i], gb);
+        }
+        atomicAdd(acc_a + j, ga);
+        atomicAdd(acc_b + j, gb);
+    }
+    return tt;
+}
 
 }  // namespace gbba

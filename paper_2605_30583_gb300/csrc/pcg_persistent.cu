@@ -12,7 +12,7 @@
 //
 // Two forms of the same Krylov iteration:
 //
-// k_pcg_persistent_twosync (the default form): the textbook recurrences, two
+// k_pcg_persistent (the default form): the textbook recurrences, two
 // exchanges per iteration:
 //   A  p = z + beta p (points in smem; cameras double-buffered in global), then
 //      q = J^T J p + mu D p with |J p|^2 and p^T D p;            -> exchange
@@ -20,7 +20,7 @@
 //      r^T z, |r|^2                                              -> exchange
 //   C  stop test (|r| <= tol |r_0| or the iteration cap), beta.
 //
-// k_pcg_persistent: one exchange per iteration.  The recurrences are arranged as in
+// k_pcg_persistent_1x: one exchange per iteration.  The recurrences are arranged as in
 // the CG of Chronopoulos and Gear (J. Comput. Appl. Math. 25, 1989): with u = M^-1 r,
 // w = A u and s = A p carried by s = w + beta s,
 //   gamma = r^T u,  delta = u^T A u = |J u|^2 + mu u^T D u,
@@ -118,10 +118,20 @@ __device__ bool exchange(DevState* st, double* pslots, unsigned long long epoch,
     return true;
 }
 
+// Local index of camera c in the CTA's sorted camera list (c must be listed).
+__device__ __forceinline__ uint32_t local_cam(const uint32_t* sCid, uint32_t ncb, uint32_t c) {
+    uint32_t lo = 0, hi = ncb;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sCid[mid] <= c) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 }  // namespace
 
 template <int TB>
-__global__ void __launch_bounds__(TB, 1) k_pcg_persistent_twosync(Views<float> v, const uint32_t* __restrict__ blk_tile,
+__global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const uint32_t* __restrict__ blk_tile,
                                                          const uint32_t* __restrict__ blk_cam_off,
                                                          const uint32_t* __restrict__ blk_cams,
                                                          double* __restrict__ pslots) {
@@ -282,6 +292,13 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_twosync(Views<float> v
             const bool head = seg_reduce<9>(cur, acc);
             if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
         }
+        // pose factors k = b, b + G, ...: both cameras are in this CTA's list
+        for (int k = blockIdx.x + (int)gridDim.x * tid; k < v.n_fac; k += (int)gridDim.x * TB) {
+            const uint32_t ca = v.fac_cam[2 * (size_t)k], cb2 = v.fac_cam[2 * (size_t)k + 1];
+            jp2 += factor_normal(v.fac_J + 72 * (size_t)k, sDir + 12 * local_cam(sCid, ncb, ca),
+                                 sDir + 12 * local_cam(sCid, ncb, cb2), v.cam_acc + (size_t)ca * CA_STRIDE,
+                                 v.cam_acc + (size_t)cb2 * CA_STRIDE);
+        }
         double sj, sp;
         {
             double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
@@ -431,7 +448,7 @@ __device__ __forceinline__ void warp_partials3(float a, float b, float c, double
 }  // namespace
 
 template <int TB>
-__global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const uint32_t* __restrict__ blk_tile,
+__global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, const uint32_t* __restrict__ blk_tile,
                                                          const uint32_t* __restrict__ blk_cam_off,
                                                          const uint32_t* __restrict__ blk_cams,
                                                          double* __restrict__ pslots) {
@@ -601,6 +618,13 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
             const bool head = seg_reduce<9>(cur, acc);
             if (head && cur != NO_CAM) flush_matvec(cacc + (size_t)cur * CA_STRIDE, acc);
         }
+        // pose factors k = b, b + G, ...: both cameras are in this CTA's list
+        for (int k = blockIdx.x + (int)gridDim.x * tid; k < v.n_fac; k += (int)gridDim.x * TB) {
+            const uint32_t ca = v.fac_cam[2 * (size_t)k], cb2 = v.fac_cam[2 * (size_t)k + 1];
+            jj += factor_normal(v.fac_J + 72 * (size_t)k, sDir + 12 * local_cam(sCid, ncb, ca),
+                                sDir + 12 * local_cam(sCid, ncb, cb2), cacc + (size_t)ca * CA_STRIDE,
+                                cacc + (size_t)cb2 * CA_STRIDE);
+        }
         jj = warp_sumf(jj);
         if ((tid & 31) == 0) red_m[tid >> 5] = (double)jj;
         __syncthreads();
@@ -753,8 +777,8 @@ int persistent_max_smem() {
 }
 
 cudaError_t persistent_prepare(int form, int smem_bytes, int* blocks_per_sm) {
-    const void* f = form == PCG_TWO_EXCHANGE ? (const void*)k_pcg_persistent_twosync<PCG_TB>
-                                            : (const void*)k_pcg_persistent<PCG_TB>;
+    const void* f = form == PCG_TWO_EXCHANGE ? (const void*)k_pcg_persistent<PCG_TB>
+                                            : (const void*)k_pcg_persistent_1x<PCG_TB>;
     cudaError_t e = ensure_dynamic_smem(f, smem_bytes);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, PCG_TB, smem_bytes);
@@ -774,8 +798,8 @@ cudaError_t launch_pcg_persistent(const Views<float>& v, const uint32_t* blk_til
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (form == PCG_TWO_EXCHANGE)
-        return cudaLaunchKernelEx(&cfg, k_pcg_persistent_twosync<PCG_TB>, v, blk_tile, blk_cam_off, blk_cams, pslots);
-    return cudaLaunchKernelEx(&cfg, k_pcg_persistent<PCG_TB>, v, blk_tile, blk_cam_off, blk_cams, pslots);
+        return cudaLaunchKernelEx(&cfg, k_pcg_persistent<PCG_TB>, v, blk_tile, blk_cam_off, blk_cams, pslots);
+    return cudaLaunchKernelEx(&cfg, k_pcg_persistent_1x<PCG_TB>, v, blk_tile, blk_cam_off, blk_cams, pslots);
 }
 
 }  // namespace gbba

@@ -28,6 +28,7 @@ struct Layout {
     size_t blk_tile, blk_cam_off, blk_cams, pslots;
     size_t cam_pre, cam_pre_new, cam_dir, cam_acc, pc, cam_lin, cam_H, cam64, cam64_new, cam_H64, pt_H, Minv_c, Minv_p, jac, res, obs_w,
         staging;
+    size_t fac_cam, fac_meas, fac_sqrt, fac_J;
     size_t s_cam_idx, s_pt_idx, s_pixels, s_pt_key, s_tile_cnt, s_keys, s_vals, sort_cap;
     size_t total;
 };
@@ -45,6 +46,11 @@ struct ba_problem {
     int32_t precision = BA_PREC_MIXED;
     std::vector<uint32_t> cam_idx, pt_idx;
     std::vector<double> pixels;
+    // pose factors (set before the workspace is bound)
+    int32_t n_fac = 0;
+    std::vector<uint32_t> fac_cam;   // [n_fac][2]
+    std::vector<double> fac_meas;    // [n_fac][6]
+    std::vector<double> fac_sqrt;    // [n_fac][6]
     int64_t pt_off = 0, n_vec = 0;
     gbba::Layout lay{};
     // bound state
@@ -75,7 +81,7 @@ struct ba_problem {
 };
 
 namespace gbba {
-Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t precision);
+Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t precision, int32_t n_fac = 0);
 template <typename T>
 Views<T> make_views(ba_problem* p);
 }  // namespace gbba

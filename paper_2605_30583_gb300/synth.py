@@ -192,6 +192,41 @@ def make_batch(n_problems: int = 512, seed: int = 30000, cams=(5, 60), pts=(200,
     return out
 
 
+def make_pose_factors(p: Problem, pairs: str = "chain", rot_sigma: float = 0.002, t_sigma: float = 0.01,
+                      seed: int = 7, noise: bool = True) -> tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray]:
+    """Relative-pose measurements between cameras of `p`, from its ground truth plus noise.
+
+    pairs: "chain" ties camera i to i + 1 around the ring (odometry, n_cams factors
+    with the loop closed), "chain+skip" adds i to i + 2.  The measurement of (a, b) is
+    the pose of b relative to a, computed here with rotation matrices: R_ab_gt =
+    R_b R_a^T and t_ab_gt = t_b - R_ab_gt t_a, then perturbed by a left rotation
+    Exp(rot_sigma n) (n ~ N(0, I3)) and N(0, t_sigma^2 I3) on the translation.
+    Returns cam_a, cam_b (uint32), meas [nf, 6] (rotation vector, translation) and
+    sqrt_info [nf, 6] = (1 / rot_sigma, 1 / t_sigma) per row.  noise=False returns the
+    exact relative poses (same weights)."""
+    rng = np.random.default_rng(seed)
+    n = p.n_cams
+    a = np.arange(n)
+    b = (a + 1) % n
+    if pairs == "chain+skip":
+        a = np.concatenate([a, np.arange(n)])
+        b = np.concatenate([b, (np.arange(n) + 2) % n])
+    elif pairs != "chain":
+        raise ValueError(pairs)
+    keep = a != b
+    a, b = a[keep], b[keep]
+    Rm = Rotation.from_rotvec(p.cams_gt[:, 0:3]).as_matrix()
+    R_ab = np.einsum("kij,klj->kil", Rm[b], Rm[a])                     # R_b R_a^T
+    t_ab = p.cams_gt[b, 3:6] - np.einsum("kij,kj->ki", R_ab, p.cams_gt[a, 3:6])
+    scale = 1.0 if noise else 0.0
+    dR = Rotation.from_rotvec(scale * rot_sigma * rng.standard_normal((a.size, 3))).as_matrix()
+    meas_R = np.einsum("kij,kjl->kil", dR, R_ab)
+    meas = np.concatenate([Rotation.from_matrix(meas_R).as_rotvec(),
+                           t_ab + scale * t_sigma * rng.standard_normal((a.size, 3))], axis=1)
+    sqrt_info = np.tile(np.array([1.0 / rot_sigma] * 3 + [1.0 / t_sigma] * 3), (a.size, 1))
+    return a.astype(np.uint32), b.astype(np.uint32), meas, sqrt_info
+
+
 def round_to_f32(p: Problem) -> Problem:
     """Same problem with every real input rounded to FP32, so an FP32 device path and an
     FP64 reference see bit-identical inputs."""

@@ -86,3 +86,37 @@ def test_workspace_grows_with_problem_and_fp64_is_larger(lib):
         sizes[prec] = n.value
         lib.ba_problem_destroy(h)
     assert sizes[1] > sizes[0]
+
+
+def test_pose_factor_validation_without_gpu(lib):
+    """ba_set_pose_factors checks indices, values and the form before any device work,
+    and the workspace grows with the factors."""
+    px = np.zeros((4, 2))
+    st, h = _create(3, 2, [0, 1, 2, 0], [0, 0, 1, 1], px)
+    assert st == 0
+    size0 = ctypes.c_size_t()
+    assert lib.ba_workspace_size(h, ctypes.byref(size0)) == 0
+    a = np.array([0, 1], np.uint32)
+    b = np.array([1, 2], np.uint32)
+    meas = np.zeros((2, 6))
+    ok = lib.ba_set_pose_factors(h, 2, a.ctypes.data, b.ctypes.data, meas.ctypes.data, None)
+    assert ok == 0
+    size1 = ctypes.c_size_t()
+    assert lib.ba_workspace_size(h, ctypes.byref(size1)) == 0
+    assert size1.value > size0.value
+    bad = np.array([1, 3], np.uint32)                               # camera 3 does not exist
+    assert lib.ba_set_pose_factors(h, 2, a.ctypes.data, bad.ctypes.data, meas.ctypes.data, None) == 1
+    same = np.array([0, 1], np.uint32)                              # a factor tying camera 0 to itself
+    assert lib.ba_set_pose_factors(h, 2, a.ctypes.data, same.ctypes.data, meas.ctypes.data, None) == 1
+    nan = meas.copy()
+    nan[1, 4] = np.nan
+    assert lib.ba_set_pose_factors(h, 2, a.ctypes.data, b.ctypes.data, nan.ctypes.data, None) == 1
+    neg = -np.ones((2, 6))
+    assert lib.ba_set_pose_factors(h, 2, a.ctypes.data, b.ctypes.data, meas.ctypes.data, neg.ctypes.data) == 1
+    assert lib.ba_set_pose_factors(h, 0, None, None, None, None) == 0   # removes them
+    size2 = ctypes.c_size_t()
+    assert lib.ba_workspace_size(h, ctypes.byref(size2)) == 0 and size2.value == size0.value
+    lib.ba_problem_destroy(h)
+    st, h = _create(3, 2, [0, 1, 2, 0], [0, 0, 1, 1], px, prec=1)   # plain FP64 form
+    assert lib.ba_set_pose_factors(h, 2, a.ctypes.data, b.ctypes.data, meas.ctypes.data, None) == 6
+    lib.ba_problem_destroy(h)

@@ -4,7 +4,7 @@ copy of the oracle (on the CPU, in a temporary tree) and the pin suite must fail
 The mutations are the mistakes a restatement of the method could make: a dropped
 Rodrigues or distortion term, a wrong sign or index, a wrong damping, gain-ratio or
 Madsen constant, a transposed block, an inverted CG coefficient, a retraction applied
-on the wrong side.
+on the wrong side, a pose factor with its measurement, sign or camera block wrong.
 """
 import os
 import shutil
@@ -34,6 +34,14 @@ MUTATIONS = {
     "cauchy_weight_squared": ("return 1.0 / (1.0 + s / d2)", "return 1.0 / (1.0 + s / d2) ** 2"),
     "schur_rhs_sign": ("b = -gc + Jc.T @ (Jp @ hpp_inv(gp))", "b = -gc - Jc.T @ (Jp @ hpp_inv(gp))"),
     "schur_backsub_sign": ("hp = hpp_inv(-gp - Jp.T @ (Jc @ hc))", "hp = hpp_inv(-gp + Jp.T @ (Jc @ hc))"),
+    "pose_measurement_not_inverted": ("cols = [rotate([-wm[0], -wm[1], -wm[2]], rot_ba(e)) for e in",
+                                      "cols = [rotate([wm[0], wm[1], wm[2]], rot_ba(e)) for e in"),
+    "pose_translation_sign": ("rt = [tb[i] - Rt[i] - tm[i] for i in range(3)]",
+                              "rt = [tb[i] + Rt[i] - tm[i] for i in range(3)]"),
+    "pose_block_to_wrong_camera": ("np.add.at(Hc, np.asarray(factors.cam_b, np.int64), np.einsum(\"oki,okj->oij\", Jb, Jb))",
+                                   "np.add.at(Hc, np.asarray(factors.cam_a, np.int64), np.einsum(\"oki,okj->oij\", Jb, Jb))"),
+    "pose_cost_dropped_from_candidate": ("return F if factors is None else F + pose_factor_cost(c, factors)",
+                                         "return F"),
 }
 
 

@@ -504,3 +504,118 @@ def test_lm_schur_reaches_the_pcgnr_optimum():
         out[sv] = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, opts)
     a, b = out["pcgnr"].final_cost, out["schur"].final_cost
     assert abs(a - b) <= 1e-9 * a
+
+
+# ---------------------------------------------------------------- pose factors -----
+
+
+def _factors(p, noise=True, pairs="chain+skip", seed=3):
+    fa, fb, meas, sq = synth.make_pose_factors(p, pairs=pairs, seed=seed, noise=noise)
+    return O.PoseFactors(fa, fb, meas, sq)
+
+
+def test_pose_factor_zero_at_exact_measurements():
+    p = _small_problem(n_cams=6)
+    f = _factors(p, noise=False)
+    assert np.abs(O.pose_factor_residuals(p.cams_gt, f)).max() < 1e-9
+    assert O.pose_factor_cost(p.cams_init, f) > 1.0   # the perturbed start is off
+
+
+def test_pose_factor_rows_match_scipy():
+    """Rotation rows = s * rotvec(R_m^T R_b R_a^T), translation rows = s * (t_b - R_b R_a^T
+    t_a - t_m), both computed through scipy's rotations."""
+    p = _small_problem(n_cams=6)
+    rng = np.random.default_rng(5)
+    cams = p.cams_init.copy()
+    cams[:, 0:3] += rng.normal(0, 0.3, (6, 3))
+    f = _factors(p)
+    f.sqrt_info = rng.uniform(0.5, 3.0, f.sqrt_info.shape)
+    r = O.pose_factor_residuals(cams, f)
+    Ra, Rb = Rotation.from_rotvec(cams[f.cam_a, 0:3]), Rotation.from_rotvec(cams[f.cam_b, 0:3])
+    Rm = Rotation.from_rotvec(f.meas[:, 0:3])
+    rot = (Rm.inv() * Rb * Ra.inv()).as_rotvec()
+    tr = cams[f.cam_b, 3:6] - (Rb * Ra.inv()).apply(cams[f.cam_a, 3:6]) - f.meas[:, 3:6]
+    np.testing.assert_allclose(r, f.sqrt_info * np.concatenate([rot, tr], axis=1), atol=1e-12, rtol=1e-10)
+
+
+@pytest.mark.parametrize("retraction", [False, True])
+def test_pose_factor_jacobian_matches_central_differences(retraction):
+    p = _small_problem(n_cams=6)
+    rng = np.random.default_rng(6)
+    cams = p.cams_init.copy()
+    cams[:, 0:3] += rng.normal(0, 0.3, (6, 3))
+    f = _factors(p)
+    f.sqrt_info = rng.uniform(0.5, 3.0, f.sqrt_info.shape)
+    _, Ja, Jb = O.pose_factor_blocks(cams, f, retraction=retraction)
+    eps = 1e-6
+    for c in range(6):
+        for k in range(9):
+            cp, cm = cams.copy(), cams.copy()
+            if retraction and k < 3:   # left step Exp(d) R(w), through scipy's composition
+                d = np.zeros(3)
+                d[k] = eps
+                cp[c, 0:3] = (Rotation.from_rotvec(d) * Rotation.from_rotvec(cams[c, 0:3])).as_rotvec()
+                cm[c, 0:3] = (Rotation.from_rotvec(-d) * Rotation.from_rotvec(cams[c, 0:3])).as_rotvec()
+            else:
+                cp[c, k] += eps
+                cm[c, k] -= eps
+            fd = (O.pose_factor_residuals(cp, f) - O.pose_factor_residuals(cm, f)) / (2 * eps)
+            an = (f.cam_a == c)[:, None] * Ja[:, :, k] + (f.cam_b == c)[:, None] * Jb[:, :, k]
+            np.testing.assert_allclose(an, fd, atol=2e-6 * max(1.0, np.abs(fd).max()))
+
+
+def test_pose_factor_is_invariant_to_a_world_transform():
+    """X' = R_w X + t_w changes each camera to (R_c R_w^T, t_c - R_c R_w^T t_w); relative
+    poses, hence the residuals, do not change."""
+    p = _small_problem(n_cams=6)
+    f = _factors(p)
+    Rw = Rotation.from_rotvec([0.3, -0.7, 1.1])
+    tw = np.array([2.0, -1.0, 0.5])
+    cams = p.cams_init.copy()
+    Rc = Rotation.from_rotvec(cams[:, 0:3])
+    moved = cams.copy()
+    moved[:, 0:3] = (Rc * Rw.inv()).as_rotvec()
+    moved[:, 3:6] = cams[:, 3:6] - (Rc * Rw.inv()).apply(np.tile(tw, (6, 1)))
+    np.testing.assert_allclose(O.pose_factor_residuals(moved, f), O.pose_factor_residuals(cams, f), atol=1e-9)
+
+
+def test_linearize_with_factors_appends_rows():
+    """F, g and the camera blocks of J^T J with factors = the observation part plus the
+    factor part assembled densely from the factor blocks."""
+    p = _small_problem(n_cams=5, n_pts=30)
+    f = _factors(p)
+    base = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels)
+    lin = O.linearize(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, factors=f)
+    r, Ja, Jb = O.pose_factor_blocks(p.cams_init, f)
+    assert abs(lin.F - base.F - 0.5 * np.sum(r * r)) < 1e-9 * lin.F
+    n = lin.J.shape[1]
+    Jf = np.zeros((6 * len(f.cam_a), n))
+    for k, (a, b) in enumerate(zip(f.cam_a, f.cam_b)):
+        Jf[6 * k:6 * k + 6, 9 * a:9 * a + 9] += Ja[k]
+        Jf[6 * k:6 * k + 6, 9 * b:9 * b + 9] += Jb[k]
+    np.testing.assert_allclose(lin.g, base.g + Jf.T @ r.reshape(-1), rtol=1e-10, atol=1e-8)
+    Hf = Jf.T @ Jf
+    for c in range(p.n_cams):
+        np.testing.assert_allclose(lin.Hc[c], base.Hc[c] + Hf[9 * c:9 * c + 9, 9 * c:9 * c + 9], rtol=1e-10, atol=1e-8)
+
+
+def test_lm_with_exact_factors_reaches_zero_cost():
+    """Noise-free pixels and exact relative poses: the optimum has zero cost and LM gets
+    there from the perturbed start."""
+    p = synth.make_problem(8, 200, ("poisson", 3.0), "uniform", seed=12, noise_px=0.0)
+    f = _factors(p, noise=False)
+    res = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, O.LMOptions(max_lm_iters=30), factors=f)
+    assert res.initial_cost > 1e3
+    assert res.final_cost < 1e-8 * res.initial_cost
+
+
+def test_lm_with_factors_is_monotone_and_stationary():
+    p = _small_problem(seed=9, n_cams=6, n_pts=60)
+    f = _factors(p)
+    res = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels,
+                     O.LMOptions(max_lm_iters=60, pcg_rel_tol=1e-10, max_pcg_iters=500), factors=f)
+    costs = [h["cost"] for h in res.history] + [res.final_cost]
+    assert all(a >= b for a, b in zip(costs, costs[1:]))
+    c, q = O.unpack(res.x, p.n_cams)
+    lin = O.linearize(c, q, p.cam_idx, p.pt_idx, p.pixels, factors=f)
+    assert np.linalg.norm(lin.g) < 1e-6 * np.sqrt(lin.F)
