@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-schur", action="store_true")
+    ap.add_argument("--no-factors", action="store_true")
     ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1, 2],
                     help="1: conditional-loop graph; 2: unrolled predicated graph; 0: host-enqueued sequence")
     return ap.parse_args()
@@ -130,7 +131,7 @@ def matvec_model(prob):
 # DRAM bytes (read + write) per 50-iteration launch of k_pcg_persistent, from one ncu
 # capture of the same workload and launch (profiles/k_pcg_persistent_medium.md).  Set to
 # None whenever the kernel changes until it is captured again.
-PCG_TRAFFIC = {}
+PCG_TRAFFIC = {"medium": 19967488}
 
 
 def pcg_iter_model(prob):
@@ -435,6 +436,35 @@ def run_ours(args, rank, world, local_rank):
                  "pcg_iters_per_s": pc / (sum(ms) / 1e3), "final_cost": sst.final_cost,
                  "time_to_cost_ms": time_to_cost(sst.history, target * (1 + 1e-4) if target else None)}
 
+    # ---- the same problem with relative-pose factors between cameras (odometry chain
+    # plus skip links, 2 per camera): the generic-factor path
+    factors = None
+    if not args.no_factors:
+        fa, fb, fm, fs = synth.make_pose_factors(prob, pairs="chain+skip", seed=5)
+        pf = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels,
+                             pose_factors=(fa, fb, fm, fs))
+        fo = binding.default_options(use_graph=args.graph_mode)
+        pf.set_params(cams0, pts0)
+        pf.solve(fo, wait=False)
+        torch.cuda.synchronize()
+        ms, pc = [], 0
+        for _ in range(max(1, min(3, args.steps))):
+            flush.fill_(5)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pf.set_params(cams0, pts0)
+            pf.solve(fo, wait=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            fst = pf.stats()
+            pc += fst.pcg_iters_total
+        factors = {"n_factors": int(len(fa)), "ms_per_solve": sum(ms) / len(ms), "pcg_iters_per_solve": pc / len(ms),
+                   "pcg_iters_per_s": pc / (sum(ms) / 1e3), "initial_cost": fst.initial_cost,
+                   "final_cost": fst.final_cost, "lm_iters": fst.lm_iters}
+        pf.close()
+
     batched = None if args.no_batch else run_batched(args, binding, synth, torch, dev, stream, flush, rank)
 
     launches_per_step = 1 + 3 + 5 * last.lm_iters + 3 * last.pcg_iters_total + 1
@@ -450,7 +480,7 @@ def run_ours(args, rank, world, local_rank):
         "time_to_cost_ms": ttc, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
         "step_ms": step_ms,
         "roofline": roofline, "roofline_matvec": other,
-        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "schur": schur, "batched": batched, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "schur": schur, "pose_factors": factors, "batched": batched, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob)

@@ -50,6 +50,8 @@ void launch_schur_start(const Views<float>& v, const LaunchCfg& L, cudaStream_t 
 // pose factors (pose_factor.cu); no-ops without factors
 void launch_factor_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode);
 void launch_factor_eval(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
+void launch_factor_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
+                          const float* zs, int use_beta);
 void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);
 void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
 void launch_commit(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);

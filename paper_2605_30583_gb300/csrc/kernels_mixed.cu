@@ -438,15 +438,6 @@ __global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* ga
         for (int i = threadIdx.x; i < 3 * npt; i += TB) v.q[base + i] = fmaf(mu * v.D[base + i], sd[i], sq[i]);
         __syncthreads();
     }
-    // pose factors: camera-only rows of J
-    for (int k = blockIdx.x * TB + threadIdx.x; k < v.n_fac; k += gridDim.x * TB) {
-        const uint32_t ca = v.fac_cam[2 * (size_t)k], cb = v.fac_cam[2 * (size_t)k + 1];
-        float da[9], db[9];
-        camera_dir(v, ca, zs, pc_old, beta, da);
-        camera_dir(v, cb, zs, pc_old, beta, db);
-        jp2 += factor_normal(v.fac_J + 72 * (size_t)k, da, db, v.cam_acc + (size_t)ca * CA_STRIDE,
-                             v.cam_acc + (size_t)cb * CA_STRIDE);
-    }
     const double bj = block_sum((double)jp2, red);
     const double bp = block_sum((double)pdp, red);
     if (threadIdx.x == 0) {
@@ -1116,8 +1107,8 @@ void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, C
 }
 void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                    const float* zs, int use_beta) {
-    (void)L;
     k_matvec<MV_TB><<<v.n_tiles > 0 ? v.n_tiles : 1, MV_TB, 0, s>>>(v, gate, zs, use_beta);
+    launch_factor_matvec(v, L, s, gate, zs, use_beta);   // pose factors, if any
 }
 void launch_schur(const Views<float>& v, cudaStream_t s, int mode, const int32_t* gate) {
     const int grid = v.n_tiles > 0 ? v.n_tiles : 1;

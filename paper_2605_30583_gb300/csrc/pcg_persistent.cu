@@ -128,6 +128,20 @@ __device__ __forceinline__ uint32_t local_cam(const uint32_t* sCid, uint32_t ncb
     return lo;
 }
 
+// Pose factors k = b, b + G, ... of CTA b through the operator (both cameras of each
+// are in the CTA's list): returns this thread's part of |J_f d|^2.
+__device__ __forceinline__ float factor_pass(const Views<float>& v, const uint32_t* sCid, uint32_t ncb,
+                                          const float* sDir, float* acc, int stride) {
+    float jj = 0.0f;
+    for (int k = blockIdx.x + (int)gridDim.x * (int)threadIdx.x; k < v.n_fac; k += stride) {
+        const uint32_t ca = v.fac_cam[2 * (size_t)k], cb = v.fac_cam[2 * (size_t)k + 1];
+        jj += factor_normal(v.fac_J + 72 * (size_t)k, sDir + 12 * local_cam(sCid, ncb, ca),
+                            sDir + 12 * local_cam(sCid, ncb, cb), acc + (size_t)ca * CA_STRIDE,
+                            acc + (size_t)cb * CA_STRIDE);
+    }
+    return jj;
+}
+
 }  // namespace
 
 template <int TB>
@@ -292,13 +306,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
             const bool head = seg_reduce<9>(cur, acc);
             if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
         }
-        // pose factors k = b, b + G, ...: both cameras are in this CTA's list
-        for (int k = blockIdx.x + (int)gridDim.x * tid; k < v.n_fac; k += (int)gridDim.x * TB) {
-            const uint32_t ca = v.fac_cam[2 * (size_t)k], cb2 = v.fac_cam[2 * (size_t)k + 1];
-            jp2 += factor_normal(v.fac_J + 72 * (size_t)k, sDir + 12 * local_cam(sCid, ncb, ca),
-                                 sDir + 12 * local_cam(sCid, ncb, cb2), v.cam_acc + (size_t)ca * CA_STRIDE,
-                                 v.cam_acc + (size_t)cb2 * CA_STRIDE);
-        }
+        if (v.n_fac > 0) jp2 += factor_pass(v, sCid, ncb, sDir, v.cam_acc, (int)gridDim.x * TB);
         double sj, sp;
         {
             double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
@@ -618,13 +626,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
             const bool head = seg_reduce<9>(cur, acc);
             if (head && cur != NO_CAM) flush_matvec(cacc + (size_t)cur * CA_STRIDE, acc);
         }
-        // pose factors k = b, b + G, ...: both cameras are in this CTA's list
-        for (int k = blockIdx.x + (int)gridDim.x * tid; k < v.n_fac; k += (int)gridDim.x * TB) {
-            const uint32_t ca = v.fac_cam[2 * (size_t)k], cb2 = v.fac_cam[2 * (size_t)k + 1];
-            jj += factor_normal(v.fac_J + 72 * (size_t)k, sDir + 12 * local_cam(sCid, ncb, ca),
-                                sDir + 12 * local_cam(sCid, ncb, cb2), cacc + (size_t)ca * CA_STRIDE,
-                                cacc + (size_t)cb2 * CA_STRIDE);
-        }
+        if (v.n_fac > 0) jj += factor_pass(v, sCid, ncb, sDir, cacc, (int)gridDim.x * TB);
         jj = warp_sumf(jj);
         if ((tid & 31) == 0) red_m[tid >> 5] = (double)jj;
         __syncthreads();
