@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-schur", action="store_true")
     ap.add_argument("--no-factors", action="store_true")
+    ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1, 2],
                     help="1: conditional-loop graph; 2: unrolled predicated graph; 0: host-enqueued sequence")
     return ap.parse_args()
@@ -131,7 +132,10 @@ def matvec_model(prob):
 # DRAM bytes (read + write) per 50-iteration launch of k_pcg_persistent, from one ncu
 # capture of the same workload and launch (profiles/k_pcg_persistent_medium.md).  Set to
 # None whenever the kernel changes until it is captured again.
-PCG_TRAFFIC = {"medium": 19967488}
+PCG_TRAFFIC = {}
+
+# Nominal HBM3e bandwidth of a GB300 (the second denominator the roofline is quoted on).
+NOMINAL_HBM_GBS = 7900.0
 
 
 def pcg_iter_model(prob):
@@ -310,7 +314,8 @@ def run_ours(args, rank, world, local_rank):
     gbs = nb / (mv_ms / 1e3) / 1e9
     tfl = nf / (mv_ms / 1e3) / 1e12
     roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "frac_of_nominal": gbs / NOMINAL_HBM_GBS}
     roof_alu = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
                 "traffic": None,
                 "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
@@ -335,7 +340,8 @@ def run_ours(args, rank, world, local_rank):
                     "kernel": "k_pcg_persistent (one PCG solve per launch, tiles resident in shared memory)",
                     "us_per_launch": us_pcg, "pcg_iters_per_launch": it_pcg,
                     "algorithmic_bytes_per_pcg_iter": pb, "algorithmic_flops_per_pcg_iter": pf,
-                    "alu_frac": pf * it_pcg / (us_pcg / 1e6) / 1e12 / alu_peak}
+                    "alu_frac": pf * it_pcg / (us_pcg / 1e6) / 1e12 / alu_peak,
+                    "frac_of_nominal": gbs_p / NOMINAL_HBM_GBS}
         # context: the same iterations priced at what a stored-Jacobian form would have
         # to move (96 B of J + 8 B of indices per observation, 36 B per point, 108 B per
         # camera for the operator, plus the same vector traffic)
@@ -436,6 +442,30 @@ def run_ours(args, rank, world, local_rank):
                  "pcg_iters_per_s": pc / (sum(ms) / 1e3), "final_cost": sst.final_cost,
                  "time_to_cost_ms": time_to_cost(sst.history, target * (1 + 1e-4) if target else None)}
 
+    # ---- the same solve with the persistent kernel's one-exchange form (pcg_kernel = 2)
+    one_x = None
+    if not args.no_schur:
+        xo = binding.default_options(use_graph=args.graph_mode, pcg_kernel=2)
+        p.set_params(cams0, pts0)
+        p.solve(xo, wait=False)
+        torch.cuda.synchronize()
+        ms, pc = [], 0
+        for _ in range(max(1, min(3, args.steps))):
+            flush.fill_(5)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.set_params(cams0, pts0)
+            p.solve(xo, wait=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            xst = p.stats()
+            pc += xst.pcg_iters_total
+        one_x = {"ms_per_solve": sum(ms) / len(ms), "pcg_iters_per_solve": pc / len(ms),
+                 "pcg_iters_per_s": pc / (sum(ms) / 1e3), "final_cost": xst.final_cost,
+                 "time_to_cost_ms": time_to_cost(xst.history, target * (1 + 1e-4) if target else None)}
+
     # ---- the same problem with relative-pose factors between cameras (odometry chain
     # plus skip links, 2 per camera): the generic-factor path
     factors = None
@@ -465,6 +495,36 @@ def run_ours(args, rank, world, local_rank):
                    "final_cost": fst.final_cost, "lm_iters": fst.lm_iters}
         pf.close()
 
+    # ---- differentiation pattern: the autograd entries (forward cost, hand-written
+    # adjoint backward) on the 200-camera, 50,000-point workload, time per observation
+    grad_leg = None
+    if not args.no_autograd:
+        from paper_2605_30583_gb300 import autograd as AG
+        ga = synth.make_config("autograd")
+        pg = binding.Problem(ga.n_cams, ga.n_pts, ga.cam_idx, ga.pt_idx, ga.pixels)
+        cams_t = torch.tensor(ga.cams_init, dtype=torch.float32, device=dev, requires_grad=True)
+        pts_t = torch.tensor(ga.pts_init, dtype=torch.float32, device=dev, requires_grad=True)
+        fwd_ms, bwd_ms = [], []
+        for it in range(8):
+            cams_t.grad = None
+            pts_t.grad = None
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            F = AG.reprojection_cost(pg, cams_t, pts_t)
+            e1.record(stream)
+            F.backward()
+            e2.record(stream)
+            e2.synchronize()
+            if it >= 3:   # warm-up first
+                fwd_ms.append(e0.elapsed_time(e1))
+                bwd_ms.append(e1.elapsed_time(e2))
+        fm, bm = sorted(fwd_ms)[len(fwd_ms) // 2], sorted(bwd_ms)[len(bwd_ms) // 2]
+        grad_leg = {"workload": f"autograd: {ga.n_cams} cameras, {ga.n_pts} points, {ga.n_obs} observations, FP32",
+                    "forward_ms": fm, "backward_ms": bm, "forward_ns_per_obs": 1e6 * fm / ga.n_obs,
+                    "backward_ns_per_obs": 1e6 * bm / ga.n_obs,
+                    "note": "median of 5 after 3 warm-up; backward = recompute + scatter of 12 floats per observation"}
+        pg.close()
+
     batched = None if args.no_batch else run_batched(args, binding, synth, torch, dev, stream, flush, rank)
 
     launches_per_step = 1 + 3 + 5 * last.lm_iters + 3 * last.pcg_iters_total + 1
@@ -480,7 +540,8 @@ def run_ours(args, rank, world, local_rank):
         "time_to_cost_ms": ttc, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
         "step_ms": step_ms,
         "roofline": roofline, "roofline_matvec": other,
-        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "schur": schur, "pose_factors": factors, "batched": batched, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "schur": schur, "pcg_one_exchange": one_x, "pose_factors": factors, "autograd": grad_leg, "batched": batched,
+        "memory": {"arena_bytes": p.workspace_bytes, "torch_max_allocated_bytes": torch.cuda.max_memory_allocated()}, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(prob)

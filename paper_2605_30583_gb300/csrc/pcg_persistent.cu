@@ -324,17 +324,39 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
         alpha = rz / denom;
         const float af = (float)alpha;
         float lrz = 0.0f, lrr = 0.0f;
-        // owned cameras: nine threads per camera (one per row), CAMS_PER_PASS per pass
-        for (int j0 = 0; j0 < n_own; j0 += CAMS_PER_PASS) {
-            const int idx = tid;
-            const int j = j0 + idx / 9, i = idx % 9;
-            const bool mine = idx < 9 * CAMS_PER_PASS && j < n_own;
+        // points: all of it in shared memory
+        auto update_points = [&]() {
+            for (int i = tid; i < np; i += TB) {
+                const int e = 3 * i;
+                const float4 p4 = sP4[i];
+                const float pq[3] = {p4.x, p4.y, p4.z};
+                float r3[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float pk = pq[q];
+                    sH[e + q] = fmaf(af, pk, sH[e + q]);
+                    r3[q] = fmaf(-af, fmaf(muf * sD[e + q], pk, sQ[e + q]), sR[e + q]);
+                    sR[e + q] = r3[q];
+                }
+                const float* m = sM + 6 * i;
+                const float z0 = fmaf(m[0], r3[0], fmaf(m[1], r3[1], m[2] * r3[2]));
+                const float z1 = fmaf(m[1], r3[0], fmaf(m[3], r3[1], m[4] * r3[2]));
+                const float z2 = fmaf(m[2], r3[0], fmaf(m[4], r3[1], m[5] * r3[2]));
+                sZ[e] = z0; sZ[e + 1] = z1; sZ[e + 2] = z2;
+                lrz = fmaf(r3[0], z0, fmaf(r3[1], z1, fmaf(r3[2], z2, lrz)));
+                lrr = fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], fmaf(r3[2], r3[2], lrr)));
+            }
+        };
+        if (n_own <= CAMS_PER_PASS) {
+            // owned cameras in one pass, nine threads per camera (one per row); their
+            // global loads go out before the point update, which hides their latency
+            const int j = tid / 9, i = tid - 9 * j;
+            const bool mine = j < n_own;
             const int c = blockIdx.x + (int)gridDim.x * j;
             const size_t e = 9 * (size_t)c + i;
-            float ri = 0.0f;
+            float qi = 0.0f, pk = 0.0f, hk = 0.0f, rk = 0.0f, dk = 0.0f;
             if (mine) {
                 const float* ca = v.cam_acc + (size_t)c * CA_STRIDE;
-                float qi;
                 if (i < 3) {
                     const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
                     qi = fmaf(__ldg(JL + i), __ldcg(ca + 0), fmaf(__ldg(JL + 3 + i), __ldcg(ca + 1),
@@ -342,17 +364,24 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                 } else {
                     qi = __ldcg(ca + i);
                 }
-                const float pk = pc_new[e];
+                pk = pc_new[e];
+                hk = v.h[e];
+                rk = v.r[e];
+                dk = __ldg(v.D + e);
+            }
+            update_points();
+            float ri = 0.0f;
+            if (mine) {
                 v.p[e] = pk;
-                v.h[e] = fmaf(af, pk, v.h[e]);
-                ri = fmaf(-af, fmaf(muf * __ldg(v.D + e), pk, qi), v.r[e]);
+                v.h[e] = fmaf(af, pk, hk);
+                ri = fmaf(-af, fmaf(muf * dk, pk, qi), rk);
                 v.r[e] = ri;
-                s_cam_r[idx] = ri;
+                s_cam_r[tid] = ri;
             }
             __syncthreads();
             if (mine) {
                 const float* M = v.Minv_c + (size_t)c * MC_STRIDE + 9 * i;
-                const float* rr9 = s_cam_r + 9 * (idx / 9);
+                const float* rr9 = s_cam_r + 9 * j;
                 float z = 0.0f;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) z = fmaf(__ldg(M + q), rr9[q], z);
@@ -361,27 +390,47 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                 lrr = fmaf(ri, ri, lrr);
                 v.cam_acc[(size_t)c * CA_STRIDE + i] = 0.0f;
             }
-            __syncthreads();
-        }
-        for (int i = tid; i < np; i += TB) {
-            const int e = 3 * i;
-            const float4 p4 = sP4[i];
-            const float pq[3] = {p4.x, p4.y, p4.z};
-            float r3[3];
+        } else {
+            // owned cameras: nine threads per camera (one per row), CAMS_PER_PASS per pass
+            for (int j0 = 0; j0 < n_own; j0 += CAMS_PER_PASS) {
+                const int idx = tid;
+                const int j = j0 + idx / 9, i = idx % 9;
+                const bool mine = idx < 9 * CAMS_PER_PASS && j < n_own;
+                const int c = blockIdx.x + (int)gridDim.x * j;
+                const size_t e = 9 * (size_t)c + i;
+                float ri = 0.0f;
+                if (mine) {
+                    const float* ca = v.cam_acc + (size_t)c * CA_STRIDE;
+                    float qi;
+                    if (i < 3) {
+                        const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
+                        qi = fmaf(__ldg(JL + i), __ldcg(ca + 0), fmaf(__ldg(JL + 3 + i), __ldcg(ca + 1),
+                                                                  __ldg(JL + 6 + i) * __ldcg(ca + 2)));
+                    } else {
+                        qi = __ldcg(ca + i);
+                    }
+                    const float pk = pc_new[e];
+                    v.p[e] = pk;
+                    v.h[e] = fmaf(af, pk, v.h[e]);
+                    ri = fmaf(-af, fmaf(muf * __ldg(v.D + e), pk, qi), v.r[e]);
+                    v.r[e] = ri;
+                    s_cam_r[idx] = ri;
+                }
+                __syncthreads();
+                if (mine) {
+                    const float* M = v.Minv_c + (size_t)c * MC_STRIDE + 9 * i;
+                    const float* rr9 = s_cam_r + 9 * (idx / 9);
+                    float z = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float pk = pq[q];
-                sH[e + q] = fmaf(af, pk, sH[e + q]);
-                r3[q] = fmaf(-af, fmaf(muf * sD[e + q], pk, sQ[e + q]), sR[e + q]);
-                sR[e + q] = r3[q];
+                    for (int q = 0; q < 9; ++q) z = fmaf(__ldg(M + q), rr9[q], z);
+                    v.z[e] = z;
+                    lrz = fmaf(ri, z, lrz);
+                    lrr = fmaf(ri, ri, lrr);
+                    v.cam_acc[(size_t)c * CA_STRIDE + i] = 0.0f;
+                }
+                __syncthreads();
             }
-            const float* m = sM + 6 * i;
-            const float z0 = fmaf(m[0], r3[0], fmaf(m[1], r3[1], m[2] * r3[2]));
-            const float z1 = fmaf(m[1], r3[0], fmaf(m[3], r3[1], m[4] * r3[2]));
-            const float z2 = fmaf(m[2], r3[0], fmaf(m[4], r3[1], m[5] * r3[2]));
-            sZ[e] = z0; sZ[e + 1] = z1; sZ[e + 2] = z2;
-            lrz = fmaf(r3[0], z0, fmaf(r3[1], z1, fmaf(r3[2], z2, lrz)));
-            lrr = fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], fmaf(r3[2], r3[2], lrr)));
+            update_points();
         }
         double rzn, rrn;
         {

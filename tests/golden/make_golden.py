@@ -3,7 +3,7 @@
 Calls only the FP64 oracle (oracle/) and the seeded input generator; nothing here
 touches the CUDA path.  Run from the repository root:
 
-    python tests/golden/make_golden.py [tiny medium autograd]
+    python tests/golden/make_golden.py [tiny medium autograd medium_100]
 """
 import json
 import os
@@ -42,8 +42,28 @@ def run(name, f32_inputs):
                 oracle_seconds=dt, numpy=np.__version__)
 
 
+def run_long(name, iters):
+    """The same workload with a longer LM budget, FP64 inputs only (context for the
+    headline's C*: how far 20 iterations are from where LM settles)."""
+    p = synth.make_config(name)
+    settings = dict(SETTINGS[name], max_lm_iters=iters)
+    t0 = time.time()
+    res = O.ba_solve(p.cams_init, p.pts_init, p.cam_idx, p.pt_idx, p.pixels, O.LMOptions(**settings))
+    return dict(config=name, inputs="fp64", options=settings, initial_cost=res.initial_cost,
+                final_cost=res.final_cost, lm_iters=res.lm_iters, accepted=res.accepted,
+                pcg_iters_total=res.pcg_iters_total,
+                costs=[float(h["cost"]) for h in res.history] + [float(res.final_cost)],
+                oracle_seconds=time.time() - t0, numpy=np.__version__)
+
+
 def main(names):
     for name in names:
+        if name.endswith("_100"):   # e.g. medium_100: 100 LM iterations
+            out = run_long(name[:-4], 100)
+            with open(os.path.join(HERE, f"oracle_lm_{name}.json"), "w") as f:
+                json.dump(out, f, indent=1)
+            print(name, out["final_cost"], f"{out['oracle_seconds']:.1f}s")
+            continue
         out = {"fp64": run(name, False), "fp32_inputs": run(name, True)}
         path = os.path.join(HERE, f"oracle_lm_{name}.json")
         with open(path, "w") as f:
