@@ -199,6 +199,12 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
     }
     for (int i = tid; i < 6 * np; i += TB) sM[i] = v.Minv_p[6 * (size_t)pb + i];
     __syncthreads();
+    // keys carry the CTA-local camera index from here on (no search in the loop)
+    for (uint32_t i = tid; i < no; i += TB) {
+        const uint32_t key = skey[i];
+        skey[i] = (local_cam(sCid, ncb, key >> 8) << 8) | (key & 0xffu);
+    }
+    __syncthreads();
 
     const double mu = st->mu;
     const float muf = (float)mu;
@@ -277,16 +283,12 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                         tpt = (int)(tcur * TILE_PTS) - pb;
                     }
                     const uint32_t key = skey[j];
-                    const uint32_t c = key >> 8;
+                    const uint32_t lc = key >> 8;   // the CTA's local camera index
                     const int lp = tpt + (int)(key & 0xffu);
-                    if (c != cur) {
-                        if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
-                        cur = c;
-                        uint32_t lo = 0, hi = ncb;   // local index of camera c
-                        while (hi - lo > 1) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (sCid[mid] <= c) lo = mid; else hi = mid;
-                        }
+                    if (lc != cur) {
+                        if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)sCid[cur] * CA_STRIDE, acc);
+                        cur = lc;
+                        const uint32_t lo = lc;
                         const float* rec = sCam + 16 * lo;
 #pragma unroll
                         for (int q = 0; q < 9; ++q) cam.R[q] = rec[q];
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
             }
             // every lane of the warp reaches this one collective
             const bool head = seg_reduce<9>(cur, acc);
-            if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
+            if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)sCid[cur] * CA_STRIDE, acc);
         }
         if (v.n_fac > 0) jp2 += factor_pass(v, sCid, ncb, sDir, v.cam_acc, (int)gridDim.x * TB);
         double sj, sp;
@@ -577,6 +579,11 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
     }
     for (int i = tid; i < 6 * np; i += TB) sM[i] = v.Minv_p[6 * (size_t)pb + i];
     __syncthreads();   // camera ids and owner bits
+    // keys carry the CTA-local camera index from here on (no search in the loop)
+    for (uint32_t i = tid; i < no; i += TB) {
+        const uint32_t key = skey[i];
+        skey[i] = (local_cam(sCid, ncb, key >> 8) << 8) | (key & 0xffu);
+    }
     for (uint32_t i = tid; i < 16 * ncb; i += TB)
         sCam[i] = __ldg(v.cam_pre + (size_t)sCid[i / 16] * CP_STRIDE + i % 16);
     for (int e = tid; e < ne; e += TB) {
@@ -646,16 +653,12 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
                         tpt = (int)(tcur * TILE_PTS) - pb;
                     }
                     const uint32_t key = skey[j];
-                    const uint32_t c = key >> 8;
+                    const uint32_t lc = key >> 8;   // the CTA's local camera index
                     const int lp = tpt + (int)(key & 0xffu);
-                    if (c != cur) {
-                        if (cur != NO_CAM) flush_matvec(cacc + (size_t)cur * CA_STRIDE, acc);
-                        cur = c;
-                        uint32_t lo = 0, hi = ncb;   // local index of camera c
-                        while (hi - lo > 1) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (sCid[mid] <= c) lo = mid; else hi = mid;
-                        }
+                    if (lc != cur) {
+                        if (cur != NO_CAM) flush_matvec(cacc + (size_t)sCid[cur] * CA_STRIDE, acc);
+                        cur = lc;
+                        const uint32_t lo = lc;
                         const float* rec = sCam + 16 * lo;
 #pragma unroll
                         for (int q = 0; q < 9; ++q) cam.R[q] = rec[q];
@@ -673,7 +676,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
             }
             // every lane of the warp reaches this one collective
             const bool head = seg_reduce<9>(cur, acc);
-            if (head && cur != NO_CAM) flush_matvec(cacc + (size_t)cur * CA_STRIDE, acc);
+            if (head && cur != NO_CAM) flush_matvec(cacc + (size_t)sCid[cur] * CA_STRIDE, acc);
         }
         if (v.n_fac > 0) jj += factor_pass(v, sCid, ncb, sDir, cacc, (int)gridDim.x * TB);
         jj = warp_sumf(jj);
