@@ -346,38 +346,58 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
 }
 
 // ------------------------------------------------------------------ K4 --------
-// One PCG direction step fused with the damped normal operator:
-//   p = zs + beta p_prev                 (zs = z during PCG; beta = 0 applies to a given p)
-//   q = J^T J p + mu D p                 (points; cameras are finished in K5)
-//   |J p|^2 and p^T D p are added to st->acc_mv.
-// Camera directions are double-buffered (pc[parity] holds p_prev, pc[parity ^ 1]
-// receives p); every CTA recomputes the direction record of the cameras it meets
-// from (zs, p_prev, J_l), and CTA b writes p for cameras b, b + grid, ...
-// Each tile's keys, points and point directions are staged in shared memory.
-
-template <int TB>
-__global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* gate, const float* zs, int use_beta) {
+// Camera part of one PCG direction step, before k_matvec: p_c = zs_c + beta p_prev_c
+// for every camera (double-buffered: pc[parity] holds p_prev, pc[parity ^ 1] receives
+// p), its direction record (phi = J_l p_w, p_t, p_intr) into cam_dir, and the camera
+// part of p^T D p into st->acc_mv.  One thread per camera entry.
+__global__ void k_cam_direction(Views<float> v, const int32_t* gate, const float* zs, int use_beta) {
     if (gated_off(gate)) return;
-    __shared__ float sx[3 * TILE_PTS], sd[3 * TILE_PTS], sq[3 * TILE_PTS];
     __shared__ double red[32];
     DevState* st = v.st;
     const int par = st->pcg_iter & 1;
     const float beta = use_beta ? (float)st->beta : 0.0f;
     const float* pc_old = v.pc + (size_t)par * v.pc_stride;
     float* pc_new = v.pc + (size_t)(par ^ 1) * v.pc_stride;
+    float pdp = 0.0f;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.n_cams; c += gridDim.x * blockDim.x) {
+        float pk[9];
+        const size_t e = 9 * (size_t)c;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            pk[k] = beta != 0.0f ? fmaf(beta, pc_old[e + k], zs[e + k]) : zs[e + k];
+            pc_new[e + k] = pk[k];
+            pdp = fmaf(v.D[e + k] * pk[k], pk[k], pdp);
+        }
+        const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
+        float* d = v.cam_dir + (size_t)c * CD_STRIDE;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            d[CD_PHI + i] = fmaf(JL[3 * i], pk[0], fmaf(JL[3 * i + 1], pk[1], JL[3 * i + 2] * pk[2]));
+#pragma unroll
+        for (int k = 3; k < 9; ++k) d[k] = pk[k];
+    }
+    const double bp = block_sum((double)pdp, red);
+    if (threadIdx.x == 0) slot_add(st->acc_mv, 1, bp);
+}
+
+// One PCG direction step fused with the damped normal operator, after k_cam_direction:
+//   p = zs + beta p_prev for the points (zs = z during PCG; beta = 0 applies to a given p)
+//   q = J^T J p + mu D p                 (points; cameras are finished in K5)
+//   |J p|^2 and the points' p^T D p are added to st->acc_mv.
+// Each tile's keys, points and point directions are staged in shared memory; a camera
+// switch loads the camera's record and direction record.
+
+template <int TB>
+__global__ void __launch_bounds__(TB, 8) k_matvec(Views<float> v, const int32_t* gate, const float* zs, int use_beta) {
+    if (gated_off(gate)) return;
+    __shared__ float sx[3 * TILE_PTS], sd[3 * TILE_PTS], sq[3 * TILE_PTS];
+    __shared__ double red[32];
+    DevState* st = v.st;
+    const float beta = use_beta ? (float)st->beta : 0.0f;
     const float mu = (float)st->mu;
     const float eps = (float)st->opt.eps;
     const bool weighted = st->opt.loss != 0;
-    float pdp = 0.0f, jp2 = 0.0f;
-    // camera part of p owned by this CTA
-    for (int c = blockIdx.x; c < v.n_cams; c += gridDim.x) {
-        if (threadIdx.x < 9) {
-            const size_t e = 9 * (size_t)c + threadIdx.x;
-            const float pk = beta != 0.0f ? fmaf(beta, pc_old[e], zs[e]) : zs[e];
-            pc_new[e] = pk;
-            pdp = fmaf(v.D[e] * pk, pk, pdp);
-        }
-    }
+    float pdp = 0.0f, jp2 = 0.0f;   // the camera part of p^T D p comes from k_cam_direction
     for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
         const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
         const int pt0 = tile * TILE_PTS;
@@ -409,7 +429,7 @@ __global__ void __launch_bounds__(TB) k_matvec(Views<float> v, const int32_t* ga
                 if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
                 cur = c;
                 cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
-                camera_dir(v, c, zs, pc_old, beta, dir);
+                load_dir(v.cam_dir + (size_t)c * CD_STRIDE, dir);   // from k_cam_direction
             }
             if (weighted) {   // robust loss: per-observation IRLS weights
                 jp2 += obs_normal<true>(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc, sq + 3 * slot,
@@ -1107,6 +1127,7 @@ void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, C
 }
 void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                    const float* zs, int use_beta) {
+    k_cam_direction<<<grid_items(L, v.n_cams), L.item_block, 0, s>>>(v, gate, zs, use_beta);
     k_matvec<MV_TB><<<v.n_tiles > 0 ? v.n_tiles : 1, MV_TB, 0, s>>>(v, gate, zs, use_beta);
     launch_factor_matvec(v, L, s, gate, zs, use_beta);   // pose factors, if any
 }

@@ -288,15 +288,17 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                     if (lc != cur) {
                         if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)sCid[cur] * CA_STRIDE, acc);
                         cur = lc;
-                        const uint32_t lo = lc;
-                        const float* rec = sCam + 16 * lo;
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) cam.R[q] = rec[q];
-                        cam.t[0] = rec[9]; cam.t[1] = rec[10]; cam.t[2] = rec[11];
-                        cam.f = rec[12]; cam.k1 = rec[13]; cam.k2 = rec[14];
-                        const float* dr = sDir + 12 * lo;
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) dir[q] = dr[q];
+                        // records as 128-bit shared loads (both arrays are 16-byte aligned)
+                        const float4* r4 = reinterpret_cast<const float4*>(sCam + 16 * lc);
+                        const float4 ra = r4[0], rb = r4[1], rc = r4[2], rd = r4[3];
+                        cam.R[0] = ra.x; cam.R[1] = ra.y; cam.R[2] = ra.z; cam.R[3] = ra.w;
+                        cam.R[4] = rb.x; cam.R[5] = rb.y; cam.R[6] = rb.z; cam.R[7] = rb.w;
+                        cam.R[8] = rc.x; cam.t[0] = rc.y; cam.t[1] = rc.z; cam.t[2] = rc.w;
+                        cam.f = rd.x; cam.k1 = rd.y; cam.k2 = rd.z;
+                        const float4* d4 = reinterpret_cast<const float4*>(sDir + 12 * lc);
+                        const float4 da = d4[0], db = d4[1], dc = d4[2];
+                        dir[0] = da.x; dir[1] = da.y; dir[2] = da.z; dir[3] = da.w;
+                        dir[4] = db.x; dir[5] = db.y; dir[6] = db.z; dir[7] = db.w; dir[8] = dc.x;
                     }
                     const float4 xp = sX4[lp], pp = sP4[lp];
                     const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
@@ -658,15 +660,17 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
                     if (lc != cur) {
                         if (cur != NO_CAM) flush_matvec(cacc + (size_t)sCid[cur] * CA_STRIDE, acc);
                         cur = lc;
-                        const uint32_t lo = lc;
-                        const float* rec = sCam + 16 * lo;
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) cam.R[q] = rec[q];
-                        cam.t[0] = rec[9]; cam.t[1] = rec[10]; cam.t[2] = rec[11];
-                        cam.f = rec[12]; cam.k1 = rec[13]; cam.k2 = rec[14];
-                        const float* dr = sDir + 12 * lo;
-#pragma unroll
-                        for (int q = 0; q < 9; ++q) dir[q] = dr[q];
+                        // records as 128-bit shared loads (both arrays are 16-byte aligned)
+                        const float4* r4 = reinterpret_cast<const float4*>(sCam + 16 * lc);
+                        const float4 ra = r4[0], rb = r4[1], rc = r4[2], rd = r4[3];
+                        cam.R[0] = ra.x; cam.R[1] = ra.y; cam.R[2] = ra.z; cam.R[3] = ra.w;
+                        cam.R[4] = rb.x; cam.R[5] = rb.y; cam.R[6] = rb.z; cam.R[7] = rb.w;
+                        cam.R[8] = rc.x; cam.t[0] = rc.y; cam.t[1] = rc.z; cam.t[2] = rc.w;
+                        cam.f = rd.x; cam.k1 = rd.y; cam.k2 = rd.z;
+                        const float4* d4 = reinterpret_cast<const float4*>(sDir + 12 * lc);
+                        const float4 da = d4[0], db = d4[1], dc = d4[2];
+                        dir[0] = da.x; dir[1] = da.y; dir[2] = da.z; dir[3] = da.w;
+                        dir[4] = db.x; dir[5] = db.y; dir[6] = db.z; dir[7] = db.w; dir[8] = dc.x;
                     }
                     const float4 xp = sX4[lp], up = sU4[lp];
                     const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {up.x, up.y, up.z};

@@ -225,21 +225,19 @@ __global__ void k_factor_eval(Views<float> v) {
 }
 
 // The pose factors' part of the multi-kernel normal operator, after k_matvec in the
-// same PCG step (same direction p = zs + beta p_prev, camera records and accumulators):
-// J_f^T J_f p into the camera sums, |J_f p|^2 into the matvec slot sums.
+// same PCG step (the camera direction records of k_cam_direction, the same camera
+// accumulators): J_f^T J_f p into the camera sums, |J_f p|^2 into the matvec slot sums.
 __global__ void k_factor_matvec(Views<float> v, const int32_t* gate, const float* zs, int use_beta) {
+    (void)zs;
+    (void)use_beta;
     if (gated_off(gate)) return;
     __shared__ double red[32];
     DevState* st = v.st;
-    const float beta = use_beta ? (float)st->beta : 0.0f;
-    const float* pc_old = v.pc + (size_t)(st->pcg_iter & 1) * v.pc_stride;
     float jp2 = 0.0f;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < v.n_fac; k += gridDim.x * blockDim.x) {
         const uint32_t ca = v.fac_cam[2 * (size_t)k], cb = v.fac_cam[2 * (size_t)k + 1];
-        float da[9], db[9];
-        camera_dir(v, ca, zs, pc_old, beta, da);
-        camera_dir(v, cb, zs, pc_old, beta, db);
-        jp2 += factor_normal(v.fac_J + 72 * (size_t)k, da, db, v.cam_acc + (size_t)ca * CA_STRIDE,
+        jp2 += factor_normal(v.fac_J + 72 * (size_t)k, v.cam_dir + (size_t)ca * CD_STRIDE,
+                             v.cam_dir + (size_t)cb * CD_STRIDE, v.cam_acc + (size_t)ca * CA_STRIDE,
                              v.cam_acc + (size_t)cb * CA_STRIDE);
     }
     const double bj = block_sum((double)jp2, red);
