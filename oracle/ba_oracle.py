@@ -476,17 +476,36 @@ def damping_diag(J, min_diag=1e-6, max_diag=1e32):
     return np.clip(d, min_diag, max_diag)
 
 
+def _spd_inverses(A):
+    """Inverse of each SPD block of A [N, k, k] by Cholesky.  A block that is not
+    positive definite in FP64 (rank-deficient J^T J once mu has shrunk far) gets its
+    inverse diagonal instead, 1 / A_ii where A_ii > 0 and 0 elsewhere."""
+    out = np.empty_like(A)
+    try:
+        L = np.linalg.cholesky(A)
+        Li = np.linalg.inv(L)
+        return Li.transpose(0, 2, 1) @ Li
+    except np.linalg.LinAlgError:
+        pass
+    for i in range(A.shape[0]):
+        try:
+            Li = np.linalg.inv(np.linalg.cholesky(A[i]))
+            out[i] = Li.T @ Li
+        except np.linalg.LinAlgError:
+            d = np.diag(A[i])
+            out[i] = np.diag(np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0))
+    return out
+
+
 def block_jacobi(lin: Linearization, D, mu):
-    """Inverses of the diagonal blocks of J^T J + mu D, one block per node, by Cholesky."""
+    """Inverses of the diagonal blocks of J^T J + mu D, one block per node, by Cholesky
+    (a block that is not positive definite falls back to its inverse diagonal)."""
     nc = lin.Hc.shape[0]
     Dc = D[: 9 * nc].reshape(nc, 9)
     Dp = D[9 * nc:].reshape(-1, 3)
     Ac = lin.Hc + mu * np.einsum("ci,ij->cij", Dc, np.eye(9))
     Ap = lin.Hp + mu * np.einsum("pi,ij->pij", Dp, np.eye(3))
-    Lc = np.linalg.cholesky(Ac)
-    Lp = np.linalg.cholesky(Ap)
-    inv = lambda L: np.linalg.inv(L).transpose(0, 2, 1) @ np.linalg.inv(L)
-    return inv(Lc), inv(Lp)
+    return _spd_inverses(Ac), _spd_inverses(Ap)
 
 
 def apply_block_jacobi(Mc, Mp, v):

@@ -619,3 +619,15 @@ def test_lm_with_factors_is_monotone_and_stationary():
     c, q = O.unpack(res.x, p.n_cams)
     lin = O.linearize(c, q, p.cam_idx, p.pt_idx, p.pixels, factors=f)
     assert np.linalg.norm(lin.g) < 1e-6 * np.sqrt(lin.F)
+
+
+def test_block_jacobi_falls_back_to_the_inverse_diagonal():
+    """A rank-deficient block (mu = 0, a point seen along one ray) is not positive
+    definite: its preconditioner block is the inverse diagonal; SPD blocks are exact."""
+    A = np.zeros((2, 3, 3))
+    A[0] = np.diag([4.0, 2.0, 1.0]) + 0.1
+    u = np.array([1.0, 2.0, 2.0])
+    A[1] = np.outer(u, u)                       # rank one
+    M = O._spd_inverses(A)
+    np.testing.assert_allclose(M[0], np.linalg.inv(A[0]), rtol=1e-12)
+    np.testing.assert_allclose(M[1], np.diag(1.0 / np.diag(A[1])), rtol=1e-12)
