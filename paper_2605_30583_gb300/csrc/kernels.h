@@ -12,7 +12,7 @@ typedef unsigned long long CondHandle;   // cudaGraphConditionalHandle
 
 constexpr int LIN_TB = 128;   // threads per tile CTA, linearisation
 constexpr int MV_TB = 128;    // threads per tile CTA, normal operator
-constexpr int EV_TB = 128;    // threads per tile CTA, candidate evaluation
+constexpr int EV_TB = 256;    // threads per tile CTA, candidate evaluation
 constexpr int PCG_TB = 512;   // threads per CTA of the persistent PCG kernel
 
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` and never lowers
