@@ -132,7 +132,7 @@ def matvec_model(prob):
 # DRAM bytes (read + write) per 50-iteration launch of k_pcg_persistent, from one ncu
 # capture of the same workload and launch (profiles/k_pcg_persistent_medium.md).  Set to
 # None whenever the kernel changes until it is captured again.
-PCG_TRAFFIC = {}
+PCG_TRAFFIC = {"medium": 19972608}
 
 # Nominal HBM3e bandwidth of a GB300 (the second denominator the roofline is quoted on).
 NOMINAL_HBM_GBS = 7900.0

@@ -1127,7 +1127,9 @@ void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, C
 }
 void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                    const float* zs, int use_beta) {
-    k_cam_direction<<<grid_items(L, v.n_cams), L.item_block, 0, s>>>(v, gate, zs, use_beta);
+    // one thread per camera, no more blocks than cameras need (each block adds one slot sum)
+    const int cd_grid = std::max(1, std::min(L.item_grid, (v.n_cams + L.item_block - 1) / L.item_block));
+    k_cam_direction<<<cd_grid, L.item_block, 0, s>>>(v, gate, zs, use_beta);
     k_matvec<MV_TB><<<v.n_tiles > 0 ? v.n_tiles : 1, MV_TB, 0, s>>>(v, gate, zs, use_beta);
     launch_factor_matvec(v, L, s, gate, zs, use_beta);   // pose factors, if any
 }
