@@ -137,6 +137,17 @@ const char* ba_last_error(void);
 const char* ba_status_string(int32_t status);
 int32_t ba_abi_version(void);
 
+/* Self-test of the bounded grid waits that every cooperative kernel of this library
+ * uses (the persistent PCG kernel's barriers).  Launches a cooperative grid of `grid`
+ * CTAs (1 <= grid <= the SM count) that waits at a barrier counting one CTA more than
+ * it has, which nothing completes; each CTA must give up after timeout_ms (1..2000)
+ * and return, leaving the context usable.  scratch: 16 bytes of caller-owned device
+ * memory, 16-byte aligned.  On BA_OK, *gave_up is the number of CTAs that gave up
+ * (grid when the mechanism works) and *error_word the shared error flag (1).  No GPU
+ * fault is involved: the wait simply runs out. */
+ba_status ba_selftest_wait_timeout(void* scratch, int32_t grid, int32_t timeout_ms, void* stream, int32_t* gave_up,
+                                   int32_t* error_word);
+
 /* Fills *opts with the defaults listed at ba_options. */
 ba_status ba_options_default(ba_options* opts);
 

@@ -69,6 +69,7 @@ SIGNATURES = {
     "ba_problem_destroy": (None, [P]),
     "ba_workspace_size": (I32, [P, ctypes.POINTER(SZ)]),
     "ba_set_pose_factors": (I32, [P, I32, P, P, P, P]),
+    "ba_selftest_wait_timeout": (I32, [P, I32, I32, P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
     "ba_bind_workspace": (I32, [P, P, SZ, P]),
     "ba_set_params": (I32, [P, P, P]),
     "ba_get_params": (I32, [P, P, P]),
@@ -124,6 +125,18 @@ def check(status: int) -> None:
 
 def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+def selftest_wait_timeout(grid: int = 4, timeout_ms: int = 50):
+    """Runs the bounded-wait self-test (ba_selftest_wait_timeout) on the current CUDA
+    stream; returns (CTAs that gave up, error word)."""
+    torch = _torch()
+    scratch = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    gave, err = ctypes.c_int32(), ctypes.c_int32()
+    check(lib().ba_selftest_wait_timeout(scratch.data_ptr(), int(grid), int(timeout_ms),
+                                         torch.cuda.current_stream().cuda_stream, ctypes.byref(gave),
+                                         ctypes.byref(err)))
+    return int(gave.value), int(err.value)
 
 
 def default_options(**kw) -> Options:

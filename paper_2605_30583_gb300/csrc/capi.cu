@@ -371,6 +371,30 @@ const char* ba_status_string(int32_t s) {
 
 int32_t ba_abi_version(void) { return 1; }
 
+ba_status ba_selftest_wait_timeout(void* scratch, int32_t grid, int32_t timeout_ms, void* stream, int32_t* gave_up,
+                                   int32_t* error_word) {
+    if (!scratch || !gave_up || !error_word || ((uintptr_t)scratch & 15u) != 0) {
+        set_error("ba_selftest_wait_timeout: null or misaligned pointer");
+        return BA_ERR_INVALID_ARG;
+    }
+    int dev = 0, sms = 0;
+    GBBA_CUDA(cudaGetDevice(&dev));
+    GBBA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (grid < 1 || grid > sms || timeout_ms < 1 || timeout_ms > 2000) {
+        set_error("ba_selftest_wait_timeout: grid must be in [1, %d] and timeout in [1, 2000] ms", sms);
+        return BA_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    GBBA_CUDA(cudaMemsetAsync(scratch, 0, 16, s));
+    GBBA_CUDA(launch_selftest_wait(scratch, grid, 1000000LL * timeout_ms, s));
+    int32_t words[4];
+    GBBA_CUDA(cudaMemcpyAsync(words, scratch, 16, cudaMemcpyDeviceToHost, s));
+    GBBA_CUDA(cudaStreamSynchronize(s));
+    *error_word = words[2];
+    *gave_up = words[3];
+    return BA_OK;
+}
+
 ba_status ba_options_default(ba_options* o) {
     if (!o) {
         set_error("ba_options_default: null pointer");

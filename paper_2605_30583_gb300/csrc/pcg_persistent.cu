@@ -53,12 +53,12 @@ constexpr long long BARRIER_TIMEOUT_NS = 2000000000LL;   // 2 s
 // get there once every CTA has arrived, and a CTA that has already moved on to the
 // next barrier only raises it further.  False on time-out or when another CTA has
 // already reported one.
-__device__ __forceinline__ bool grid_sync(DevState* st, unsigned int nblocks, unsigned long long epoch) {
+__device__ __forceinline__ bool grid_sync_on(unsigned long long* cnt, int* err, unsigned int nblocks,
+                                             unsigned long long epoch, long long timeout_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned long long* cnt = &st->bar_count;
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(cnt), "l"(1ull) : "memory");
         const unsigned long long target = epoch * nblocks;
         const long long t0 = global_ns();
@@ -68,9 +68,9 @@ __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int nblocks, un
             asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(cnt) : "memory");
             if (c >= target) break;
             if ((++spins & 15u) == 0u) {
-                if (*reinterpret_cast<volatile int*>(&st->bar_err)) { ok = 0; break; }
-                if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
-                    atomicExch(&st->bar_err, 1);
+                if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicExch(err, 1);
                     ok = 0;
                     break;
                 }
@@ -82,6 +82,10 @@ __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int nblocks, un
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(DevState* st, unsigned int nblocks, unsigned long long epoch) {
+    return grid_sync_on(&st->bar_count, &st->bar_err, nblocks, epoch, BARRIER_TIMEOUT_NS);
 }
 
 // Grid-wide sums of XCH_NV per-CTA values, then the grid barrier.  Exchange e adds
@@ -858,6 +862,30 @@ cudaError_t launch_pcg_persistent(const Views<float>& v, const uint32_t* blk_til
     if (form == PCG_TWO_EXCHANGE)
         return cudaLaunchKernelEx(&cfg, k_pcg_persistent<PCG_TB>, v, blk_tile, blk_cam_off, blk_cams, pslots);
     return cudaLaunchKernelEx(&cfg, k_pcg_persistent_1x<PCG_TB>, v, blk_tile, blk_cam_off, blk_cams, pslots);
+}
+
+// Self-test of the bounded grid wait: a cooperative grid of `grid` CTAs waits at a
+// barrier that counts one CTA more than it has, which nothing will ever complete.
+// Every CTA must give up after `timeout_ns`, set the shared error word and return;
+// scratch = {arrival count (u64), error word (i32), CTAs that gave up (u32)}.
+__global__ void k_selftest_wait(unsigned long long* scratch, long long timeout_ns) {
+    int* err = reinterpret_cast<int*>(scratch + 1);
+    unsigned int* gave_up = reinterpret_cast<unsigned int*>(scratch + 1) + 1;
+    const bool ok = grid_sync_on(scratch, err, gridDim.x + 1, 1ull, timeout_ns);
+    if (!ok && threadIdx.x == 0) atomicAdd(gave_up, 1u);
+}
+
+cudaError_t launch_selftest_wait(void* scratch, int grid, long long timeout_ns, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(64);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_selftest_wait, (unsigned long long*)scratch, timeout_ns);
 }
 
 }  // namespace gbba

@@ -140,3 +140,34 @@ def test_rejections(B):
     with pytest.raises(B.BAError) as e:
         p.solve(solver=1)
     assert e.value.status == 6   # not implemented
+
+
+def test_cameras_held_only_by_factors_or_by_nothing(B):
+    """Camera 3 loses its observations and is held by pose factors alone; camera 5 loses
+    its observations and has no factor (its block is mu D alone, its step stays zero)."""
+    base = synth.make_config("tiny", seed=23, n_cams=12)
+    keep = (base.cam_idx != 3) & (base.cam_idx != 5)
+    counts = np.bincount(base.pt_idx[keep], minlength=base.n_pts)
+    live = counts >= 2                          # points that keep two views
+    keep &= live[base.pt_idx]
+    new_id = np.cumsum(live) - 1
+    prob = synth.round_to_f32(synth.Problem(base.n_cams, int(live.sum()), base.cam_idx[keep],
+                                            new_id[base.pt_idx[keep]].astype(np.uint32), base.pixels[keep],
+                                            base.cams_init, base.pts_init[live], base.cams_gt, base.pts_gt[live],
+                                            "tiny-holes"))
+    assert not np.any(prob.cam_idx == 3) and not np.any(prob.cam_idx == 5)
+    fa, fb, meas, sq = synth.make_pose_factors(prob, pairs="chain", seed=23)
+    sel = (fa != 5) & (fb != 5)
+    fac = (fa[sel], fb[sel], meas[sel], sq[sel])
+    f = O.PoseFactors(*fac)
+    opts = dict(max_lm_iters=10, max_pcg_iters=50)
+    ref = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels, O.LMOptions(**opts),
+                     factors=f)
+    for k in (0, 1, 2):
+        p = _problem(B, prob, fac)
+        res = p.solve(pcg_kernel=k, **opts)
+        assert res.status == 0 and res.lm_iters == ref.lm_iters
+        assert abs(res.final_cost - ref.final_cost) <= 1e-4 * ref.final_cost, (k, res.final_cost, ref.final_cost)
+        c, _ = p.get_params()
+        np.testing.assert_allclose(c[5], prob.cams_init[5], rtol=0, atol=1e-6)   # untouched
+        assert np.abs(c[3] - prob.cams_init[3]).max() > 1e-5                     # moved by its factors
