@@ -1130,7 +1130,7 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
     return write_options(p, &d);
 }
 
-// ---- not yet available in this build --------------------------------------------
+// ---- autograd entries: the cost and its adjoint J^T r at caller-given parameters ---
 
 ba_status ba_cost_forward(ba_problem* p, const void* cams, const void* pts, int32_t dtype, double* cost_dev) {
     ba_status st = check_bound(p, "ba_cost_forward");

@@ -349,7 +349,8 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
 // Camera part of one PCG direction step, before k_matvec: p_c = zs_c + beta p_prev_c
 // for every camera (double-buffered: pc[parity] holds p_prev, pc[parity ^ 1] receives
 // p), its direction record (phi = J_l p_w, p_t, p_intr) into cam_dir, and the camera
-// part of p^T D p into st->acc_mv.  One thread per camera entry.
+// part of p^T D p into st->acc_mv.  One thread per camera entry; the three rotation
+// rows of phi recompute the camera's p_w themselves.
 __global__ void k_cam_direction(Views<float> v, const int32_t* gate, const float* zs, int use_beta) {
     if (gated_off(gate)) return;
     __shared__ double red[32];
@@ -359,22 +360,22 @@ __global__ void k_cam_direction(Views<float> v, const int32_t* gate, const float
     const float* pc_old = v.pc + (size_t)par * v.pc_stride;
     float* pc_new = v.pc + (size_t)(par ^ 1) * v.pc_stride;
     float pdp = 0.0f;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.n_cams; c += gridDim.x * blockDim.x) {
-        float pk[9];
-        const size_t e = 9 * (size_t)c;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            pk[k] = beta != 0.0f ? fmaf(beta, pc_old[e + k], zs[e + k]) : zs[e + k];
-            pc_new[e + k] = pk[k];
-            pdp = fmaf(v.D[e + k] * pk[k], pk[k], pdp);
+    const int n = 9 * v.n_cams;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int c = e / 9, k = e - 9 * c;
+        auto p_of = [&](int i) {
+            const size_t x = 9 * (size_t)c + i;
+            return beta != 0.0f ? fmaf(beta, pc_old[x], zs[x]) : zs[x];
+        };
+        const float pk = p_of(k);
+        pc_new[e] = pk;
+        pdp = fmaf(v.D[e] * pk, pk, pdp);
+        float d = pk;
+        if (k < 3) {
+            const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL + 3 * k;
+            d = fmaf(__ldg(JL), p_of(0), fmaf(__ldg(JL + 1), p_of(1), __ldg(JL + 2) * p_of(2)));
         }
-        const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
-        float* d = v.cam_dir + (size_t)c * CD_STRIDE;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            d[CD_PHI + i] = fmaf(JL[3 * i], pk[0], fmaf(JL[3 * i + 1], pk[1], JL[3 * i + 2] * pk[2]));
-#pragma unroll
-        for (int k = 3; k < 9; ++k) d[k] = pk[k];
+        v.cam_dir[(size_t)c * CD_STRIDE + k] = d;   // CD_PHI = 0, CD_T = 3, CD_I = 6
     }
     const double bp = block_sum((double)pdp, red);
     if (threadIdx.x == 0) slot_add(st->acc_mv, 1, bp);
@@ -1127,8 +1128,8 @@ void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, C
 }
 void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                    const float* zs, int use_beta) {
-    // one thread per camera, no more blocks than cameras need (each block adds one slot sum)
-    const int cd_grid = std::max(1, std::min(L.item_grid, (v.n_cams + L.item_block - 1) / L.item_block));
+    // one thread per camera entry, no more blocks than that needs (each adds one slot sum)
+    const int cd_grid = std::max(1, std::min(L.item_grid, (9 * v.n_cams + L.item_block - 1) / L.item_block));
     k_cam_direction<<<cd_grid, L.item_block, 0, s>>>(v, gate, zs, use_beta);
     k_matvec<MV_TB><<<v.n_tiles > 0 ? v.n_tiles : 1, MV_TB, 0, s>>>(v, gate, zs, use_beta);
     launch_factor_matvec(v, L, s, gate, zs, use_beta);   // pose factors, if any
