@@ -29,7 +29,7 @@ namespace gbba {
 // ------------------------------------------------------------------ K0 --------
 // Camera records from the current parameters; zeroes the linearisation sums.
 __global__ void k_camera_precompute(Views<float> v) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < v.n_cams; c += gridDim.x * blockDim.x) {
+    for (int c = 32 * (int)blockIdx.x + (int)threadIdx.x; threadIdx.x < 32 && c < v.n_cams; c += 32 * (int)gridDim.x) {
         double p[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) p[k] = (double)v.x[9 * (size_t)c + k];
@@ -221,10 +221,13 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
 // ------------------------------------------------------------------ K3 --------
 // Block-Jacobi preconditioner (Sec. V: one block per node) of J^T J + mu D, inverted
 // by FP64 Cholesky, and the start of PCGNR: h = 0, r = -g, z = M^-1 r, p = 0.
-// Camera c of an item kernel runs in block c % gridDim, thread c / gridDim, so the
-// (slow, FP64) per-camera work spreads over every SM.
+// Camera c of an item kernel runs in lane c % 32 of warp 0 of block (c / 32) % gridDim:
+// 32 cameras share every warp instruction (the FP64 pipe takes whole warps, so a warp
+// with one busy lane costs as much as a full one) and the cameras spread over the SMs.
+// The other warps of the block skip the loop.
 #define FOR_CAMERAS(c, v) \
-    for (int c = blockIdx.x + gridDim.x * threadIdx.x; c < (v).n_cams; c += gridDim.x * blockDim.x)
+    for (int c = 32 * (int)blockIdx.x + (int)threadIdx.x; threadIdx.x < 32 && c < (v).n_cams; \
+         c += 32 * (int)gridDim.x)
 #define FOR_POINTS(i, v) \
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (v).n_pts; i += gridDim.x * blockDim.x)
 
@@ -1113,10 +1116,15 @@ inline int grid_items(const LaunchCfg& L, int items) {
     return g < 1 ? 1 : (g > L.item_grid ? L.item_grid : g);
 }
 inline int grid_tiles(int cap, int n_tiles) { return n_tiles < 1 ? 1 : (n_tiles > cap ? cap : n_tiles); }
+// Blocks for a camera-only kernel: one warp of 32 cameras per block (FOR_CAMERAS).
+inline int grid_cams(const LaunchCfg& L, int n_cams) {
+    const int g = (n_cams + 31) / 32;
+    return g < 1 ? 1 : (g > L.item_grid ? L.item_grid : g);
+}
 }  // namespace
 
 void launch_camera_precompute(const Views<float>& v, const LaunchCfg& L, cudaStream_t s) {
-    k_camera_precompute<<<grid_items(L, v.n_cams), L.item_block, 0, s>>>(v);
+    k_camera_precompute<<<grid_cams(L, v.n_cams), 32, 0, s>>>(v);
 }
 void launch_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode,
                       float* res_out, float* jac_out, CondHandle lm_cond, int use_cond) {
@@ -1143,14 +1151,15 @@ void launch_schur(const Views<float>& v, cudaStream_t s, int mode, const int32_t
     else k_schur<MV_TB, SCHUR_BACK><<<grid, MV_TB, 0, s>>>(v, gate);
 }
 void launch_schur_start(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
-    k_schur_start<<<grid_items(L, v.n_cams), L.item_block, 0, s>>>(v, c, use);
+    k_schur_start<<<grid_cams(L, v.n_cams), L.item_block, 0, s>>>(v, c, use);
 }
 void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
                    int cameras_only) {
-    k_update<<<grid_items(L, cameras_only ? v.n_cams : v.n_quads), L.item_block, 0, s>>>(v, c, use, cameras_only);
+    k_update<<<cameras_only ? std::max(grid_cams(L, v.n_cams), 1) : std::max(grid_items(L, v.n_quads), grid_cams(L, v.n_cams)),
+               L.item_block, 0, s>>>(v, c, use, cameras_only);
 }
 void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s) {
-    k_candidate<<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v);
+    k_candidate<<<std::max(grid_items(L, v.n_pts), grid_cams(L, v.n_cams)), L.item_block, 0, s>>>(v);
 }
 void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
     launch_factor_eval(v, L, s);
@@ -1175,7 +1184,7 @@ void launch_unpack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, co
     else k_unpack<float><<<g, L.item_block, 0, s>>>(v, src, (float*)cams, (float*)pts);
 }
 void launch_set_direction(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const float* src) {
-    k_set_direction<float><<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v, src);
+    k_set_direction<float><<<std::max(grid_items(L, v.n_pts), grid_cams(L, v.n_cams)), L.item_block, 0, s>>>(v, src);
 }
 void launch_normal_out(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, float* out) {
     k_normal_out<float><<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v, out);
@@ -1355,8 +1364,7 @@ void launch_cost_grad(const Views<float>& v, const LaunchCfg& L, cudaStream_t s,
     const int gi = std::max(1, std::min((v.n_cams + v.n_pts + 255) / 256, L.item_grid));
     if (dtype == 1) k_pack_to<double><<<gi, 256, 0, s>>>(v, (const double*)cams, (const double*)pts, v.x_new);
     else k_pack_to<float><<<gi, 256, 0, s>>>(v, (const float*)cams, (const float*)pts, v.x_new);
-    k_camera_records_from<<<std::max(1, std::min((v.n_cams + 255) / 256, L.item_grid)), 256, 0, s>>>(v, v.x_new,
-                                                                                                     v.cam_pre_new);
+    k_camera_records_from<<<grid_cams(L, v.n_cams), 32, 0, s>>>(v, v.x_new, v.cam_pre_new);
     const int gt = std::max(1, std::min(v.n_tiles, L.lin_grid));
     k_cost_grad<LIN_TB><<<gt, LIN_TB, 0, s>>>(v, v.x_new, v.cam_pre_new, want_grad, cost_dev);
 }
