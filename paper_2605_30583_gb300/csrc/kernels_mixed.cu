@@ -231,7 +231,10 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
 #define FOR_POINTS(i, v) \
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (v).n_pts; i += gridDim.x * blockDim.x)
 
-__global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, double* pslots) {
+// Blocks [0, cam_blocks) invert the camera blocks (a warp per camera); the others
+// invert the point blocks (a thread per point), so the long FP64 camera eliminations run
+// beside the point work instead of before it in the same warps.
+__global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, double* pslots, int cam_blocks) {
     DevState* st = v.st;
     if (pslots != nullptr && blockIdx.x == 0) {   // state of the persistent PCG kernel
         for (int i = threadIdx.x; i < PSLOT_TOTAL; i += blockDim.x) pslots[i] = 0.0;
@@ -248,8 +251,9 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
     const double mu = st->mu, lo = st->opt.min_diag, hi = st->opt.max_diag;
     double rz = 0.0, rr = 0.0;
     const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < v.n_cams; c += warps) {
+    const int warps = cam_blocks * (blockDim.x >> 5);
+    const bool cam_role = (int)blockIdx.x < cam_blocks;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; cam_role && c < v.n_cams; c += warps) {
         const double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
         double col[9];
         const int j = lane < 18 ? lane : 17;
@@ -303,7 +307,8 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
                     v.cam_acc[((size_t)set * v.n_cams + c) * CA_STRIDE + lane] = 0.0f;
         }
     }
-    FOR_POINTS(i, v) {
+    const int pt_stride = ((int)gridDim.x - cam_blocks) * blockDim.x;
+    for (int i = ((int)blockIdx.x - cam_blocks) * blockDim.x + threadIdx.x; !cam_role && i < v.n_pts; i += pt_stride) {
         const float* H = v.pt_H + (size_t)i * PH_STRIDE;
         const size_t e = v.pt_off + 3 * (size_t)i;
         double a00 = H[0], a01 = H[1], a02 = H[2], a11 = H[3], a12 = H[4], a22 = H[5];
@@ -1134,7 +1139,11 @@ void launch_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s,
 }
 void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
                     double* pslots) {
-    k_precond<<<grid_items(L, std::max(v.n_pts, 32 * v.n_cams)), L.item_block, 0, s>>>(v, c, use, pslots);
+    // camera blocks: a warp per camera; point blocks: a thread per point
+    const int wpb = L.item_block / 32;
+    const int cam_blocks = std::max(1, std::min((v.n_cams + wpb - 1) / wpb, L.item_grid / 2));
+    const int pt_blocks = std::max(1, std::min(grid_items(L, v.n_pts), L.item_grid - cam_blocks));
+    k_precond<<<cam_blocks + pt_blocks, L.item_block, 0, s>>>(v, c, use, pslots, cam_blocks);
 }
 void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                    const float* zs, int use_beta) {
