@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-schur", action="store_true")
     ap.add_argument("--no-factors", action="store_true")
+    ap.add_argument("--no-one-exchange", action="store_true")
     ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1, 2],
                     help="1: conditional-loop graph; 2: unrolled predicated graph; 0: host-enqueued sequence")
@@ -444,7 +445,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- the same solve with the persistent kernel's one-exchange form (pcg_kernel = 2)
     one_x = None
-    if not args.no_schur:
+    if not args.no_one_exchange:
         xo = binding.default_options(use_graph=args.graph_mode, pcg_kernel=2)
         p.set_params(cams0, pts0)
         p.solve(xo, wait=False)
