@@ -631,3 +631,15 @@ def test_block_jacobi_falls_back_to_the_inverse_diagonal():
     M = O._spd_inverses(A)
     np.testing.assert_allclose(M[0], np.linalg.inv(A[0]), rtol=1e-12)
     np.testing.assert_allclose(M[1], np.diag(1.0 / np.diag(A[1])), rtol=1e-12)
+
+
+def test_pose_factor_hand_cases():
+    """Hand-worked residuals of the relative-pose factor (tests/golden/pose_factor_hand.json)."""
+    data = json.load(open(os.path.join(GOLDEN, "pose_factor_hand.json")))
+    for case in data["cases"]:
+        cams = np.zeros((2, 9))
+        cams[0, :6] = case["cam_a"]
+        cams[1, :6] = case["cam_b"]
+        f = O.PoseFactors(np.array([0]), np.array([1]), np.array([case["meas"]], float),
+                          np.array([case["sqrt_info"]], float))
+        np.testing.assert_allclose(O.pose_factor_residuals(cams, f)[0], case["residual"], atol=1e-12)
