@@ -1,0 +1,48 @@
+"""bench.py's accounting, on the CPU: the algorithmic byte model behind `roofline`, the
+time-to-cost rule, and the medium workload's counts the design notes quote."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+class _P:
+    def __init__(self, n_cams, n_pts, n_obs):
+        self.n_cams, self.n_pts, self.n_obs = n_cams, n_pts, n_obs
+
+
+def test_operator_bytes_per_unit():
+    # 4 B per observation key; 48 B per point (X, p, D read, q written); 64 + 48 + 96 B per
+    # camera (record, direction record, accumulator read-modify-write)
+    nb, nf = bench.matvec_model(_P(1, 0, 0))
+    assert nb == 208 and nf == 0
+    assert bench.matvec_model(_P(0, 1, 0))[0] == 48
+    assert bench.matvec_model(_P(0, 0, 1)) == (4, 120)
+
+
+def test_pcg_iteration_bytes_add_the_vector_update_and_preconditioner():
+    # per unknown 44 B; per point block 24 B of M^-1; per camera block 324 B
+    nb_c = bench.pcg_iter_model(_P(1, 0, 0))[0]
+    assert nb_c == 208 + 44 * 9 + 324
+    nb_p = bench.pcg_iter_model(_P(0, 1, 0))[0]
+    assert nb_p == 48 + 44 * 3 + 24
+
+
+def test_medium_workload_counts():
+    # 1,000 cameras, 200,000 points, 1,199,169 observations: 46,524,676 B per PCG iteration
+    nb, _ = bench.pcg_iter_model(_P(1000, 200_000, 1_199_169))
+    assert nb == 46_524_676
+
+
+def test_time_to_cost_takes_the_first_accepted_step_at_the_target():
+    hist = [dict(accepted=True, cost_new=10.0, t_ns=1_000_000),
+            dict(accepted=False, cost_new=1.0, t_ns=2_000_000),     # rejected: does not count
+            dict(accepted=True, cost_new=4.0, t_ns=3_000_000),
+            dict(accepted=True, cost_new=3.0, t_ns=4_000_000)]
+    assert bench.time_to_cost(hist, 5.0) == 3.0
+    assert bench.time_to_cost(hist, 2.0) is None
+    assert bench.time_to_cost(hist, None) is None
