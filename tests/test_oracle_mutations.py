@@ -42,6 +42,8 @@ MUTATIONS = {
                                    "np.add.at(Hc, np.asarray(factors.cam_a, np.int64), np.einsum(\"oki,okj->oij\", Jb, Jb))"),
     "pose_cost_dropped_from_candidate": ("return F if factors is None else F + pose_factor_cost(c, factors)",
                                          "return F"),
+    "fallback_diagonal_not_inverted": ("out[i] = np.diag(np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0))",
+                                       "out[i] = np.diag(np.where(d > 0, d, 0.0))"),
 }
 
 
