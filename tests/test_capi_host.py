@@ -120,3 +120,26 @@ def test_pose_factor_validation_without_gpu(lib):
     st, h = _create(3, 2, [0, 1, 2, 0], [0, 0, 1, 1], px, prec=1)   # plain FP64 form
     assert lib.ba_set_pose_factors(h, 2, a.ctypes.data, b.ctypes.data, meas.ctypes.data, None) == 6
     lib.ba_problem_destroy(h)
+
+
+def _struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in the public header, in order."""
+    src = open(os.path.join(ROOT, "include", "gbba.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct(?:\s+\w+)?\s*\{([^}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    names = []
+    for decl in re.findall(r"\b(?:int32_t|int64_t|uint32_t|double|float)\s+([a-z_0-9,\s]+);", m.group(1)):
+        names += [n.strip() for n in decl.split(",")]
+    return names
+
+
+@pytest.mark.parametrize("cname,pyname", [("ba_options", "Options"), ("ba_stats", "Stats"),
+                                          ("ba_iter_stat", "IterStat"), ("ba_batch_trial", "BatchTrial")])
+def test_ctypes_mirrors_follow_the_header(lib, cname, pyname):
+    """The binding's ctypes structures list the header's fields in the header's order
+    (the layout the library reads), and have the C size."""
+    cls = getattr(binding, pyname, None)
+    if cls is None:
+        pytest.skip(f"binding has no {pyname}")
+    assert [f[0] for f in cls._fields_] == _struct_fields(cname)
