@@ -761,28 +761,19 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
 // camera linearisation sums for the relinearisation that follows.
 __global__ void k_commit(Views<float> v) {
     if (v.st->accepted == 0) return;
-    const int items = v.n_cams + v.n_pts;
-    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
-        if (it < v.n_cams) {
-            const size_t e = 9 * (size_t)it;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) v.x[e + k] = v.x_new[e + k];
-            const float4* s = reinterpret_cast<const float4*>(v.cam_pre_new + (size_t)it * CP_STRIDE);
-            float4* d = reinterpret_cast<float4*>(v.cam_pre + (size_t)it * CP_STRIDE);
-#pragma unroll
-            for (int k = 0; k < CP_STRIDE / 4; ++k) d[k] = s[k];
-            double* cl = v.cam_lin + (size_t)it * CL_STRIDE;
-#pragma unroll
-            for (int k = 0; k < CL_STRIDE; ++k) cl[k] = 0.0;
-            float* ch = v.cam_H + (size_t)it * CH_STRIDE;
-#pragma unroll
-            for (int k = 0; k < CH_STRIDE; ++k) ch[k] = 0.0f;
-        } else {
-            const size_t e = v.pt_off + 3 * (size_t)(it - v.n_cams);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) v.x[e + k] = v.x_new[e + k];
-        }
-    }
+    // flat, coalesced 16-byte copies: x <- x' over the whole parameter vector (cameras,
+    // their zero padding, point quads), camera records <- the candidate's, and the
+    // camera linearisation sums cleared for the next linearisation
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (size_t)gridDim.x * blockDim.x;
+    const float4* xs = reinterpret_cast<const float4*>(v.x_new);
+    float4* xd = reinterpret_cast<float4*>(v.x);
+    for (size_t i = tid; i < (size_t)v.n_vec / 4; i += nth) xd[i] = xs[i];
+    const float4* cs = reinterpret_cast<const float4*>(v.cam_pre_new);
+    float4* cd = reinterpret_cast<float4*>(v.cam_pre);
+    for (size_t i = tid; i < (size_t)v.n_cams * (CP_STRIDE / 4); i += nth) cd[i] = cs[i];
+    for (size_t i = tid; i < (size_t)v.n_cams * CL_STRIDE; i += nth) v.cam_lin[i] = 0.0;
+    float4* ch = reinterpret_cast<float4*>(v.cam_H);
+    for (size_t i = tid; i < (size_t)v.n_cams * (CH_STRIDE / 4); i += nth) ch[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 // ------------------------------------------------------------ Schur complement ---
