@@ -130,10 +130,27 @@ def matvec_model(prob):
     return nb, nf
 
 
-# DRAM bytes (read + write) per 50-iteration launch of k_pcg_persistent, from one ncu
-# capture of the same workload and launch (profiles/k_pcg_persistent_medium.md).  Set to
-# None whenever the kernel changes until it is captured again.
-PCG_TRAFFIC = {"medium": 19972608}
+# DRAM bytes (read + write) per launch of a roofline kernel, from one ncu capture of the
+# same workload and launch (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# (kernel source file, workload) and stamped with the first 16 hex digits of the
+# SHA-256 of that source file when it was captured: a figure whose source has changed
+# since is reported as null (stale) until it is captured again.
+TRAFFIC = {}
+
+
+def source_sha16(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2605_30583_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(src, workload):
+    rec = TRAFFIC.get((src, workload))
+    if rec is None:
+        return None
+    nbytes, sha = rec
+    return nbytes if sha == source_sha16(src) else None
 
 # Nominal HBM3e bandwidth of a GB300 (the second denominator the roofline is quoted on).
 NOMINAL_HBM_GBS = 7900.0
@@ -336,7 +353,7 @@ def run_ours(args, rank, world, local_rank):
     if us_pcg > 0 and it_pcg > 0:
         gbs_p = pb * it_pcg / (us_pcg / 1e6) / 1e9
         roofline = {"bound": "hbm", "achieved": gbs_p, "peak": hbm_peak, "unit": "GB/s", "frac": gbs_p / hbm_peak,
-                    "traffic": PCG_TRAFFIC.get(args.config),
+                    "traffic": measured_traffic("pcg_persistent.cu", args.config),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured, burst copy)",
                     "kernel": "k_pcg_persistent (one PCG solve per launch, tiles resident in shared memory)",
                     "us_per_launch": us_pcg, "pcg_iters_per_launch": it_pcg,

@@ -107,6 +107,15 @@ typedef struct {
                                      block-Jacobi on the camera blocks.  Mixed precision
                                      only (BA_ERR_NOT_IMPLEMENTED for the FP64 form and
                                      the batched mode).                                 */
+    int32_t wait_timeout_ms;      /* limit on each grid-wide wait of the persistent PCG
+                                     kernel (its CTAs meet at a barrier twice per
+                                     iteration), default 2000.  A wait that does not end
+                                     within it gives up: every CTA leaves the kernel and
+                                     the solve reports BA_ERR_TIMEOUT (the context stays
+                                     usable).  0 gives up at the first poll that finds
+                                     the barrier incomplete.  0..60000.  The separate-
+                                     kernel PCG and the batched mode have no grid-wide
+                                     waits and ignore it.                              */
 } ba_options;
 
 /* One LM iteration (Sec. V): cost before the step, candidate cost, damping used,
@@ -148,6 +157,12 @@ int32_t ba_abi_version(void);
 ba_status ba_selftest_wait_timeout(void* scratch, int32_t grid, int32_t timeout_ms, void* stream, int32_t* gave_up,
                                    int32_t* error_word);
 
+/* Self-test of the FP64 reciprocal that the block-Jacobi inversions use (a hardware
+ * approximation refined by two Newton-Raphson steps).  y[i] = 1/x[i] for i < n, with
+ * x and y device arrays of n doubles (n >= 1), enqueued on `stream` (cudaStream_t).
+ * Zero, non-finite and |x| outside [1e-300, 1e300] take the IEEE quotient 1.0 / x. */
+ba_status ba_selftest_rcp64(const double* x, double* y, int64_t n, void* stream);
+
 /* Fills *opts with the defaults listed at ba_options. */
 ba_status ba_options_default(ba_options* opts);
 
@@ -156,8 +171,8 @@ ba_status ba_options_default(ba_options* opts);
  *   cam_idx[n_obs], pt_idx[n_obs]: host, camera / point of each observation.
  *   pixels[n_obs][2]: host, measured pixels.
  * Copied; the caller keeps ownership.  Requirements (else BA_ERR_INVALID_ARG):
- * 1 <= n_cams < 2^24, 1 <= n_pts, 1 <= n_obs < 2^32, every index in range, and
- * every point observed at least twice.  No device memory is touched until
+ * 1 <= n_cams < 2^24, 1 <= n_pts, 1 <= n_obs < 2^32, every index in range, every
+ * pixel finite, and every point observed at least twice.  No device memory is touched until
  * ba_bind_workspace. */
 ba_status ba_problem_create(int32_t n_cams, int32_t n_pts, int64_t n_obs,
                             const uint32_t* cam_idx, const uint32_t* pt_idx,
@@ -277,16 +292,21 @@ ba_status ba_cost_backward(ba_problem* problem, const void* cams, const void* pt
  * Computes F = 1/2 sum_o |r_o|^2 with the arithmetic of ba_evaluate for
  * BA_PREC_MIXED (FP32 residuals, FP64 sum) from caller-provided device arrays in user
  * layout: cams float[n_cams][9], pts float[n_pts][3], cam_idx / pt_idx uint32[n_obs],
- * pixels float[n_obs][2].  The result goes to *cost_dev (device double).  Enqueued on
+ * pixels float[n_obs][2].  Indices are not validated on the host: every cam_idx must be
+ * < n_cams and every pt_idx < n_pts; an observation whose index is out of range is
+ * skipped without being read and makes the result NaN.  The result goes to *cost_dev
+ * (device double).  Enqueued on
  * `stream` (cudaStream_t); no synchronisation, no cudaMalloc, no cudaFree and no
  * allocating library call.
  *
  * Scratch (camera records and per-block partial sums, about 1.1 MiB) is a fixed array
  * inside the library: every GPU that loads the library holds it until the process
  * exits.  Limits: n_cams <= BA_NOALLOC_MAX_CAMS and n_obs <= BA_NOALLOC_MAX_BLOCKS *
- * 1024; larger sizes are rejected with BA_ERR_INVALID_ARG before any GPU work.  The
- * first call on each device looks up the array's device address once (with that
- * device current); make that first call before any stream capture.  All calls share
+ * 1024; larger sizes are rejected with BA_ERR_INVALID_ARG before any GPU work.  Each
+ * call made outside stream capture looks up the array's device address on the current
+ * device (so a device reset is followed); a call under capture uses the address of the
+ * last uncaptured call on that device, so make a first call on each device before any
+ * stream capture (otherwise BA_ERR_STATE).  All calls share
  * the one array, so calls whose GPU work overlaps (other streams, other host threads
  * on the same device) race and must be serialised by the caller. */
 #define BA_NOALLOC_MAX_CAMS 16384

@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
                 ("min_diag", ctypes.c_double), ("max_diag", ctypes.c_double), ("max_mu", ctypes.c_double),
                 ("eps_depth", ctypes.c_double), ("use_graph", ctypes.c_int32), ("pcg_kernel", ctypes.c_int32),
                 ("rotation_update", ctypes.c_int32), ("loss", ctypes.c_int32), ("loss_scale", ctypes.c_double),
-                ("solver", ctypes.c_int32)]
+                ("solver", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32)]
 
 
 class IterStat(ctypes.Structure):
@@ -70,6 +70,7 @@ SIGNATURES = {
     "ba_workspace_size": (I32, [P, ctypes.POINTER(SZ)]),
     "ba_set_pose_factors": (I32, [P, I32, P, P, P, P]),
     "ba_selftest_wait_timeout": (I32, [P, I32, I32, P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+    "ba_selftest_rcp64": (I32, [P, P, I64, P]),
     "ba_bind_workspace": (I32, [P, P, SZ, P]),
     "ba_set_params": (I32, [P, P, P]),
     "ba_get_params": (I32, [P, P, P]),
@@ -137,6 +138,17 @@ def selftest_wait_timeout(grid: int = 4, timeout_ms: int = 50):
                                          torch.cuda.current_stream().cuda_stream, ctypes.byref(gave),
                                          ctypes.byref(err)))
     return int(gave.value), int(err.value)
+
+
+def selftest_rcp64(x):
+    """1/x through the FP64 reciprocal of the block inversions (ba_selftest_rcp64) for a
+    CUDA float64 tensor x; returns a new tensor."""
+    torch = _torch()
+    x = x.contiguous()
+    assert x.is_cuda and x.dtype == torch.float64
+    y = torch.empty_like(x)
+    check(lib().ba_selftest_rcp64(x.data_ptr(), y.data_ptr(), x.numel(), torch.cuda.current_stream().cuda_stream))
+    return y
 
 
 def default_options(**kw) -> Options:

@@ -395,6 +395,16 @@ ba_status ba_selftest_wait_timeout(void* scratch, int32_t grid, int32_t timeout_
     return BA_OK;
 }
 
+ba_status ba_selftest_rcp64(const double* x, double* y, int64_t n, void* stream) {
+    if (!x || !y || n < 1) {
+        set_error("ba_selftest_rcp64: null pointer or n < 1");
+        return BA_ERR_INVALID_ARG;
+    }
+    launch_selftest_rcp64(x, y, n, (cudaStream_t)stream);
+    GBBA_CUDA(cudaGetLastError());
+    return BA_OK;
+}
+
 ba_status ba_options_default(ba_options* o) {
     if (!o) {
         set_error("ba_options_default: null pointer");
@@ -414,6 +424,7 @@ ba_status ba_options_default(ba_options* o) {
     o->loss = 0;
     o->loss_scale = 1.0;
     o->solver = 0;
+    o->wait_timeout_ms = 2000;
     return BA_OK;
 }
 
@@ -442,6 +453,10 @@ ba_status ba_problem_create(int32_t n_cams, int32_t n_pts, int64_t n_obs, const 
         if (cam_idx[o] >= (uint32_t)n_cams || pt_idx[o] >= (uint32_t)n_pts) {
             set_error("ba_problem_create: observation %lld has camera %u / point %u out of range", (long long)o,
                       cam_idx[o], pt_idx[o]);
+            return BA_ERR_INVALID_ARG;
+        }
+        if (!std::isfinite(pixels[2 * o]) || !std::isfinite(pixels[2 * o + 1])) {
+            set_error("ba_problem_create: observation %lld has a non-finite pixel", (long long)o);
             return BA_ERR_INVALID_ARG;
         }
         deg[pt_idx[o]] += 1;
@@ -835,8 +850,10 @@ static ba_status check_options(const ba_options* o) {
         !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0) ||
         (o->pcg_kernel < 0 || o->pcg_kernel > 2) || o->use_graph < 0 || o->use_graph > 2 ||
         (o->rotation_update != 0 && o->rotation_update != 1) || o->loss < 0 || o->loss > 2 ||
-        !(o->loss_scale > 0) || (o->solver != 0 && o->solver != 1)) {
-        set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive)");
+        !(o->loss_scale > 0) || (o->solver != 0 && o->solver != 1) || o->wait_timeout_ms < 0 ||
+        o->wait_timeout_ms > 60000) {
+        set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive, "
+                  "wait_timeout_ms in [0, 60000])");
         return BA_ERR_INVALID_ARG;
     }
     return BA_OK;
@@ -855,6 +872,7 @@ static ba_status write_options(ba_problem* p, const ba_options* o) {
     d.retract = o->rotation_update;
     d.loss = o->loss;
     d.loss_scale = o->loss_scale;
+    d.wait_ns = 1000000LL * (int64_t)o->wait_timeout_ms;
     static_assert(offsetof(DevState, opt) == 0, "options first");
     GBBA_CUDA(cudaMemcpyAsync(p->ws + p->lay.state, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
     return BA_OK;
@@ -1053,6 +1071,7 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
     o.max_diag = 1e32;
     o.max_mu = 1e300;
     o.eps = 0.0;
+    o.wait_ns = 2000000000LL;
     GBBA_CUDA(cudaMemcpyAsync(p->ws + p->lay.state, &o, sizeof(o), cudaMemcpyHostToDevice, s));
     const int32_t flags[4] = {1, 1, 1, 1};
     auto open_gates = [&]() -> cudaError_t {

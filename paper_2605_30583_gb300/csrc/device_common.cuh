@@ -91,8 +91,12 @@ __device__ __forceinline__ double slot_sum_warp(const double* base, int k) {
 }
 
 // 1/x in FP64: hardware approximation refined by two Newton-Raphson steps
-// y <- y + y (1 - x y), each roughly doubling the correct bits.
+// y <- y + y (1 - x y), each roughly doubling the correct bits.  Zero, non-finite and
+// |x| outside [1e-300, 1e300] (where x y or the approximation could leave the normal
+// range, flushing or overflowing before the refinement) take the IEEE quotient.
 __device__ __forceinline__ double rcp64(double x) {
+    const double ax = fabs(x);
+    if (!(ax >= 1e-300 && ax <= 1e300)) return 1.0 / x;
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     y = fma(y, fma(-x, y, 1.0), y);

@@ -71,6 +71,8 @@ enum : int { PCG_TWO_EXCHANGE = 0, PCG_ONE_EXCHANGE = 2 };
 // Entries of blk_cams: camera id, bit 31 set in the one list that owns the camera.
 constexpr uint32_t BLK_CAM_OWNER = 0x80000000u;
 int persistent_max_smem();
+// Self-test of the FP64 reciprocal of the block inversions: y[i] = rcp64(x[i]).
+void launch_selftest_rcp64(const double* x, double* y, int64_t n, cudaStream_t s);
 // Self-test of the bounded grid wait (16 bytes of device scratch).
 cudaError_t launch_selftest_wait(void* scratch, int grid, long long timeout_ns, cudaStream_t s);
 cudaError_t persistent_prepare(int form, int smem_bytes, int* blocks_per_sm);

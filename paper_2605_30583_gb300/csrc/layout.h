@@ -56,6 +56,7 @@ struct DevOptions {
     int32_t retract;   // 1: rotations updated by retraction R <- Exp(d) R (J w.r.t. d)
     int32_t loss;      // robust loss: 0 squared, 1 Huber, 2 Cauchy
     double loss_scale;
+    int64_t wait_ns;   // limit on each grid-wide wait of the persistent PCG kernels
 };
 
 // Layout-compatible with ba_iter_stat of the public header.

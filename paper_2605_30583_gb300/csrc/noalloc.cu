@@ -51,11 +51,13 @@ __global__ void k_na_cameras(const float* __restrict__ cams, int n_cams, NaScrat
 }
 
 // One block per NA_OBS_PER_BLOCK observations; the last block to finish sums the
-// block partials in block order.
+// block partials in block order.  An index out of range is never followed: that
+// observation contributes NaN, so the returned cost is NaN.
 __global__ void __launch_bounds__(NA_THREADS) k_na_cost(const float* __restrict__ pts, const uint32_t* __restrict__ cam_idx,
                                                         const uint32_t* __restrict__ pt_idx,
-                                                        const float* __restrict__ pixels, int64_t n_obs, float eps,
-                                                        NaScratch sc, double* __restrict__ cost_out) {
+                                                        const float* __restrict__ pixels, int64_t n_obs, int n_cams,
+                                                        int n_pts, float eps, NaScratch sc,
+                                                        double* __restrict__ cost_out) {
     __shared__ double sh[32];
     __shared__ bool is_last;
     double acc = 0.0;
@@ -63,8 +65,13 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_cost(const float* __restrict_
     for (int k = 0; k < NA_OBS_PER_BLOCK / NA_THREADS; ++k) {
         const int64_t o = base + (int64_t)k * NA_THREADS + threadIdx.x;
         if (o < n_obs) {
-            const Cam cam = load_cam(sc.cams + 16 * (size_t)cam_idx[o]);
-            const float* X = pts + 3 * (size_t)pt_idx[o];
+            const uint32_t c = cam_idx[o], i = pt_idx[o];
+            if (c >= (uint32_t)n_cams || i >= (uint32_t)n_pts) {
+                acc = __longlong_as_double(0x7ff8000000000000LL);   // quiet NaN
+                continue;
+            }
+            const Cam cam = load_cam(sc.cams + 16 * (size_t)c);
+            const float* X = pts + 3 * (size_t)i;
             float r0, r1;
             project_residual(cam, X[0], X[1], X[2], eps, pixels[2 * o], pixels[2 * o + 1], r0, r1);
             acc += (double)r0 * r0 + (double)r1 * r1;
@@ -88,8 +95,11 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_cost(const float* __restrict_
     }
 }
 
-// Device address of the scratch array, looked up once per device with that device
-// current (the host-side symbol is only a stand-in, never a device address).
+// Device address of the scratch array per device, looked up with that device current
+// (the host-side symbol is only a stand-in, never a device address).  It is looked up
+// again on every call made outside stream capture, so a device reset (which may load
+// the module at another address) is followed; under capture the address cached by the
+// last uncaptured call on that device is used.
 std::mutex g_na_mutex;
 void* g_na_addr[64] = {nullptr};
 
@@ -128,13 +138,19 @@ extern "C" ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_pts, int64_t n_ob
         set_error("ba_cost_noalloc: device ordinal %d out of the supported range", dev);
         return BA_ERR_INVALID_ARG;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    GBBA_CUDA(cudaStreamIsCapturing(s, &cap));
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* a = nullptr;
             GBBA_CUDA(cudaGetSymbolAddress(&a, g_noalloc_scratch));
             g_na_addr[dev] = a;
+        } else if (!g_na_addr[dev]) {
+            set_error("ba_cost_noalloc: the first call on device %d must come before any stream capture", dev);
+            return BA_ERR_STATE;
         }
         base = g_na_addr[dev];
     }
@@ -142,13 +158,12 @@ extern "C" ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_pts, int64_t n_ob
     sc.cams = reinterpret_cast<float*>(base);
     sc.partials = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + NA_CAM_BYTES);
     sc.ticket = reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(base) + NA_CAM_BYTES + NA_PART_BYTES);
-    cudaStream_t s = (cudaStream_t)stream;
     // the ticket must start at zero on every call (an earlier failed call may have left it set)
     GBBA_CUDA(cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned int), s));
     const int cgrid = (n_cams + 255) / 256;
     k_na_cameras<<<cgrid, 256, 0, s>>>(cams, n_cams, sc);
-    k_na_cost<<<(unsigned int)blocks, NA_THREADS, 0, s>>>(pts, cam_idx, pt_idx, pixels, n_obs, (float)eps_depth, sc,
-                                                          cost_dev);
+    k_na_cost<<<(unsigned int)blocks, NA_THREADS, 0, s>>>(pts, cam_idx, pt_idx, pixels, n_obs, n_cams, n_pts,
+                                                          (float)eps_depth, sc, cost_dev);
     GBBA_CUDA(cudaGetLastError());
     return BA_OK;
 }

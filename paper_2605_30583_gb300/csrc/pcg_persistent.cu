@@ -45,14 +45,13 @@ namespace gbba {
 
 namespace {
 
-constexpr long long BARRIER_TIMEOUT_NS = 2000000000LL;   // 2 s
-
 // Grid-wide barrier number `epoch` (1, 2, ... within a launch) for a co-resident
 // (cooperative) grid.  Each CTA adds one to a counter, cleared before the launch, with
 // release semantics, and waits until it reaches epoch * nblocks: the count can only
 // get there once every CTA has arrived, and a CTA that has already moved on to the
 // next barrier only raises it further.  False on time-out or when another CTA has
-// already reported one.
+// already reported one.  Limits below 1 ms are checked at every poll (0: give up at the
+// first poll that finds the barrier incomplete), longer ones every 16th poll.
 __device__ __forceinline__ bool grid_sync_on(unsigned long long* cnt, int* err, unsigned int nblocks,
                                              unsigned long long epoch, long long timeout_ns) {
     __shared__ int s_ok;
@@ -67,9 +66,9 @@ __device__ __forceinline__ bool grid_sync_on(unsigned long long* cnt, int* err, 
             unsigned long long c;
             asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(c) : "l"(cnt) : "memory");
             if (c >= target) break;
-            if ((++spins & 15u) == 0u) {
+            if (timeout_ns < 1000000LL || (++spins & 15u) == 0u) {
                 if (*reinterpret_cast<volatile int*>(err)) { ok = 0; break; }
-                if (global_ns() - t0 > timeout_ns) {
+                if (global_ns() - t0 >= timeout_ns) {
                     atomicExch(err, 1);
                     ok = 0;
                     break;
@@ -85,7 +84,7 @@ __device__ __forceinline__ bool grid_sync_on(unsigned long long* cnt, int* err, 
 }
 
 __device__ __forceinline__ bool grid_sync(DevState* st, unsigned int nblocks, unsigned long long epoch) {
-    return grid_sync_on(&st->bar_count, &st->bar_err, nblocks, epoch, BARRIER_TIMEOUT_NS);
+    return grid_sync_on(&st->bar_count, &st->bar_err, nblocks, epoch, st->opt.wait_ns);
 }
 
 // Grid-wide sums of XCH_NV per-CTA values, then the grid barrier.  Exchange e adds
@@ -873,6 +872,16 @@ __global__ void k_selftest_wait(unsigned long long* scratch, long long timeout_n
     unsigned int* gave_up = reinterpret_cast<unsigned int*>(scratch + 1) + 1;
     const bool ok = grid_sync_on(scratch, err, gridDim.x + 1, 1ull, timeout_ns);
     if (!ok && threadIdx.x == 0) atomicAdd(gave_up, 1u);
+}
+
+__global__ void k_selftest_rcp64(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = rcp64(x[i]);
+}
+
+void launch_selftest_rcp64(const double* x, double* y, int64_t n, cudaStream_t s) {
+    const int64_t b = (n + 255) / 256;
+    k_selftest_rcp64<<<(unsigned int)(b < 1024 ? b : 1024), 256, 0, s>>>(x, y, n);
 }
 
 cudaError_t launch_selftest_wait(void* scratch, int grid, long long timeout_ns, cudaStream_t s) {

@@ -143,3 +143,33 @@ def test_ctypes_mirrors_follow_the_header(lib, cname, pyname):
     if cls is None:
         pytest.skip(f"binding has no {pyname}")
     assert [f[0] for f in cls._fields_] == _struct_fields(cname)
+
+
+def test_create_rejects_non_finite_pixels(lib):
+    """Non-finite measurements are refused at creation, before any device work."""
+    for bad in (np.nan, np.inf, -np.inf):
+        px = np.zeros((4, 2))
+        px[2, 1] = bad
+        st, h = _create(2, 2, [0, 1, 0, 1], [0, 0, 1, 1], px)
+        assert st == 1 and not h.value
+        assert b"non-finite pixel" in lib.ba_last_error()
+
+
+def test_bind_rejects_a_workspace_one_byte_short(lib):
+    """ba_bind_workspace checks the size before it touches the device: a workspace one
+    byte smaller than ba_workspace_size is refused with BA_ERR_WORKSPACE_TOO_SMALL (the
+    pointer is never dereferenced, so a 256-byte aligned stand-in address serves)."""
+    st, h = _create(3, 2, [0, 1, 2, 0], [0, 0, 1, 1], np.zeros((4, 2)))
+    assert st == 0
+    n = ctypes.c_size_t()
+    assert lib.ba_workspace_size(h, ctypes.byref(n)) == 0
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.ba_bind_workspace(h, fake, n.value - 1, None) == 3
+    assert b"needs" in lib.ba_last_error()
+    assert lib.ba_bind_workspace(h, ctypes.c_void_p((1 << 20) + 16), n.value, None) == 1   # misaligned
+    lib.ba_problem_destroy(h)
+
+
+def test_wait_timeout_default(lib):
+    o = binding.default_options()
+    assert o.wait_timeout_ms == 2000

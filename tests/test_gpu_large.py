@@ -72,7 +72,7 @@ def test_large_sampled_normal_operator(B, mixed, large):
     vc = vf[: 9 * large.n_cams].reshape(-1, 9)
     vp = vf[9 * large.n_cams:].reshape(-1, 3)
     clamp = lambda d: np.clip(d, 1e-6, 1e32)
-    got, ref = [], []
+    got, ref, scale = [], [], []
     # sampled points: all their observations
     order = np.argsort(large.pt_idx, kind="stable")
     starts = np.searchsorted(large.pt_idx[order], np.arange(large.n_pts + 1))
@@ -82,6 +82,9 @@ def test_large_sampled_normal_operator(B, mixed, large):
         t = np.einsum("oij,oj->oi", Jc, vc[large.cam_idx[obs]]) + np.einsum("oij,j->oi", Jp, vp[p])
         D = clamp(np.einsum("oij,oij->j", Jp, Jp))
         ref.append(np.einsum("oij,oi->j", Jp, t) + mu * D * vp[p])
+        ta = np.einsum("oij,oj->oi", np.abs(Jc), np.abs(vc[large.cam_idx[obs]])) + \
+            np.einsum("oij,j->oi", np.abs(Jp), np.abs(vp[p]))
+        scale.append(np.einsum("oij,oi->j", np.abs(Jp), ta) + mu * D * np.abs(vp[p]))
         got.append(q[9 * large.n_cams + 3 * p: 9 * large.n_cams + 3 * p + 3])
     # sampled cameras with modest observation counts
     counts = np.bincount(large.cam_idx, minlength=large.n_cams)
@@ -92,10 +95,17 @@ def test_large_sampled_normal_operator(B, mixed, large):
         t = np.einsum("oij,j->oi", Jc, vc[c]) + np.einsum("oij,oj->oi", Jp, vp[large.pt_idx[obs]])
         D = clamp(np.einsum("oij,oij->j", Jc, Jc))
         ref.append(np.einsum("oij,oi->j", Jc, t) + mu * D * vc[c])
+        ta = np.einsum("oij,j->oi", np.abs(Jc), np.abs(vc[c])) + \
+            np.einsum("oij,oj->oi", np.abs(Jp), np.abs(vp[large.pt_idx[obs]]))
+        scale.append(np.einsum("oij,oi->j", np.abs(Jc), ta) + mu * D * np.abs(vc[c]))
         got.append(q[9 * c: 9 * c + 9])
     got = np.concatenate(got)
     ref = np.concatenate(ref)
+    scale = np.concatenate(scale)
     assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref), np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    # per entry, against the sum of the magnitudes of its terms (see test_gpu_parity)
+    err = np.abs(got - ref) / scale
+    assert err.max() <= 1e-4, err.max()
 
 
 def test_large_solve_against_fp64_form(B, mixed, large):
