@@ -1,11 +1,14 @@
 """Benchmark of the LM + PCGNR bundle-adjustment hot path on one or more GB300s.
 
 One step = one complete LM solve (20 LM iterations, at most 50 PCG iterations each,
-initial trust region 100, CG tolerance 1e-3) of the medium synthetic workload
-(1,000 cameras, 200,000 points, ~1.2M observations), restarted from the same
-initial parameters, with every input already resident in HBM.  The metric is PCG
-iterations per second of whole-solve wall time (device events); the time to reach
-the FP64 oracle's final cost within 1e-4 is reported beside it.
+initial trust region 100, CG tolerance 1e-3) of the large synthetic workload (13,000
+cameras, 4.5M points, ~28.8M observations, the largest that the workloads define on
+one GPU), restarted from the same initial parameters, with every input already
+resident in HBM.  The metric is PCG iterations per second of whole-solve wall time
+(device events); beside it: the time to reach the plain all-FP64 GPU form's final cost
+(same budget, same inputs) within 1e-4 for both forms, the dominant kernel's roofline,
+the same solve end to end through the C ABI from host buffers, and the medium workload
+(1,000 cameras, 200,000 points) with the FP64 oracle's stored cost as its target.
 
 Multi-GPU: problems are independent, so ranks run replicas on their own seeds with
 no collective on the data path (weak scaling); timing is max over ranks.
@@ -38,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="medium")
+    ap.add_argument("--config", default="large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -47,6 +50,7 @@ def parse():
     ap.add_argument("--no-factors", action="store_true")
     ap.add_argument("--no-one-exchange", action="store_true")
     ap.add_argument("--no-autograd", action="store_true")
+    ap.add_argument("--no-medium", action="store_true", help="skip the medium-workload legs")
     ap.add_argument("--graph-mode", type=int, default=1, choices=[0, 1, 2],
                     help="1: conditional-loop graph; 2: unrolled predicated graph; 0: host-enqueued sequence")
     return ap.parse_args()
@@ -156,6 +160,31 @@ def measured_traffic(src, workload):
 NOMINAL_HBM_GBS = 7900.0
 
 
+def operator_model(prob):
+    """Algorithmic bytes and FP32 flops of one launch of the tile operator as timed
+    (k_cam_direction + k_tile_normal applied to a given direction, beta = 0).
+
+    Bytes: per observation its 4-byte key; per point the direction, D and X read and p
+    and q written (5 x 12 B); per camera the direction, D and J_l read and p_c and the
+    direction record written by k_cam_direction (5 x 36 B), its record and direction
+    record read by the tiles once (64 + 48 B) and its accumulator read-modify-write
+    (2 x 36 B): 364 B.  Flops: 120 per observation as in matvec_model."""
+    nb = 4 * prob.n_obs + 60 * prob.n_pts + 364 * prob.n_cams
+    return nb, 120 * prob.n_obs
+
+
+def pcg_iter_tile_model(prob):
+    """Algorithmic bytes of one PCG iteration of the separate-kernel form (operator with
+    the point direction step p = z + beta p fused in, then k_update).
+
+    Per point: z, p_prev, D, X read and p, q written by the operator (6 x 12 B); p, h, r,
+    q read and h, r, z written by the update (7 x 12 B); its M^-1 block (24 B): 180 B.
+    Per observation its key (4 B).  Per camera the operator's 364 B plus the update's
+    (p, h, r, D and the accumulator read, h, r, z, p written: 9 x 36 B; M^-1 324 B; J_l
+    36 B): 1,048 B."""
+    return 4 * prob.n_obs + 180 * prob.n_pts + 1048 * prob.n_cams
+
+
 def pcg_iter_model(prob):
     """Algorithmic bytes and FP32 flops of one PCG iteration (recomputed Jacobian).
 
@@ -172,64 +201,96 @@ def pcg_iter_model(prob):
 
 # ---------------------------------------------------------------- reference arm ---
 
-def run_reference(args, rank, world):
-    """The FP64 CPU oracle on a bounded sample: one linearisation and PCG iterations."""
-    if rank != 0:
-        return
-    from oracle import ba_oracle as O
+def oracle_subsample(prob, stride):
+    """Every `stride`-th point of a workload with all its observations and every camera
+    (points renumbered): a bounded sample of the same problem for the CPU oracle."""
     from paper_2605_30583_gb300 import synth
-    prob = synth.make_config(args.config)
+    keep = np.zeros(prob.n_pts, bool)
+    keep[::stride] = True
+    sel = keep[prob.pt_idx]
+    newid = np.cumsum(keep) - 1
+    return synth.Problem(prob.n_cams, int(keep.sum()), prob.cam_idx[sel], newid[prob.pt_idx[sel]].astype(np.uint32),
+                         prob.pixels[sel], prob.cams_init, prob.pts_init[keep], prob.cams_gt, prob.pts_gt[keep],
+                         name=f"{prob.name} 1/{stride}")
+
+
+# Points of the large workload the CPU oracle samples (every 32nd point, all its
+# observations, all cameras); smaller workloads are timed whole.
+ORACLE_STRIDE = {"large": 32}
+
+
+def oracle_pcg_rate(prob, seconds=None, steps=None, warmup=0, iters_per_step=5):
+    """The FP64 oracle as it stands: one linearisation, then PCGNR iterations (5 per
+    step, zero tolerance) until `seconds` have passed or `steps` steps are done.
+    Returns (iterations, seconds spent in PCG)."""
+    from oracle import ba_oracle as O
     lin = O.linearize(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
     D = O.damping_diag(lin.J)
     Mc, Mp = O.block_jacobi(lin, D, 0.01)
-    pre = lambda v: O.apply_block_jacobi(Mc, Mp, v)
-    iters_per_step = 5
+
+    def pre(v):
+        return O.apply_block_jacobi(Mc, Mp, v)
 
     def step():
         t0 = time.perf_counter()
         res = O.pcgnr(lin.J, D, 0.01, -lin.g, pre, tol=0.0, max_iters=iters_per_step)
         return res.iters, time.perf_counter() - t0
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-    it = 0
-    dt = 0.0
-    for _ in range(args.steps):
+    it, dt, k = 0, 0.0, 0
+    while (steps is not None and k < steps) or (seconds is not None and dt < seconds):
         a, b = step()
         it += a
         dt += b
-    v = it / dt
+        k += 1
+    return it, dt
+
+
+def oracle_sample(prob, config):
+    stride = ORACLE_STRIDE.get(config, 1)
+    sub = oracle_subsample(prob, stride) if stride > 1 else prob
+    # a PCG iteration costs the oracle O(observations + unknowns); the sample is 1/stride
+    # of both, so its rate divided by that ratio is the full workload's rate
+    scale = sub.n_obs / prob.n_obs
+    return sub, scale
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on a bounded sample: one linearisation and PCG iterations."""
+    if rank != 0:
+        return
+    from paper_2605_30583_gb300 import synth
+    prob = synth.make_config(args.config)
+    sub, scale = oracle_sample(prob, args.config)
+    it, dt = oracle_pcg_rate(sub, steps=args.steps, warmup=args.warmup)
+    v = it / dt * scale
+    sample = (f"{it} PCGNR iterations (5 per step after one linearisation) of the FP64 oracle on "
+              f"{sub.n_pts} points / {sub.n_obs} observations / {sub.n_cams} cameras"
+              + (f" (every {ORACLE_STRIDE[args.config]}th point of the workload with all its observations), rate "
+                 f"scaled by the observation ratio {scale:.5f} to the full workload" if scale < 1 else ""))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{args.config}: {prob.n_cams} cameras, {prob.n_pts} points, {prob.n_obs} observations",
-                   "sample": f"{iters_per_step} PCGNR iterations per step after one linearisation"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{iters_per_step} PCG iterations per step, {args.steps} steps"},
+                   "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def cpu_baseline(prob, seconds=12.0):
+def cpu_baseline(prob, config, seconds=12.0):
     """The oracle as it stands, timed on the host: PCG iterations per second over a
-    bounded sample (one linearisation, then PCG iterations until ~`seconds`)."""
-    from oracle import ba_oracle as O
-    lin = O.linearize(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
-    D = O.damping_diag(lin.J)
-    Mc, Mp = O.block_jacobi(lin, D, 0.01)
-    pre = lambda v: O.apply_block_jacobi(Mc, Mp, v)
-    t0 = time.perf_counter()
-    it = 0
-    while time.perf_counter() - t0 < seconds:
-        res = O.pcgnr(lin.J, D, 0.01, -lin.g, pre, tol=0.0, max_iters=5)
-        it += res.iters
-    dt = time.perf_counter() - t0
-    return {"value": it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{it} PCGNR iterations of the FP64 oracle on the same workload after one linearisation"}
+    bounded sample (one linearisation, then PCG iterations for ~`seconds`)."""
+    sub, scale = oracle_sample(prob, config)
+    it, dt = oracle_pcg_rate(sub, seconds=seconds)
+    return {"value": it / dt * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{it} PCGNR iterations of the FP64 oracle after one linearisation on {sub.n_pts} points / "
+                      f"{sub.n_obs} observations / {sub.n_cams} cameras"
+                      + (f" (every {ORACLE_STRIDE[config]}th point of the workload), rate scaled by the observation "
+                         f"ratio {scale:.5f}" if scale < 1 else " (the whole workload)")}
 
-
-# ---------------------------------------------------------------- our arm ---------
 
 def replica_seed(config_seed, rank):
     """Seed of rank `rank`'s replica: every rank solves its own problem of the same shape."""
@@ -250,6 +311,133 @@ def aggregate_over_ranks(total_ms, units, world, device):
     return float(t.item()), float(u.item())
 
 
+def timed_solves(p, cams0, pts0, opts, n, flush, stream, torch, fill=1):
+    """`n` solves from the same start, each after an L2 flush and bracketed by CUDA
+    events on the solve's stream; returns (ms per solve, PCG iterations, last stats)."""
+    ms, pcg, last = [], 0, None
+    for _ in range(n):
+        flush.fill_(fill)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p.set_params(cams0, pts0)
+        p.solve(opts, wait=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        last = p.stats()
+        pcg += last.pcg_iters_total
+    return ms, pcg, last
+
+
+def load_peaks():
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(pk_path)) if os.path.exists(pk_path) else {}
+
+
+def operator_roofline(p, prob, config, torch, stream, flush, hbm_peak, alu_peak, reps=100):
+    """The normal operator the separate-kernel PCG launches (k_cam_direction + the tile
+    operator), timed live with CUDA events on its stream over `reps` back-to-back
+    launches after an L2 flush, against its algorithmic bytes (operator_model)."""
+    p.set_params(prob.cams_init, prob.pts_init)
+    p.evaluate()
+    n = 9 * prob.n_cams + 3 * prob.n_pts
+    v = torch.randn(n, dtype=torch.float32, device="cuda")
+    p.apply_normal(0.01, v)
+    p.repeat_normal(5)
+    flush.fill_(2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    p.repeat_normal(reps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nb, nf = operator_model(prob)
+    gbs = nb / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+            "traffic": measured_traffic("tile_kernels.cu", config),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured burst copy)",
+            "frac_of_nominal": gbs / NOMINAL_HBM_GBS,
+            "kernel": "k_cam_direction + k_tile_normal (damped normal operator, Jacobian recomputed per "
+                      "observation, per-tile camera tables in shared memory)",
+            "us_per_launch": 1e3 * ms, "algorithmic_bytes": nb, "algorithmic_flops": nf,
+            "alu": {"achieved_tflops": nf / (ms / 1e3) / 1e12, "peak_tflops": alu_peak,
+                    "frac": nf / (ms / 1e3) / 1e12 / alu_peak,
+                    "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock"}}
+
+
+def persistent_roofline(kernel_us, prob, config, hbm_peak, alu_peak):
+    """k_pcg_persistent (one launch = one PCG solve), from ba_profile_kernels' event-timed
+    launches, against the algorithmic bytes of its PCG iterations (pcg_iter_model)."""
+    it_pcg = kernel_us.get("pcg_persistent_iters", 0.0)
+    us_pcg = kernel_us.get("pcg_persistent", -1.0)
+    if not (us_pcg > 0 and it_pcg > 0):
+        return None
+    pb, pf = pcg_iter_model(prob)
+    gbs = pb * it_pcg / (us_pcg / 1e6) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+            "traffic": measured_traffic("pcg_persistent.cu", config),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured burst copy)",
+            "kernel": "k_pcg_persistent (one PCG solve per launch, tiles resident in shared memory)",
+            "us_per_launch": us_pcg, "pcg_iters_per_launch": it_pcg, "algorithmic_bytes_per_pcg_iter": pb,
+            "alu_frac": pf * it_pcg / (us_pcg / 1e6) / 1e12 / alu_peak, "frac_of_nominal": gbs / NOMINAL_HBM_GBS}
+
+
+def solve_leg(binding, prob, opts, torch, stream, flush, steps, target=None, pose_factors=None):
+    """One more workload or option set: a warm solve, then `steps` timed solves."""
+    q = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels,
+                        pose_factors=pose_factors)
+    q.set_params(prob.cams_init, prob.pts_init)
+    q.solve(opts, wait=False)
+    torch.cuda.synchronize()
+    ms, pc, st = timed_solves(q, prob.cams_init, prob.pts_init, opts, steps, flush, stream, torch, fill=5)
+    out = {"ms_per_solve": sum(ms) / len(ms), "pcg_iters_per_solve": pc / len(ms),
+           "pcg_iters_per_s": pc / (sum(ms) / 1e3), "initial_cost": st.initial_cost, "final_cost": st.final_cost,
+           "lm_iters": st.lm_iters, "status": st.status}
+    if target is not None:
+        out["time_to_cost_ms"] = time_to_cost(st.history, target * (1 + 1e-4))
+    q.close()
+    return out
+
+
+def medium_legs(args, binding, synth, torch, dev, stream, flush, hbm_peak, alu_peak):
+    """The medium workload (1,000 cameras, 200,000 points, 1,199,169 observations): the
+    default solver against the FP64 oracle's stored 20-iteration cost C*, the persistent
+    PCG kernel's roofline, and the option legs (one-exchange PCG form, Schur complement,
+    relative-pose factors)."""
+    prob = synth.make_config("medium")
+    target = golden_cost("medium")
+    opts = binding.default_options(use_graph=args.graph_mode)
+    n = max(1, min(3, args.steps))
+    out = {"workload": f"medium: {prob.n_cams} cameras, {prob.n_pts} points, {prob.n_obs} observations",
+           "oracle_final_cost": target}
+    out["default"] = solve_leg(binding, prob, opts, torch, stream, flush, n, target)
+    p = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels)
+    p.set_params(prob.cams_init, prob.pts_init)
+    p.evaluate()
+    ku = p.profile_kernels(20)
+    out["kernel_us"] = ku
+    out["roofline_pcg_persistent"] = persistent_roofline(ku, prob, "medium", hbm_peak, alu_peak)
+    p.close()
+    if not args.no_one_exchange:
+        out["pcg_one_exchange"] = solve_leg(binding, prob, binding.default_options(use_graph=args.graph_mode,
+                                                                                   pcg_kernel=2),
+                                            torch, stream, flush, n, target)
+    out["pcg_separate_kernels"] = solve_leg(binding, prob, binding.default_options(use_graph=args.graph_mode,
+                                                                                   pcg_kernel=1),
+                                            torch, stream, flush, n, target)
+    if not args.no_schur:
+        out["schur"] = solve_leg(binding, prob, binding.default_options(use_graph=args.graph_mode, solver=1),
+                                 torch, stream, flush, n, target)
+    if not args.no_factors:
+        fa, fb, fm, fs = synth.make_pose_factors(prob, pairs="chain+skip", seed=5)
+        out["pose_factors"] = dict(n_factors=int(len(fa)),
+                                   **solve_leg(binding, prob, binding.default_options(use_graph=args.graph_mode),
+                                               torch, stream, flush, n, pose_factors=(fa, fb, fm, fs)))
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -259,7 +447,6 @@ def run_ours(args, rank, world, local_rank):
     build.build()
     dev = torch.device("cuda", local_rank)
     prob = synth.make_config(args.config, seed=replica_seed(synth.CONFIGS[args.config]["seed"], rank))
-    target = golden_cost(args.config) if rank == 0 else None
     opts = binding.default_options(use_graph=args.graph_mode)
 
     p = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels)
@@ -268,12 +455,9 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def one_solve():
+    for _ in range(max(3, args.warmup)):
         p.set_params(cams0, pts0)
         p.solve(opts, wait=False)
-
-    for _ in range(max(3, args.warmup)):
-        one_solve()
     torch.cuda.synchronize()
 
     if world > 1:
@@ -281,22 +465,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     sampler = ClockSampler(local_rank)
     sampler.start()
-    step_ms = []
-    pcg = 0
-    lm = 0
-    last = None
-    for _ in range(args.steps):
-        flush.fill_(1)                                   # L2 flush between timed steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        one_solve()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        last = p.stats()
-        pcg += last.pcg_iters_total
-        lm += last.lm_iters
+    step_ms, pcg, last = timed_solves(p, cams0, pts0, opts, args.steps, flush, stream, torch)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -304,72 +473,26 @@ def run_ours(args, rank, world, local_rank):
     total_ms_max, pcg_all = aggregate_over_ranks(sum(step_ms), pcg, world, dev)
     value = pcg_all / (total_ms_max / 1e3)
 
-    # ---- normal-operator kernel: live timing with CUDA events on the launching stream
-    p.set_params(cams0, pts0)
-    p.evaluate()
-    n = 9 * prob.n_cams + 3 * prob.n_pts
-    v = torch.randn(n, dtype=torch.float32, device=dev)
-    p.apply_normal(0.01, v)
-    reps = 200
-    p.repeat_normal(10)
-    flush.fill_(2)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    p.repeat_normal(reps)
-    e1.record(stream)
-    e1.synchronize()
-    mv_ms = e0.elapsed_time(e1) / reps
-    nb, nf = matvec_model(prob)
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
+    # ---- rooflines: per-kernel times in isolation (CUDA events, each launch timed alone),
+    # the operator timed live on its stream; the dominant kernel of the timed step is the
+    # persistent PCG kernel when the tiles fit in shared memory, else the operator
+    peaks = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    sm_mhz = clocks.get("sm_mhz") or 1920.0
     props = torch.cuda.get_device_properties(dev)
     alu_peak = props.multi_processor_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    gbs = nb / (mv_ms / 1e3) / 1e9
-    tfl = nf / (mv_ms / 1e3) / 1e12
-    roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                "frac_of_nominal": gbs / NOMINAL_HBM_GBS}
-    roof_alu = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
-                "traffic": None,
-                "peak_source": "FP32 FMA: SMs x 128 lanes x 2 flop x max SM clock (MEASURED_PEAKS.json sm_max_mhz)"}
-    matvec_roofline = dict(roof_alu if roof_alu["frac"] >= roof_hbm["frac"] else roof_hbm,
-                           kernel="k_matvec (damped normal operator, recomputed Jacobian, multi-kernel path)",
-                           ms_per_launch=mv_ms, algorithmic_bytes=nb, algorithmic_flops=nf)
-
-    # ---- per-kernel times in isolation (CUDA events, warm, back-to-back); the
-    # persistent PCG kernel (one launch = one PCG solve) is the dominant kernel of the
-    # timed step: its roofline is taken from its own event-timed launches
     p.set_params(cams0, pts0)
     p.evaluate()
     kernel_us = p.profile_kernels(20)
-    pb, pf = pcg_iter_model(prob)
-    it_pcg = kernel_us.get("pcg_persistent_iters", 0.0)
-    us_pcg = kernel_us.get("pcg_persistent", -1.0)
-    if us_pcg > 0 and it_pcg > 0:
-        gbs_p = pb * it_pcg / (us_pcg / 1e6) / 1e9
-        roofline = {"bound": "hbm", "achieved": gbs_p, "peak": hbm_peak, "unit": "GB/s", "frac": gbs_p / hbm_peak,
-                    "traffic": measured_traffic("pcg_persistent.cu", args.config),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured, burst copy)",
-                    "kernel": "k_pcg_persistent (one PCG solve per launch, tiles resident in shared memory)",
-                    "us_per_launch": us_pcg, "pcg_iters_per_launch": it_pcg,
-                    "algorithmic_bytes_per_pcg_iter": pb, "algorithmic_flops_per_pcg_iter": pf,
-                    "alu_frac": pf * it_pcg / (us_pcg / 1e6) / 1e12 / alu_peak,
-                    "frac_of_nominal": gbs_p / NOMINAL_HBM_GBS}
-        # context: the same iterations priced at what a stored-Jacobian form would have
-        # to move (96 B of J + 8 B of indices per observation, 36 B per point, 108 B per
-        # camera for the operator, plus the same vector traffic)
-        sj_bytes = 104 * prob.n_obs + 36 * prob.n_pts + 108 * prob.n_cams + (pb - matvec_model(prob)[0])
-        sj_gbs = sj_bytes * it_pcg / (us_pcg / 1e6) / 1e9
-        roofline["stored_jacobian_equivalent"] = {"bytes_per_pcg_iter": sj_bytes, "achieved": sj_gbs,
-                                                  "frac": sj_gbs / hbm_peak}
-    else:
-        roofline = matvec_roofline
-    other = matvec_roofline
+    roof_op = operator_roofline(p, prob, args.config, torch, stream, flush, hbm_peak, alu_peak)
+    roof_pp = persistent_roofline(kernel_us, prob, args.config, hbm_peak, alu_peak)
+    roofline = roof_pp if roof_pp is not None else roof_op
+    # the separate-kernel PCG iteration as a whole (operator + update) against its bytes
+    pcg_us = kernel_us["matvec"] + kernel_us["update"]
+    pcg_bytes = pcg_iter_tile_model(prob)
+    roof_iter = {"us_per_pcg_iter": pcg_us, "algorithmic_bytes": pcg_bytes,
+                 "achieved": pcg_bytes / (pcg_us / 1e6) / 1e9, "frac": pcg_bytes / (pcg_us / 1e6) / 1e9 / hbm_peak,
+                 "unit": "GB/s", "kernels": "k_cam_direction + k_tile_normal + k_update (isolated launches)",
+                 "update_us": kernel_us["update"]}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -407,111 +530,32 @@ def run_ours(args, rank, world, local_rank):
                "path": "ba_problem_create + ba_bind_workspace (upload + ordering) + ba_set_params + ba_solve "
                        "+ ba_get_params, host FP64 arrays"}
 
-    # ---- plain all-FP64 GPU form on the same problem
+    # ---- plain all-FP64 GPU form on the same problem: the time-to-cost target C* is its
+    # final cost after the same budget (workloads without a stored oracle cost)
     fp64 = None
+    target = golden_cost(args.config)
+    target_src = "FP64 oracle, same budget (tests/golden)" if target is not None else None
     if not args.no_fp64:
         try:
             q = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels, precision="fp64")
             q.set_params(cams0, pts0)
             q.solve(opts, wait=False)
             torch.cuda.synchronize()
-            ms = []
-            pc = 0
-            for _ in range(max(1, min(3, args.steps))):
-                flush.fill_(3)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                q.set_params(cams0, pts0)
-                q.solve(opts, wait=False)
-                e1.record(stream)
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-                st64 = q.stats()
-                pc += st64.pcg_iters_total
+            ms, pc, st64 = timed_solves(q, cams0, pts0, opts, max(1, min(3, args.steps)), flush, stream, torch, 3)
+            if target is None:
+                target, target_src = st64.final_cost, "plain FP64 GPU form's final cost, same budget and inputs"
             fp64 = {"value": pc / (sum(ms) / 1e3), "unit": UNIT, "ms_per_solve": sum(ms) / len(ms),
-                    "final_cost": st64.final_cost, "time_to_cost_ms": time_to_cost(st64.history, target * (1 + 1e-4)
-                                                                                   if target else None)}
+                    "final_cost": st64.final_cost, "pcg_iters_per_solve": pc / len(ms),
+                    "time_to_cost_ms": time_to_cost(st64.history, target * (1 + 1e-4)),
+                    "roofline_note": "stored FP64 Jacobian (200 B per observation per operator) with per-observation "
+                                     "FP64 atomics: see DESIGN.md for its own HBM fraction"}
             q.close()
         except binding.BAError as e:
             fp64 = {"unavailable": str(e)}
 
-    # ---- the Schur-complement solver on the same problem (PCG on the camera system)
-    schur = None
-    if not args.no_schur:
-        so = binding.default_options(use_graph=args.graph_mode, solver=1)
-        p.set_params(cams0, pts0)
-        p.solve(so, wait=False)
-        torch.cuda.synchronize()
-        ms, pc = [], 0
-        for _ in range(max(1, min(3, args.steps))):
-            flush.fill_(5)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            p.set_params(cams0, pts0)
-            p.solve(so, wait=False)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            sst = p.stats()
-            pc += sst.pcg_iters_total
-        schur = {"ms_per_solve": sum(ms) / len(ms), "pcg_iters_per_solve": pc / len(ms),
-                 "pcg_iters_per_s": pc / (sum(ms) / 1e3), "final_cost": sst.final_cost,
-                 "time_to_cost_ms": time_to_cost(sst.history, target * (1 + 1e-4) if target else None)}
-
-    # ---- the same solve with the persistent kernel's one-exchange form (pcg_kernel = 2)
-    one_x = None
-    if not args.no_one_exchange:
-        xo = binding.default_options(use_graph=args.graph_mode, pcg_kernel=2)
-        p.set_params(cams0, pts0)
-        p.solve(xo, wait=False)
-        torch.cuda.synchronize()
-        ms, pc = [], 0
-        for _ in range(max(1, min(3, args.steps))):
-            flush.fill_(5)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            p.set_params(cams0, pts0)
-            p.solve(xo, wait=False)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            xst = p.stats()
-            pc += xst.pcg_iters_total
-        one_x = {"ms_per_solve": sum(ms) / len(ms), "pcg_iters_per_solve": pc / len(ms),
-                 "pcg_iters_per_s": pc / (sum(ms) / 1e3), "final_cost": xst.final_cost,
-                 "time_to_cost_ms": time_to_cost(xst.history, target * (1 + 1e-4) if target else None)}
-
-    # ---- the same problem with relative-pose factors between cameras (odometry chain
-    # plus skip links, 2 per camera): the generic-factor path
-    factors = None
-    if not args.no_factors:
-        fa, fb, fm, fs = synth.make_pose_factors(prob, pairs="chain+skip", seed=5)
-        pf = binding.Problem(prob.n_cams, prob.n_pts, prob.cam_idx, prob.pt_idx, prob.pixels,
-                             pose_factors=(fa, fb, fm, fs))
-        fo = binding.default_options(use_graph=args.graph_mode)
-        pf.set_params(cams0, pts0)
-        pf.solve(fo, wait=False)
-        torch.cuda.synchronize()
-        ms, pc = [], 0
-        for _ in range(max(1, min(3, args.steps))):
-            flush.fill_(5)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            pf.set_params(cams0, pts0)
-            pf.solve(fo, wait=False)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            fst = pf.stats()
-            pc += fst.pcg_iters_total
-        factors = {"n_factors": int(len(fa)), "ms_per_solve": sum(ms) / len(ms), "pcg_iters_per_solve": pc / len(ms),
-                   "pcg_iters_per_s": pc / (sum(ms) / 1e3), "initial_cost": fst.initial_cost,
-                   "final_cost": fst.final_cost, "lm_iters": fst.lm_iters}
-        pf.close()
+    medium = None
+    if args.config != "medium" and not args.no_medium:
+        medium = medium_legs(args, binding, synth, torch, dev, stream, flush, hbm_peak, alu_peak)
 
     # ---- differentiation pattern: the autograd entries (forward cost, hand-written
     # adjoint backward) on the 200-camera, 50,000-point workload, time per observation
@@ -545,7 +589,12 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None if args.no_batch else run_batched(args, binding, synth, torch, dev, stream, flush, rank)
 
-    launches_per_step = 1 + 3 + 5 * last.lm_iters + 3 * last.pcg_iters_total + 1
+    # kernels of one solve: init (state, camera records, linearisation) + per LM
+    # iteration 5 (preconditioner, candidate, its evaluation, commit, relinearisation)
+    # + per separate-kernel PCG iteration 3 (camera directions, tile operator, update)
+    # or one persistent launch per LM iteration + the closing state kernel
+    per_pcg = 3 if roof_pp is None else 0
+    launches_per_step = 3 + 5 * last.lm_iters + per_pcg * last.pcg_iters_total + (last.lm_iters if roof_pp else 0) + 1
     ttc = time_to_cost(last.history, target * (1 + 1e-4) if target else None)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -554,15 +603,18 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": f"{args.config}: {prob.n_cams} cameras, {prob.n_pts} points, {prob.n_obs} observations,"
                                f" 20 LM x <=50 PCG, TR0=100, CG tol 1e-3",
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-        "final_cost": last.final_cost, "oracle_final_cost": target,
-        "time_to_cost_ms": ttc, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
+        "final_cost": last.final_cost, "lm_iters": last.lm_iters, "pcg_iters_per_solve": last.pcg_iters_total,
+        "time_to_cost": {"target": target, "target_source": target_src, "rel_band": 1e-4, "mixed_ms": ttc,
+                         "fp64_plain_ms": fp64.get("time_to_cost_ms") if fp64 else None},
         "step_ms": step_ms,
-        "roofline": roofline, "roofline_matvec": other,
-        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "schur": schur, "pcg_one_exchange": one_x, "pose_factors": factors, "autograd": grad_leg, "batched": batched,
-        "memory": {"arena_bytes": p.workspace_bytes, "torch_max_allocated_bytes": torch.cuda.max_memory_allocated()}, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+        "roofline": roofline, "roofline_operator": roof_op, "roofline_pcg_iteration": roof_iter,
+        "kernel_us": kernel_us, "e2e": e2e, "fp64_plain": fp64, "medium": medium, "autograd": grad_leg,
+        "batched": batched,
+        "memory": {"arena_bytes": p.workspace_bytes, "torch_max_allocated_bytes": torch.cuda.max_memory_allocated()},
+        "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(prob)
+        out["cpu_baseline"] = cpu_baseline(prob, args.config)
     if rank == 0:
         print(json.dumps(out), flush=True)
 

@@ -258,7 +258,8 @@ ba_status ba_apply_normal(ba_problem* problem, double mu, const void* v, void* o
 ba_status ba_repeat_normal(ba_problem* problem, int32_t launches);
 
 /* Times each kernel of the solver in isolation with CUDA events on the bound stream:
- * `reps` back-to-back launches each, after a prior ba_evaluate or ba_solve.  Writes
+ * `reps` launches each (after one warm-up launch), every launch timed alone with its
+ * gates opened just before it, after a prior ba_evaluate or ba_solve.  Writes
  * the average microseconds per launch into us_out[0..n) in this order: camera
  * records, linearisation, preconditioner, normal operator (matvec), PCG update,
  * candidate step, candidate evaluation, commit; then [8] one launch of the persistent

@@ -82,6 +82,10 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     const size_t nfc = 2 * (size_t)std::max(0, n_fac);
     l.blk_cams = b.take(4 * std::min(no + nfc + nc + MAX_PBLOCKS, (size_t)(MAX_PBLOCKS * 4096)));
     l.pslots = b.take(8 * PSLOT_TOTAL);
+    // long-run tables: a tile holds at most (its observations / LONG_RUN) long runs
+    l.long_off = b.take(4 * (n_tiles + 1));
+    l.long_run = b.take(12 * (no / LONG_RUN + n_tiles));
+    l.short_start = b.take(4 * n_tiles);
     const size_t union_base = align_up(b.off, 256);
     // solver arrays
     Bump s;
@@ -148,6 +152,9 @@ Views<T> make_views(ba_problem* p) {
     v.pt_internal = (const uint32_t*)(w + l.pt_internal);
     v.obs_pm = (const uint32_t*)(w + l.obs_pm);
     v.pt_obs_off = (const uint32_t*)(w + l.pt_obs_off);
+    v.long_off = (const uint32_t*)(w + l.long_off);
+    v.long_run = (const uint32_t*)(w + l.long_run);
+    v.short_start = (const uint32_t*)(w + l.short_start);
     T** vecs[9] = {&v.x, &v.x_new, &v.h, &v.r, &v.z, &v.p, &v.q, &v.g, &v.D};
     for (int i = 0; i < 9; ++i) *vecs[i] = (T*)(w + l.vec[i]);
     v.cam_pre = (float*)(w + l.cam_pre);
@@ -747,6 +754,12 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
     if (p->precision == BA_PREC_MIXED) {
         ba_status pst = plan_persistent(p, sms);
         if (pst) return pst;
+        std::vector<uint32_t> toff((size_t)p->n_tiles + 1);
+        GBBA_CUDA(cudaMemcpy(toff.data(), p->vf.tile_off, 4 * toff.size(), cudaMemcpyDeviceToHost));
+        uint32_t most = 1;
+        for (int t = 0; t < p->n_tiles; ++t) most = std::max(most, toff[t + 1] - toff[t]);
+        plan_tile_kernels(p->L, p->n_tiles, sms, (int)most);
+        GBBA_CUDA(cudaGetLastError());
     }
     p->bound = true;
     return BA_OK;
@@ -1084,17 +1097,22 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
     cudaEvent_t e0, e1;
     GBBA_CUDA(cudaEventCreate(&e0));
     GBBA_CUDA(cudaEventCreate(&e1));
+    // each launch timed alone, its gates opened just before it (a kernel that closes a
+    // gate, e.g. the LM decision, would otherwise leave the next launches idle); the
+    // first launch warms up
     auto timeit = [&](auto&& launch) -> double {
-        open_gates();
-        launch();   // warm
-        open_gates();
-        cudaEventRecord(e0, s);
-        for (int i = 0; i < reps; ++i) launch();
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        return 1e3 * ms / reps;
+        double total = 0.0;
+        for (int i = 0; i <= reps; ++i) {
+            open_gates();
+            cudaEventRecord(e0, s);
+            launch();
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (i > 0) total += ms;
+        }
+        return 1e3 * total / reps;
     };
     // the persistent PCG kernel first, while the state is the caller's linearisation:
     // one launch = one PCG solve (50 iterations, zero tolerance), timed alone after a
@@ -1133,7 +1151,24 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
     out[1] = timeit([&] { launch_linearize(v, p->L, s, 1, nullptr, nullptr, 0, 0); });
     out[2] = timeit([&] { launch_precond(v, p->L, s, 0, 0, nullptr); });
     out[3] = timeit([&] { launch_matvec(v, p->L, s, nullptr, v.z, 1); });
-    out[4] = timeit([&] { launch_update(v, p->L, s, 0, 0); });
+    {
+        // the update skips its work once the operator sums it consumes are cleared, so
+        // each timed launch follows a re-armed |J p|^2 slot and is timed alone
+        const double one = 1.0;
+        double total = 0.0;
+        for (int i = 0; i <= reps; ++i) {
+            open_gates();
+            GBBA_CUDA(cudaMemcpyAsync(&v.st->acc_mv[0], &one, sizeof(double), cudaMemcpyHostToDevice, s));
+            cudaEventRecord(e0, s);
+            launch_update(v, p->L, s, 0, 0);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (i > 0) total += ms;
+        }
+        out[4] = 1e3 * total / reps;
+    }
     out[5] = timeit([&] { launch_candidate(v, p->L, s); });
     out[6] = timeit([&] { launch_eval_candidate(v, p->L, s, 0, 0); });
     out[7] = timeit([&] { launch_commit(v, p->L, s); });

@@ -104,6 +104,63 @@ __device__ __forceinline__ double rcp64(double x) {
     return y;
 }
 
+// Kahan's compensated summation (W. Kahan, "Further remarks on reducing truncation
+// errors", CACM 8(1), 1965) of FP32 terms: s - c is the running sum, c the negated
+// low-order part lost so far.  Per-thread partials of the FP64 reductions use it, so a
+// thread's FP32 sum over many terms keeps the accuracy of its largest term's rounding.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly (s = fl(a + b)).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp sum of per-lane compensated values hi + lo in FP32 pairs: every level adds the
+// partner's high parts with TwoSum and carries the rounding error into the low parts,
+// so the result has about twice FP32's precision (FP64 shuffles cost ~67x more on this
+// GPU).  Result valid in lane 0 as a double.
+__device__ __forceinline__ double warp_sum_pair(float hi, float lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, h2, s, e);
+        hi = s;
+        lo = lo + l2 + e;
+    }
+    return (double)hi + (double)lo;
+}
+
+// Block sums of two compensated per-thread partials (Kahan pairs s - c): compensated
+// FP32 pairs inside each warp, FP64 across warps.  Results valid in thread 0.  `sh`
+// holds 2 * (blockDim.x / 32) doubles.  Contains __syncthreads.
+__device__ __forceinline__ void block_sum2c(float sa, float ca, float sb, float cb, double* sh, double& ra,
+                                            double& rb) {
+    const double a = warp_sum_pair(sa, -ca), b = warp_sum_pair(sb, -cb);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sh[w] = a;
+        sh[nw + w] = b;
+    }
+    __syncthreads();
+    ra = rb = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < nw; ++i) {
+            ra += sh[i];
+            rb += sh[nw + i];
+        }
+    }
+}
+
 // Block sums of two FP32 per-thread partials: FP32 inside each warp (32 terms), FP64
 // across warps.  Results valid in thread 0.  `sh` holds 2 * (blockDim.x / 32) doubles.
 __device__ __forceinline__ void block_sum2(float a, float b, double* sh, double& ra, double& rb) {

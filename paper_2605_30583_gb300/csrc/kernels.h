@@ -32,6 +32,13 @@ struct LaunchCfg {
     int lin_grid = 1024;    // cap on blocks of tile kernels
     int mv_grid = 1024;
     int ev_grid = 1024;
+    // tile kernels (tile_kernels.cu: long runs in camera-uniform warp steps); a grid of 0
+    // selects the per-thread-chunk kernel of kernels_mixed.cu instead
+    int tn_grid = 0;   // normal operator, one CTA per tile
+    int tl_grid = 0;   // linearisation
+    int te_grid = 0;   // candidate evaluation
+    int tk_key_cap = 0;                      // observations of the largest tile, rounded up to 32
+    int tn_smem = 0, tl_smem = 0, te_smem = 0;   // their dynamic shared memory (staged observations)
 };
 
 // mixed precision (kernels_mixed.cu)
@@ -44,6 +51,13 @@ void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, co
                    const float* zs, int use_beta);
 void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
                    int cameras_only = 0);
+// tile kernels (tile_kernels.cu): launch shapes, then the launches
+void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs);
+void launch_tile_normal(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
+                        const float* zs, int use_beta);
+void launch_tile_eval(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle lm_cond, int use_cond);
+void launch_tile_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode, float* res_out,
+                           float* jac_out, CondHandle lm_cond, int use_cond);
 // Schur-complement PCG (kernels_mixed.cu): mode 0 right-hand side, 1 operator, 2 back-substitution
 void launch_schur(const Views<float>& v, cudaStream_t s, int mode, const int32_t* gate);
 void launch_schur_start(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use);
@@ -141,5 +155,6 @@ template <typename T>
 void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s);
 // Ascending sort of (key, value) pairs, n a power of two >= 2 (order.cu).
 void sort_pairs(uint64_t* keys, uint32_t* vals, size_t n, cudaStream_t s);
+
 
 }  // namespace gbba

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
     // robust loss (evaluation, mode 2, is always the squared loss)
     const int loss = mode == 2 ? 0 : v.st->opt.loss;
     const float lscale = (float)v.st->opt.loss_scale;
-    float cost = 0.0f;
+    float cost = 0.0f, costc = 0.0f;   // Kahan pair
     for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
         const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
         const int pt0 = tile * TILE_PTS;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
                 if (loss) {   // IRLS weight w = rho'(|r|^2): rows scaled by sqrt(w)
                     const float w = loss_weight(s2, loss, lscale);
                     if (mode != 2) v.obs_w[j] = w;
-                    cost += loss_rho(s2, loss, lscale);
+                    kahan_add(cost, costc, loss_rho(s2, loss, lscale));
                     const float sw = sqrtf(w);
                     r0 *= sw;
                     r1 *= sw;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
 #pragma unroll
                     for (int q = 0; q < 3; ++q) { jx0[q] *= sw; jx1[q] *= sw; }
                 } else {
-                    cost += s2;
+                    kahan_add(cost, costc, s2);
                 }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) acc[CL_G + i] = fmaf(j0[i], r0, fmaf(j1[i], r1, acc[CL_G + i]));
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
             for (int q = 0; q < PH_STRIDE; ++q) v.pt_H[(size_t)(pt0 + i) * PH_STRIDE + q] = sh[6 * i + q];
         }
     }
-    double in[1] = {(double)cost}, out[1];
+    double in[1] = {(double)cost - (double)costc}, out[1];
     if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_LIN], out) && threadIdx.x == 0) {
         DevState* st = v.st;
         const double F = 0.5 * out[0] + (v.n_fac > 0 ? st->fac_cost : 0.0);   // pose factors: k_factor_linearize
@@ -369,7 +369,7 @@ __global__ void k_cam_direction(Views<float> v, const int32_t* gate, const float
     const float beta = use_beta ? (float)st->beta : 0.0f;
     const float* pc_old = v.pc + (size_t)par * v.pc_stride;
     float* pc_new = v.pc + (size_t)(par ^ 1) * v.pc_stride;
-    float pdp = 0.0f;
+    float pdp = 0.0f, pdpc = 0.0f;   // Kahan pair
     const int n = 9 * v.n_cams;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const int c = e / 9, k = e - 9 * c;
@@ -379,7 +379,7 @@ __global__ void k_cam_direction(Views<float> v, const int32_t* gate, const float
         };
         const float pk = p_of(k);
         pc_new[e] = pk;
-        pdp = fmaf(v.D[e] * pk, pk, pdp);
+        kahan_add(pdp, pdpc, v.D[e] * pk * pk);
         float d = pk;
         if (k < 3) {
             const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL + 3 * k;
@@ -387,7 +387,7 @@ __global__ void k_cam_direction(Views<float> v, const int32_t* gate, const float
         }
         v.cam_dir[(size_t)c * CD_STRIDE + k] = d;   // CD_PHI = 0, CD_T = 3, CD_I = 6
     }
-    const double bp = block_sum((double)pdp, red);
+    const double bp = block_sum((double)pdp - (double)pdpc, red);
     if (threadIdx.x == 0) slot_add(st->acc_mv, 1, bp);
 }
 
@@ -408,7 +408,8 @@ __global__ void __launch_bounds__(TB, 8) k_matvec(Views<float> v, const int32_t*
     const float mu = (float)st->mu;
     const float eps = (float)st->opt.eps;
     const bool weighted = st->opt.loss != 0;
-    float pdp = 0.0f, jp2 = 0.0f;   // the camera part of p^T D p comes from k_cam_direction
+    // Kahan pairs; the camera part of p^T D p comes from k_cam_direction
+    float pdp = 0.0f, jp2 = 0.0f, pdpc = 0.0f, jp2c = 0.0f;
     for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
         const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
         const int pt0 = tile * TILE_PTS;
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(TB, 8) k_matvec(Views<float> v, const int32_t*
             sd[i] = pn;
             sx[i] = v.x[base + i];
             sq[i] = 0.0f;
-            pdp = fmaf(v.D[base + i] * pn, pn, pdp);
+            kahan_add(pdp, pdpc, v.D[base + i] * pn * pn);
         }
         __syncthreads();
         const uint32_t n = hi - lo;
@@ -443,8 +444,8 @@ __global__ void __launch_bounds__(TB, 8) k_matvec(Views<float> v, const int32_t*
                 load_dir(v.cam_dir + (size_t)c * CD_STRIDE, dir);   // from k_cam_direction
             }
             if (weighted) {   // robust loss: per-observation IRLS weights
-                jp2 += obs_normal<true>(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc, sq + 3 * slot,
-                                        __ldg(v.obs_w + j));
+                kahan_add(jp2, jp2c, obs_normal<true>(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc,
+                                                      sq + 3 * slot, __ldg(v.obs_w + j)));
                 j += 1;
                 continue;
             }
@@ -455,12 +456,13 @@ __global__ void __launch_bounds__(TB, 8) k_matvec(Views<float> v, const int32_t*
                     const uint32_t slot1 = key1 & 0xffu;
                     const float a0 = obs_normal(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc, sq + 3 * slot);
                     const float a1 = obs_normal(cam, dir, sx + 3 * slot1, sd + 3 * slot1, eps, acc, sq + 3 * slot1);
-                    jp2 += a0 + a1;
+                    kahan_add(jp2, jp2c, a0);
+                    kahan_add(jp2, jp2c, a1);
                     j += 2;
                     continue;
                 }
             }
-            jp2 += obs_normal(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc, sq + 3 * slot);
+            kahan_add(jp2, jp2c, obs_normal(cam, dir, sx + 3 * slot, sd + 3 * slot, eps, acc, sq + 3 * slot));
             j += 1;
         }
         const bool head = seg_reduce<9>(cur, acc);
@@ -469,8 +471,8 @@ __global__ void __launch_bounds__(TB, 8) k_matvec(Views<float> v, const int32_t*
         for (int i = threadIdx.x; i < 3 * npt; i += TB) v.q[base + i] = fmaf(mu * v.D[base + i], sd[i], sq[i]);
         __syncthreads();
     }
-    const double bj = block_sum((double)jp2, red);
-    const double bp = block_sum((double)pdp, red);
+    const double bj = block_sum((double)jp2 - (double)jp2c, red);
+    const double bp = block_sum((double)pdp - (double)pdpc, red);
     if (threadIdx.x == 0) {
         slot_add(st->acc_mv, 0, bj);
         slot_add(st->acc_mv, 1, bp);
@@ -489,7 +491,7 @@ __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond, int 
     __shared__ double sh_mv[2];
     __shared__ bool is_last;
     const int active = st->pcg_active;
-    float rz = 0.0f, rr = 0.0f;
+    float rz = 0.0f, rr = 0.0f, rzc = 0.0f, rrc = 0.0f;   // Kahan pairs
     double alpha_d = 0.0;
     bool bad = false;
     if (active) {
@@ -534,8 +536,8 @@ __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond, int 
 #pragma unroll
                 for (int k = 0; k < 9; ++k) z = fmaf(M[9 * i + k], rn[k], z);
                 v.z[e + i] = z;
-                rz = fmaf(rn[i], z, rz);
-                rr = fmaf(rn[i], rn[i], rr);
+                kahan_add(rz, rzc, rn[i] * z);
+                kahan_add(rr, rrc, rn[i] * rn[i]);
             }
         }
         for (int qd = blockIdx.x * blockDim.x + threadIdx.x; !cameras_only && qd < v.n_quads;
@@ -576,9 +578,9 @@ __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond, int 
                 Z[3 * j + 2] = fmaf(m[2], rj[0], fmaf(m[4], rj[1], m[5] * rj[2]));
             }
 #pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                rz = fmaf(R[k], Z[k], rz);
-                rr = fmaf(R[k], R[k], rr);
+            for (int k = 0; k < 12; k += 3) {
+                kahan_add(rz, rzc, fmaf(R[k], Z[k], fmaf(R[k + 1], Z[k + 1], R[k + 2] * Z[k + 2])));
+                kahan_add(rr, rrc, fmaf(R[k], R[k], fmaf(R[k + 1], R[k + 1], R[k + 2] * R[k + 2])));
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -588,8 +590,8 @@ __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond, int 
             }
         }
     }
-    const double brz = block_sum((double)rz, red);
-    const double brr = block_sum((double)rr, red);
+    const double brz = block_sum((double)rz - (double)rzc, red);
+    const double brr = block_sum((double)rr - (double)rrc, red);
     if (threadIdx.x == 0) {
         if (active && !bad) {
             slot_add(st->acc_up, 0, brz);
@@ -718,7 +720,7 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
             uint32_t cur = NO_CAM;
             Cam cn, co;
             float dir[9];
-            float fc = 0.0f, jc = 0.0f;
+            float fc = 0.0f, jc = 0.0f, fcc = 0.0f, jcc = 0.0f;   // Kahan pairs
             for (uint32_t j = a; j < b; ++j) {
                 const uint32_t key = __ldg(v.obs_key + j);
                 const uint32_t c = key >> 8, slot = key & 0xffu;
@@ -736,15 +738,15 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
                 float t0, t1;
                 jdir(g, co, dir, v.h[xi], v.h[xi + 1], v.h[xi + 2], t0, t1);
                 if (loss) {   // F' = 1/2 sum rho(|r'|^2); |J h|^2 weighted at x
-                    fc += loss_rho(fmaf(r0, r0, r1 * r1), loss, lscale);
-                    jc = fmaf(__ldg(v.obs_w + j), fmaf(t0, t0, t1 * t1), jc);
+                    kahan_add(fc, fcc, loss_rho(fmaf(r0, r0, r1 * r1), loss, lscale));
+                    kahan_add(jc, jcc, __ldg(v.obs_w + j) * fmaf(t0, t0, t1 * t1));
                 } else {
-                    fc = fmaf(r0, r0, fmaf(r1, r1, fc));
-                    jc = fmaf(t0, t0, fmaf(t1, t1, jc));
+                    kahan_add(fc, fcc, fmaf(r0, r0, r1 * r1));
+                    kahan_add(jc, jcc, fmaf(t0, t0, t1 * t1));
                 }
             }
-            fnew += (double)fc;
-            jh2 += (double)jc;
+            fnew += (double)fc - (double)fcc;
+            jh2 += (double)jc - (double)jcc;
         }
     }
     double in[2] = {fnew, jh2}, out[2];
@@ -1124,9 +1126,12 @@ void launch_camera_precompute(const Views<float>& v, const LaunchCfg& L, cudaStr
 }
 void launch_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode,
                       float* res_out, float* jac_out, CondHandle lm_cond, int use_cond) {
-    launch_factor_linearize(v, L, s, mode);   // its cost is added by k_linearize
-    k_linearize<LIN_TB><<<grid_tiles(L.lin_grid, v.n_tiles), LIN_TB, 0, s>>>(v, mode, res_out, jac_out,
-                                                                             lm_cond, use_cond);
+    launch_factor_linearize(v, L, s, mode);   // its cost is added by the linearisation
+    if (L.tl_grid > 0)   // tiles with their camera tables in shared memory
+        launch_tile_linearize(v, L, s, mode, res_out, jac_out, lm_cond, use_cond);
+    else
+        k_linearize<LIN_TB><<<grid_tiles(L.lin_grid, v.n_tiles), LIN_TB, 0, s>>>(v, mode, res_out, jac_out,
+                                                                                 lm_cond, use_cond);
 }
 void launch_precond(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
                     double* pslots) {
@@ -1141,7 +1146,10 @@ void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, co
     // one thread per camera entry, no more blocks than that needs (each adds one slot sum)
     const int cd_grid = std::max(1, std::min(L.item_grid, (9 * v.n_cams + L.item_block - 1) / L.item_block));
     k_cam_direction<<<cd_grid, L.item_block, 0, s>>>(v, gate, zs, use_beta);
-    k_matvec<MV_TB><<<v.n_tiles > 0 ? v.n_tiles : 1, MV_TB, 0, s>>>(v, gate, zs, use_beta);
+    if (L.tn_grid > 0)   // tiles with their camera tables in shared memory
+        launch_tile_normal(v, L, s, gate, zs, use_beta);
+    else
+        k_matvec<MV_TB><<<v.n_tiles > 0 ? v.n_tiles : 1, MV_TB, 0, s>>>(v, gate, zs, use_beta);
     launch_factor_matvec(v, L, s, gate, zs, use_beta);   // pose factors, if any
 }
 void launch_schur(const Views<float>& v, cudaStream_t s, int mode, const int32_t* gate) {
@@ -1163,7 +1171,10 @@ void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s)
 }
 void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
     launch_factor_eval(v, L, s);
-    k_eval_candidate<EV_TB><<<grid_tiles(L.ev_grid, v.n_tiles), EV_TB, 0, s>>>(v, c, use);
+    if (L.te_grid > 0)   // tiles with their camera tables in shared memory
+        launch_tile_eval(v, L, s, c, use);
+    else
+        k_eval_candidate<EV_TB><<<grid_tiles(L.ev_grid, v.n_tiles), EV_TB, 0, s>>>(v, c, use);
 }
 void launch_commit(const Views<float>& v, const LaunchCfg& L, cudaStream_t s) {
     k_commit<<<grid_items(L, v.n_cams + v.n_pts), L.item_block, 0, s>>>(v);

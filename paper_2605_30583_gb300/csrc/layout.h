@@ -28,6 +28,8 @@ constexpr int PSLOT_TOTAL = 3 * NSLOT * SLOT_STRIDE;
 static_assert(XCH_NV <= SLOT_STRIDE, "a slot holds every sum of one exchange");
 // Camera accumulator sets of the one-exchange kernel (rotating over iterations).
 constexpr int CA_SETS = 3;
+// A camera run of a tile this long or longer is walked in camera-uniform warp steps.
+constexpr int LONG_RUN = 32;
 
 // Camera record (floats), written once per parameter change (FP64 math, FP32 store).
 enum : int { CP_R = 0, CP_T = 9, CP_F = 12, CP_K1 = 13, CP_K2 = 14, CP_PAD = 15,
@@ -104,6 +106,13 @@ struct Views {
     const uint32_t* pt_internal; // caller -> internal point index
     const uint32_t* obs_pm;      // point-major order: positions (in the order above) of each
     const uint32_t* pt_obs_off;  //   internal point's observations, offsets [n_pts + 1]
+    // long runs: inside a tile the camera runs of at least LONG_RUN observations come
+    // first; long_run[3 e + 0, 1, 2] = start (absolute position), length and camera of long
+    // run e, tile t's long runs are e in [long_off[t], long_off[t + 1]), and its short runs
+    // occupy [short_start[t], tile_off[t + 1])
+    const uint32_t* long_off;       // [n_tiles + 1]
+    const uint32_t* long_run;       // [3 * long runs]
+    const uint32_t* short_start;    // [n_tiles]
     // vectors of length n_vec
     T *x, *x_new, *h, *r, *z, *p, *q, *g, *D;
     // camera records

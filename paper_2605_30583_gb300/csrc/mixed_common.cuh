@@ -30,6 +30,45 @@ __device__ __forceinline__ bool seg_reduce(uint32_t key, float (&acc)[V]) {
     return head;
 }
 
+// Warp sum of N per-lane values by recursive halving: at each of the five levels the two
+// lanes of a pair (lane, lane ^ o) split the values they still carry, each keeping one
+// half and adding the partner's copy of it (about 4 N + 10 instructions, where a
+// butterfly of every value takes 10 N).  Every lane ends with split_sum_slots(N) values;
+// the first `returned` of them are complete sums, v[k] of value idx + k, and together
+// the lanes hold each of the N sums exactly once.
+__host__ __device__ constexpr int split_sum_slots(int n) {
+    return ((((((n + 1) / 2 + 1) / 2 + 1) / 2 + 1) / 2) + 1) / 2;
+}
+
+template <int N>
+__device__ __forceinline__ int warp_split_sum(float (&v)[N], int lane, int& idx) {
+    int m = N;    // values every lane carries (the same in all lanes)
+    int rc = N;   // of which real (the rest pad the upper halves of odd splits)
+    idx = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int h = (m + 1) / 2;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < (N + 1) / 2; ++k) {
+            if (k < h) {
+                const float hi = (k + h < m) ? v[k + h] : 0.0f;
+                const float send = up ? v[k] : hi;
+                const float keep = up ? hi : v[k];
+                v[k] = keep + __shfl_xor_sync(FULL, send, o);
+            }
+        }
+        if (up) {
+            idx += h;
+            rc = rc > h ? rc - h : 0;
+        } else {
+            rc = rc < h ? rc : h;
+        }
+        m = h;
+    }
+    return rc;
+}
+
 __device__ __forceinline__ void flush_matvec(float* __restrict__ dst, float (&a)[9]) {
     atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a[0], a[1], a[2], a[3]));
     atomicAdd(reinterpret_cast<float4*>(dst + 4), make_float4(a[4], a[5], a[6], a[7]));

@@ -5,7 +5,8 @@
 //     sorted by (key, caller index), giving the internal point order;
 //  2. tiles are TILE_PTS consecutive internal points;
 //  3. observations are sorted by (tile, camera, tile slot, caller index), so a
-//     tile's observations are contiguous and grouped into camera runs.
+//     tile's observations are contiguous and grouped into camera runs;
+//  4. inside each tile the runs of at least LONG_RUN observations move to the front.
 //
 // Sorting is a bitonic network on (64-bit key, 32-bit value) pairs: shared-memory
 // passes for distances below 2048 elements and global passes above.  Deterministic
@@ -128,10 +129,101 @@ __global__ void k_obs_gather(const uint64_t* keys, const uint32_t* vals, const d
 }
 
 // Point-major index: key = (internal point, position in the tile-major order).
-__global__ void k_pm_keys(const uint32_t* vals, const uint32_t* pt_idx, const uint32_t* pt_internal, int64_t n_obs,
-                          size_t sort_n, uint64_t* keys) {
+__global__ void k_pm_keys(const uint32_t* obs_user, const uint32_t* pt_idx, const uint32_t* pt_internal,
+                          int64_t n_obs, size_t sort_n, uint64_t* keys) {
     for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < sort_n; j += (size_t)gridDim.x * blockDim.x)
-        keys[j] = j < (size_t)n_obs ? (((uint64_t)pt_internal[pt_idx[vals[j]]] << 32) | (uint64_t)j) : ~0ull;
+        keys[j] = j < (size_t)n_obs ? (((uint64_t)pt_internal[pt_idx[obs_user[j]]] << 32) | (uint64_t)j) : ~0ull;
+}
+
+// --- long runs first ------------------------------------------------------------------
+// Inside each tile the camera runs of length >= LONG_RUN move to the front (camera order
+// kept), the short runs follow.  The tile kernels walk the long runs in camera-uniform
+// steps of 32 observations and the short tail thread by thread; every other kernel only
+// needs each camera's observations of a tile to be contiguous, which stays true.  One
+// warp per tile walks the runs, 32 observations at a time (ballot of run heads).
+
+// Calls visit(start, len) for every run of tile [lo, hi) in order (uniform in the warp).
+template <typename F>
+__device__ __forceinline__ void for_each_run(const uint32_t* __restrict__ obs_key, uint32_t lo, uint32_t hi, F&& visit) {
+    const int lane = threadIdx.x & 31;
+    uint32_t cur = lo;
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t j = base + lane;
+        const bool head = j < hi && j > lo && (obs_key[j - 1] >> 8) != (obs_key[j] >> 8);
+        uint32_t hm = __ballot_sync(0xffffffffu, head);
+        while (hm) {
+            const uint32_t h = base + (uint32_t)(__ffs(hm) - 1);
+            visit(cur, h - cur);
+            cur = h;
+            hm &= hm - 1u;
+        }
+    }
+    if (hi > lo) visit(cur, hi - cur);
+}
+
+__global__ void k_long_count(const uint32_t* __restrict__ obs_key, const uint32_t* __restrict__ tile_off, int n_tiles,
+                             uint32_t* n_long, uint32_t* long_obs) {
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_tiles; t += warps) {
+        uint32_t nl = 0, no = 0;
+        for_each_run(obs_key, tile_off[t], tile_off[t + 1], [&](uint32_t, uint32_t len) {
+            if (len >= (uint32_t)LONG_RUN) { ++nl; no += len; }
+        });
+        if ((threadIdx.x & 31) == 0) {
+            n_long[t] = nl;
+            long_obs[t] = no;
+        }
+    }
+}
+
+// Copies each run to its place (long runs from the tile's start, short runs after them)
+// and writes the long-run table {start, length, camera} and the short tail's start.
+template <typename T>
+__global__ void k_long_place(const uint32_t* __restrict__ obs_key, const T* __restrict__ obs_uv,
+                             const uint32_t* __restrict__ obs_user, const uint32_t* __restrict__ tile_off,
+                             const uint32_t* __restrict__ long_off, const uint32_t* __restrict__ long_obs, int n_tiles,
+                             uint32_t* tmp_key, T* tmp_uv, uint32_t* tmp_user, uint32_t* long_run,
+                             uint32_t* short_start) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_tiles; t += warps) {
+        const uint32_t lo = tile_off[t], hi = tile_off[t + 1];
+        uint32_t next_long = lo, next_short = lo + long_obs[t], e = long_off[t];
+        for_each_run(obs_key, lo, hi, [&](uint32_t start, uint32_t len) {
+            uint32_t dest;
+            if (len >= (uint32_t)LONG_RUN) {
+                dest = next_long;
+                next_long += len;
+                if (lane == 0) {
+                    long_run[3 * (size_t)e] = dest;
+                    long_run[3 * (size_t)e + 1] = len;
+                    long_run[3 * (size_t)e + 2] = obs_key[start] >> 8;
+                }
+                ++e;
+            } else {
+                dest = next_short;
+                next_short += len;
+            }
+            for (uint32_t i = lane; i < len; i += 32) {
+                tmp_key[dest + i] = obs_key[start + i];
+                tmp_user[dest + i] = obs_user[start + i];
+                tmp_uv[2 * (size_t)(dest + i)] = obs_uv[2 * (size_t)(start + i)];
+                tmp_uv[2 * (size_t)(dest + i) + 1] = obs_uv[2 * (size_t)(start + i) + 1];
+            }
+        });
+        if (lane == 0) short_start[t] = lo + long_obs[t];
+    }
+}
+
+template <typename T>
+__global__ void k_copy_back(const uint32_t* tmp_key, const T* tmp_uv, const uint32_t* tmp_user, int64_t n_obs,
+                            uint32_t* obs_key, T* obs_uv, uint32_t* obs_user) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_obs; j += (int64_t)gridDim.x * blockDim.x) {
+        obs_key[j] = tmp_key[j];
+        obs_user[j] = tmp_user[j];
+        obs_uv[2 * j] = tmp_uv[2 * j];
+        obs_uv[2 * j + 1] = tmp_uv[2 * j + 1];
+    }
 }
 
 __global__ void k_pm_finish(const uint64_t* keys, int64_t n_obs, int n_pts, uint32_t* obs_pm, uint32_t* pt_obs_off) {
@@ -257,9 +349,26 @@ void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s) {
                                                            const_cast<uint32_t*>(v.obs_key),
                                                            const_cast<T*>(v.obs_uv),
                                                            const_cast<uint32_t*>(v.obs_user));
-    // 4. point-major index over the tile-major order (every point has >= 2 observations,
+    // 4. long runs first inside every tile, and the long-run table
+    {
+        uint32_t* n_long = b.tile_cnt;            // [n_tiles + 1] scratch (the tile counts are done)
+        uint32_t* long_obs = b.vals;               // [n_tiles] scratch (the sort values are consumed)
+        uint32_t* tmp_key = reinterpret_cast<uint32_t*>(b.keys);     // the sort scratch is free here
+        uint32_t* tmp_user = tmp_key + v.n_obs;
+        T* tmp_uv = reinterpret_cast<T*>(const_cast<double*>(b.pixels));   // the uploaded pixels are consumed
+        k_long_count<<<blocks_for(32 * (size_t)v.n_tiles, TB), TB, 0, s>>>(v.obs_key, tile_off, v.n_tiles, n_long,
+                                                                            long_obs);
+        k_scan_single<<<1, 1024, 0, s>>>(n_long, v.n_tiles, const_cast<uint32_t*>(v.long_off));
+        k_long_place<T><<<blocks_for(32 * (size_t)v.n_tiles, TB), TB, 0, s>>>(
+            v.obs_key, v.obs_uv, v.obs_user, tile_off, v.long_off, long_obs, v.n_tiles, tmp_key, tmp_uv, tmp_user,
+            const_cast<uint32_t*>(v.long_run), const_cast<uint32_t*>(v.short_start));
+        k_copy_back<T><<<blocks_for(v.n_obs, TB), TB, 0, s>>>(tmp_key, tmp_uv, tmp_user, v.n_obs,
+                                                              const_cast<uint32_t*>(v.obs_key), const_cast<T*>(v.obs_uv),
+                                                              const_cast<uint32_t*>(v.obs_user));
+    }
+    // 5. point-major index over the tile-major order (every point has >= 2 observations,
     //    so every internal point owns a non-empty run)
-    k_pm_keys<<<blocks_for(no2, TB), TB, 0, s>>>(b.vals, b.pt_idx, pt_internal, v.n_obs, no2, b.keys);
+    k_pm_keys<<<blocks_for(no2, TB), TB, 0, s>>>(v.obs_user, b.pt_idx, pt_internal, v.n_obs, no2, b.keys);
     bitonic_sort(b.keys, b.vals, no2, s);
     k_pm_finish<<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.keys, v.n_obs, v.n_pts, const_cast<uint32_t*>(v.obs_pm),
                                                         const_cast<uint32_t*>(v.pt_obs_off));

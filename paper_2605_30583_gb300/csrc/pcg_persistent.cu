@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
         const float* pc_old = v.pc + (size_t)(k & 1) * v.pc_stride;
         float* pc_new = v.pc + (size_t)((k & 1) ^ 1) * v.pc_stride;
         // ------------------------------------------------------------ phase A
-        float pdp = 0.0f, jp2 = 0.0f;
+        float pdp = 0.0f, pdpc = 0.0f, jp2 = 0.0f, jp2c = 0.0f;   // Kahan pairs
         // direction records of this CTA's cameras: p_c = z_c + beta p_prev_c, phi = J_l p_w
         // (global loads first, so their latency overlaps the point loop below)
         for (uint32_t i = tid; i < ncb; i += TB) {
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
             const float zc = __ldcg(v.z + e);
             const float pk = beta != 0.0f ? fmaf(beta, __ldcg(pc_old + e), zc) : zc;
             pc_new[e] = pk;
-            pdp = fmaf(__ldg(v.D + e) * pk, pk, pdp);
+            kahan_add(pdp, pdpc, __ldg(v.D + e) * pk * pk);
         }
         for (int i = tid; i < np; i += TB) {
             const float4 po = sP4[i];
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
             sQ[3 * i] = 0.0f;
             sQ[3 * i + 1] = 0.0f;
             sQ[3 * i + 2] = 0.0f;
-            pdp = fmaf(sD[3 * i] * p0, p0, fmaf(sD[3 * i + 1] * p1, p1, fmaf(sD[3 * i + 2] * p2, p2, pdp)));
+            kahan_add(pdp, pdpc, fmaf(sD[3 * i] * p0, p0, fmaf(sD[3 * i + 1] * p1, p1, sD[3 * i + 2] * p2 * p2)));
         }
         __syncthreads();
         {
@@ -305,19 +305,20 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                     }
                     const float4 xp = sX4[lp], pp = sP4[lp];
                     const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
-                    if (weighted) jp2 += obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * lp, __ldg(v.obs_w + ob + j));
-                    else jp2 += obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * lp);
+                    kahan_add(jp2, jp2c, weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * lp,
+                                                                     __ldg(v.obs_w + ob + j))
+                                                  : obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * lp));
                 }
             }
             // every lane of the warp reaches this one collective
             const bool head = seg_reduce<9>(cur, acc);
             if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)sCid[cur] * CA_STRIDE, acc);
         }
-        if (v.n_fac > 0) jp2 += factor_pass(v, sCid, ncb, sDir, v.cam_acc, (int)gridDim.x * TB);
+        if (v.n_fac > 0) kahan_add(jp2, jp2c, factor_pass(v, sCid, ncb, sDir, v.cam_acc, (int)gridDim.x * TB));
         double sj, sp;
         {
             double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
-            block_sum2(jp2, pdp, red, mine[0], mine[1]);
+            block_sum2c(jp2, jp2c, pdp, pdpc, red, mine[0], mine[1]);
             if (!exchange(st, pslots, ++epoch, mine, tot, shx)) { ok = false; break; }
             sj = tot[0];
             sp = tot[1];
@@ -330,7 +331,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
         }
         alpha = rz / denom;
         const float af = (float)alpha;
-        float lrz = 0.0f, lrr = 0.0f;
+        float lrz = 0.0f, lrzc = 0.0f, lrr = 0.0f, lrrc = 0.0f;   // Kahan pairs
         // points: all of it in shared memory
         auto update_points = [&]() {
             for (int i = tid; i < np; i += TB) {
@@ -350,8 +351,8 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                 const float z1 = fmaf(m[1], r3[0], fmaf(m[3], r3[1], m[4] * r3[2]));
                 const float z2 = fmaf(m[2], r3[0], fmaf(m[4], r3[1], m[5] * r3[2]));
                 sZ[e] = z0; sZ[e + 1] = z1; sZ[e + 2] = z2;
-                lrz = fmaf(r3[0], z0, fmaf(r3[1], z1, fmaf(r3[2], z2, lrz)));
-                lrr = fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], fmaf(r3[2], r3[2], lrr)));
+                kahan_add(lrz, lrzc, fmaf(r3[0], z0, fmaf(r3[1], z1, r3[2] * z2)));
+                kahan_add(lrr, lrrc, fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], r3[2] * r3[2])));
             }
         };
         if (n_own <= CAMS_PER_PASS) {
@@ -393,8 +394,8 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
 #pragma unroll
                 for (int q = 0; q < 9; ++q) z = fmaf(__ldg(M + q), rr9[q], z);
                 v.z[e] = z;
-                lrz = fmaf(ri, z, lrz);
-                lrr = fmaf(ri, ri, lrr);
+                kahan_add(lrz, lrzc, ri * z);
+                kahan_add(lrr, lrrc, ri * ri);
                 v.cam_acc[(size_t)c * CA_STRIDE + i] = 0.0f;
             }
         } else {
@@ -431,8 +432,8 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
 #pragma unroll
                     for (int q = 0; q < 9; ++q) z = fmaf(__ldg(M + q), rr9[q], z);
                     v.z[e] = z;
-                    lrz = fmaf(ri, z, lrz);
-                    lrr = fmaf(ri, ri, lrr);
+                    kahan_add(lrz, lrzc, ri * z);
+                    kahan_add(lrr, lrrc, ri * ri);
                     v.cam_acc[(size_t)c * CA_STRIDE + i] = 0.0f;
                 }
                 __syncthreads();
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
         double rzn, rrn;
         {
             double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
-            block_sum2(lrz, lrr, red, mine[0], mine[1]);
+            block_sum2c(lrz, lrzc, lrr, lrrc, red, mine[0], mine[1]);
             if (!exchange(st, pslots, ++epoch, mine, tot, shx)) { ok = false; break; }
             rzn = tot[0];
             rrn = tot[1];
@@ -496,16 +497,16 @@ __device__ __forceinline__ void camera_dirs(const Views<float>& v, const uint32_
     }
 }
 
-// Warp sums of the update's three partials into red[3 * warp + k] (FP32 in the warp).
-__device__ __forceinline__ void warp_partials3(float a, float b, float c, double* red) {
-    a = warp_sumf(a);
-    b = warp_sumf(b);
-    c = warp_sumf(c);
+// Warp sums of the update's three compensated partials (Kahan pairs s - c) into
+// red[3 * warp + k]: compensated FP32 pairs inside the warp (warp_sum_pair).
+__device__ __forceinline__ void warp_partials3(float a, float ac, float b, float bc, float c, float cc,
+                                               double* red) {
+    const double sa = warp_sum_pair(a, -ac), sb = warp_sum_pair(b, -bc), sc = warp_sum_pair(c, -cc);
     if ((threadIdx.x & 31) == 0) {
         const int w = threadIdx.x >> 5;
-        red[3 * w] = (double)a;
-        red[3 * w + 1] = (double)b;
-        red[3 * w + 2] = (double)c;
+        red[3 * w] = sa;
+        red[3 * w + 1] = sb;
+        red[3 * w + 2] = sc;
     }
 }
 
@@ -562,7 +563,8 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         sOwn[w] = m;
     }
     for (uint32_t i = tid; i < no; i += TB) skey[i] = __ldg(v.obs_key + ob + i);
-    float lg = 0.0f, lr = 0.0f, lu = 0.0f;   // partials of r^T u, |r|^2, u^T D u
+    // partials of r^T u, |r|^2, u^T D u (Kahan pairs)
+    float lg = 0.0f, lr = 0.0f, lu = 0.0f, lgc = 0.0f, lrc = 0.0f, luc = 0.0f;
     for (int i = tid; i < np; i += TB) {
         const size_t e = g0 + 3 * (size_t)i;
         const float D0 = v.D[e], D1 = v.D[e + 1], D2 = v.D[e + 2];
@@ -572,9 +574,9 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         sU4[i] = make_float4(u0, u1, u2, D1);
         sD2[i] = D2;
         sR[3 * i] = r0; sR[3 * i + 1] = r1; sR[3 * i + 2] = r2;
-        lg = fmaf(r0, u0, fmaf(r1, u1, fmaf(r2, u2, lg)));
-        lr = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, lr)));
-        lu = fmaf(D0 * u0, u0, fmaf(D1 * u1, u1, fmaf(D2 * u2, u2, lu)));
+        kahan_add(lg, lgc, fmaf(r0, u0, fmaf(r1, u1, r2 * u2)));
+        kahan_add(lr, lrc, fmaf(r0, r0, fmaf(r1, r1, r2 * r2)));
+        kahan_add(lu, luc, fmaf(D0 * u0, u0, fmaf(D1 * u1, u1, D2 * u2 * u2)));
     }
     for (int i = tid; i < n3p; i += TB) {
         sP[i] = 0.0f;
@@ -601,12 +603,12 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         sCs[e] = 0.0f;
         sCh[e] = 0.0f;
         if (owns(sOwn, lc)) {
-            lg = fmaf(r, u, lg);
-            lr = fmaf(r, r, lr);
-            lu = fmaf(__ldg(v.D + ge) * u, u, lu);
+            kahan_add(lg, lgc, r * u);
+            kahan_add(lr, lrc, r * r);
+            kahan_add(lu, luc, __ldg(v.D + ge) * u * u);
         }
     }
-    warp_partials3(lg, lr, lu, red_u);
+    warp_partials3(lg, lgc, lr, lrc, lu, luc, red_u);
     __syncthreads();   // camera u
     camera_dirs<TB>(v, sCid, sCu, sDir, ne);
     __syncthreads();
@@ -639,7 +641,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
     while (k < max_pcg) {
         float* cacc = v.cam_acc + (size_t)(k % CA_SETS) * cas;
         // ------------------------------------------------------------ M: w = A u
-        float jj = 0.0f;
+        float jj = 0.0f, jjc = 0.0f;   // Kahan pair
         {
             uint32_t cur = NO_CAM;
             float acc[9];
@@ -677,17 +679,18 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
                     }
                     const float4 xp = sX4[lp], up = sU4[lp];
                     const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {up.x, up.y, up.z};
-                    if (weighted) jj += obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * lp, __ldg(v.obs_w + ob + j));
-                    else jj += obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * lp);
+                    kahan_add(jj, jjc, weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * lp,
+                                                                   __ldg(v.obs_w + ob + j))
+                                                : obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * lp));
                 }
             }
             // every lane of the warp reaches this one collective
             const bool head = seg_reduce<9>(cur, acc);
             if (head && cur != NO_CAM) flush_matvec(cacc + (size_t)sCid[cur] * CA_STRIDE, acc);
         }
-        if (v.n_fac > 0) jj += factor_pass(v, sCid, ncb, sDir, cacc, (int)gridDim.x * TB);
-        jj = warp_sumf(jj);
-        if ((tid & 31) == 0) red_m[tid >> 5] = (double)jj;
+        if (v.n_fac > 0) kahan_add(jj, jjc, factor_pass(v, sCid, ncb, sDir, cacc, (int)gridDim.x * TB));
+        const double jw = warp_sum_pair(jj, -jjc);
+        if ((tid & 31) == 0) red_m[tid >> 5] = jw;
         __syncthreads();
         // ------------------------------------------------------------ X: exchange
         double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
@@ -716,7 +719,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         beta = (float)b_k;
         const float af = (float)alpha;
         // ------------------------------------------------------------ U: update
-        lg = lr = lu = 0.0f;
+        lg = lr = lu = lgc = lrc = luc = 0.0f;
         // cameras, step 1: w from the assembled sums, then p, s, h, r
         for (int e = tid; e < ne; e += TB) {
             const int lc = e / 9, i = e - 9 * lc;
@@ -763,9 +766,9 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
             const float z1 = fmaf(m[1], r3[0], fmaf(m[3], r3[1], m[4] * r3[2]));
             const float z2 = fmaf(m[2], r3[0], fmaf(m[4], r3[1], m[5] * r3[2]));
             sU4[i] = make_float4(z0, z1, z2, u4.w);
-            lg = fmaf(r3[0], z0, fmaf(r3[1], z1, fmaf(r3[2], z2, lg)));
-            lr = fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], fmaf(r3[2], r3[2], lr)));
-            lu = fmaf(Dq[0] * z0, z0, fmaf(Dq[1] * z1, z1, fmaf(Dq[2] * z2, z2, lu)));
+            kahan_add(lg, lgc, fmaf(r3[0], z0, fmaf(r3[1], z1, r3[2] * z2)));
+            kahan_add(lr, lrc, fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], r3[2] * r3[2])));
+            kahan_add(lu, luc, fmaf(Dq[0] * z0, z0, fmaf(Dq[1] * z1, z1, Dq[2] * z2 * z2)));
         }
         __syncthreads();   // camera r
         // cameras, step 2: u = M^-1 r; the owner adds the partials and clears the
@@ -784,14 +787,14 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
                 sCu[e] = z;
                 if (owns(sOwn, lc)) {
                     const float ri = r9[i];
-                    lg = fmaf(ri, z, lg);
-                    lr = fmaf(ri, ri, lr);
-                    lu = fmaf(__ldg(v.D + 9 * (size_t)c + i) * z, z, lu);
+                    kahan_add(lg, lgc, ri * z);
+                    kahan_add(lr, lrc, ri * ri);
+                    kahan_add(lu, luc, __ldg(v.D + 9 * (size_t)c + i) * z * z);
                     clear[(size_t)c * CA_STRIDE + i] = 0.0f;
                 }
             }
         }
-        warp_partials3(lg, lr, lu, red_u);
+        warp_partials3(lg, lgc, lr, lrc, lu, luc, red_u);
         __syncthreads();   // camera u
         camera_dirs<TB>(v, sCid, sCu, sDir, ne);
         __syncthreads();

@@ -26,6 +26,7 @@ struct Layout {
     size_t state, partials, obs_key, obs_uv, obs_user, tile_off, pt_user, pt_internal, obs_pm, pt_obs_off;
     size_t vec[9];                       // x, x_new, h, r, z, p, q, g, D
     size_t blk_tile, blk_cam_off, blk_cams, pslots;
+    size_t long_off, long_run, short_start;
     size_t cam_pre, cam_pre_new, cam_dir, cam_acc, pc, cam_lin, cam_H, cam64, cam64_new, cam_H64, pt_H, Minv_c, Minv_p, jac, res, obs_w,
         staging;
     size_t fac_cam, fac_meas, fac_sqrt, fac_J;
@@ -78,6 +79,7 @@ struct ba_problem {
     uint32_t* blk_cam_off = nullptr;   // device, [p_grid + 1]: per-CTA camera list offsets
     uint32_t* blk_cams = nullptr;      // device, the lists (inside the ordering region of the workspace)
     double* pslots = nullptr;       // device, [PSLOT_TOTAL]
+
 };
 
 namespace gbba {

@@ -1,0 +1,574 @@
+// Tile kernels of the mixed-precision form: the damped normal operator of the
+// separate-kernel PCG, the linearisation and the candidate evaluation.
+//
+// Work decomposition.  A tile is TILE_PTS consecutive points (locality order) and all
+// their observations.  Inside a tile each camera's observations form one run, and the
+// runs of at least LONG_RUN observations come first (order.cu); on the large workloads
+// they hold over 90 % of the observations.  A CTA stages in shared memory, in one round
+// trip, the tile's points, its observation keys (and pixels where needed) and its table
+// of long runs {start, length, camera}; then
+//   * its warps take the long runs in turn and walk each in camera-uniform steps of 32
+//     consecutive observations: the camera sits in registers for the whole run, and the
+//     run's camera sums stay in per-lane
+//     registers until the run ends, when one recursive-halving warp reduction
+//     (warp_split_sum) hands each lane complete sums to add to the global camera
+//     accumulators;
+//   * its threads split the short runs that follow into contiguous chunks; a thread
+//     reads a camera through L1 when its chunk enters the camera's run and adds its
+//     camera sums to the global accumulators when it leaves it.
+// Point sums go into shared memory (the tile owns its points) and are written once per
+// tile.  This is our counterpart of the paper's Shared Read / Shared Add accessors
+// (Sec. IV-A).
+//
+// Per-thread sums that feed FP64 reductions (|J p|^2, p^T D p, the cost) are kept in
+// FP32 with Kahan's compensated summation, summed inside each warp in compensated FP32
+// pairs and across warps and CTAs in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+#include "kernels.h"
+#include "mixed_common.cuh"
+
+namespace gbba {
+
+namespace {
+
+struct TileRange {
+    uint32_t lo, hi, l0, nl, ss;   // observations [lo, hi), long runs [l0, l0 + nl), short tail from ss
+    int pt0, npt;
+    size_t base;                   // the tile's first point entry in parameter vectors
+};
+
+__device__ __forceinline__ TileRange tile_range(const Views<float>& v, int tile) {
+    TileRange r;
+    r.lo = v.tile_off[tile];
+    r.hi = v.tile_off[tile + 1];
+    r.l0 = v.long_off[tile];
+    r.nl = v.long_off[tile + 1] - r.l0;
+    r.ss = v.short_start[tile];
+    r.pt0 = tile * TILE_PTS;
+    r.npt = min(TILE_PTS, v.n_pts - r.pt0);
+    r.base = v.pt_off + 3 * (size_t)r.pt0;
+    return r;
+}
+
+// The tile's observation keys (and pixels) and long-run table into shared memory:
+// sKey[i] / sUV[i] of observation lo + i, sRun[3 r + k] of long run l0 + r.
+template <int TB, bool UV>
+__device__ __forceinline__ void stage_obs(const Views<float>& v, const TileRange& T, uint32_t* sKey, float2* sUV,
+                                          uint32_t* sRun) {
+    const uint32_t n = T.hi - T.lo;
+    for (uint32_t i = threadIdx.x; i < n; i += TB) {
+        sKey[i] = __ldg(v.obs_key + T.lo + i);
+        if (UV) sUV[i] = __ldg(reinterpret_cast<const float2*>(v.obs_uv) + T.lo + i);
+    }
+    for (uint32_t i = threadIdx.x; i < 3 * T.nl; i += TB) sRun[i] = __ldg(v.long_run + 3 * (size_t)T.l0 + i);
+}
+
+// Block sums of compensated per-thread partials (Kahan pairs s - c): FP32 pairs inside
+// each warp, FP64 across the warps; valid in thread 0.  `sh` holds 2 * (TB / 32) doubles.
+template <int TB>
+__device__ __forceinline__ void block_pair_sums(float sa, float ca, float sb, float cb, double* sh, double& ra,
+                                                double& rb) {
+    block_sum2c(sa, ca, sb, cb, sh, ra, rb);
+}
+
+// ------------------------------------------------------------------ normal operator ---
+// q = J^T W J p + mu D p for the tile's points (written), camera parts J^T W J p into the
+// camera accumulators (k_update adds mu D p and applies J_l^T), |J p|^2 and the points'
+// p^T D p into the slot sums (the cameras' p^T D p comes from k_cam_direction).  The
+// points' direction step p = zs + beta p_prev is fused into the staging.  One CTA per
+// tile.
+
+template <int TB>
+__global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_t* gate, const float* zs,
+                                                    int use_beta, int key_cap) {
+    if (gated_off(gate)) return;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);   // [key_cap]
+    uint32_t* sRun = sKey + key_cap;                     // [3 key_cap / LONG_RUN]
+    __shared__ float4 sX4[TILE_PTS], sP4[TILE_PTS];
+    __shared__ float sQ[3 * TILE_PTS];
+    __shared__ unsigned int s_next;
+    __shared__ double red[2 * (TB / 32)];
+    DevState* st = v.st;
+    const float beta = use_beta ? (float)st->beta : 0.0f;
+    const float mu = (float)st->mu;
+    const float eps = (float)st->opt.eps;
+    const bool weighted = st->opt.loss != 0;
+    const int lane = threadIdx.x & 31;
+    const TileRange T = tile_range(v, blockIdx.x);
+    float jp_s = 0.0f, jp_c = 0.0f, pd_s = 0.0f, pd_c = 0.0f;
+    {
+        float* sPf = reinterpret_cast<float*>(sP4);
+        float* sXf = reinterpret_cast<float*>(sX4);
+        for (int i = threadIdx.x; i < 3 * T.npt; i += TB) {
+            const float z = zs[T.base + i];
+            const float pn = beta != 0.0f ? fmaf(beta, v.p[T.base + i], z) : z;
+            v.p[T.base + i] = pn;
+            const float d = v.D[T.base + i];
+            const int slot = i / 3, k = i - 3 * slot;
+            sPf[4 * slot + k] = pn;
+            sXf[4 * slot + k] = v.x[T.base + i];
+            sQ[i] = mu * d * pn;
+            kahan_add(pd_s, pd_c, d * pn * pn);
+        }
+    }
+    stage_obs<TB, false>(v, T, sKey, nullptr, sRun);
+    if (threadIdx.x == 0) s_next = 0u;
+    __syncthreads();
+    // long runs: camera-uniform steps of 32 observations
+    for (;;) {
+        unsigned int r = 0;
+        if (lane == 0) r = atomicAdd(&s_next, 1u);
+        r = __shfl_sync(FULL, r, 0);
+        if (r >= T.nl) break;
+        const uint32_t start = sRun[3 * r] - T.lo, len = sRun[3 * r + 1], c = sRun[3 * r + 2];
+        const Cam cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+        float dir[9];
+        load_dir(v.cam_dir + (size_t)c * CD_STRIDE, dir);
+        float acc[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+        for (uint32_t off = lane; off < len; off += 32) {
+            const uint32_t j = T.lo + start + off;
+            const uint32_t slot = sKey[start + off] & 0xffu;
+            const float4 xp = sX4[slot], pp = sP4[slot];
+            const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
+            const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * slot, __ldg(v.obs_w + j))
+                                      : obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * slot);
+            kahan_add(jp_s, jp_c, tt);
+        }
+        int idx;
+        const int nv = warp_split_sum<9>(acc, lane, idx);
+        if (nv > 0) atomicAdd(v.cam_acc + (size_t)c * CA_STRIDE + idx, acc[0]);
+    }
+    // short runs: one contiguous chunk per thread
+    {
+        const uint32_t n = T.hi - T.ss;
+        const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
+        const uint32_t a = T.ss + min(threadIdx.x * chunk, n), b = T.ss + min(threadIdx.x * chunk + chunk, n);
+        uint32_t cur = NO_CAM;
+        float acc[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+        Cam cam;
+        float dir[9];
+        for (uint32_t j = a; j < b; ++j) {
+            const uint32_t key = sKey[j - T.lo];
+            const uint32_t c = key >> 8, slot = key & 0xffu;
+            if (c != cur) {
+                if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
+                cur = c;
+                cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+                load_dir(v.cam_dir + (size_t)c * CD_STRIDE, dir);
+            }
+            const float4 xp = sX4[slot], pp = sP4[slot];
+            const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
+            const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * slot, __ldg(v.obs_w + j))
+                                      : obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * slot);
+            kahan_add(jp_s, jp_c, tt);
+        }
+        if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * T.npt; i += TB) v.q[T.base + i] = sQ[i];
+    double bj, bp;
+    block_pair_sums<TB>(jp_s, jp_c, pd_s, pd_c, red, bj, bp);
+    if (threadIdx.x == 0) {
+        slot_add(st->acc_mv, 0, bj);
+        slot_add(st->acc_mv, 1, bp);
+    }
+}
+
+constexpr int TN_TB = 128;
+
+// ---------------------------------------------------------------- linearisation ---
+// Linearisation (fused score + Jacobian products, Sec. V-A): cost F = 1/2 sum rho(|r|^2),
+// g = J^T W r and the diagonal blocks J_c^T W J_c, J_p^T W J_p.  `mode` as k_linearize:
+// 0 first linearisation of a solve, 1 relinearisation after an accepted step (gated by
+// st->relin), 2 evaluation only (squared loss; optional r and J in the caller's order).
+constexpr int TL_ACC = 9 + 45;   // per-lane camera sums: g, upper triangle of J_c^T J_c
+constexpr int TL_TB = 128;
+
+struct LinObs {
+    float r0, r1, j0[9], j1[9], jx0[3], jx1[3];
+};
+
+// Residual and Jacobian rows of one observation (J_w[:,k] = A (J_l[:,k] x RX)).
+__device__ __forceinline__ LinObs lin_obs(const Cam& cam, const float (&JL)[9], float4 X, float u0, float u1,
+                                          float eps) {
+    LinObs o;
+    const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
+    const float fs = cam.f * g.s;
+    o.r0 = fmaf(fs, g.p[0], -u0);
+    o.r1 = fmaf(fs, g.p[1], -u1);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float w0 = JL[k], w1 = JL[3 + k], w2 = JL[6 + k];
+        const float c0 = fmaf(w1, g.RX[2], -w2 * g.RX[1]);
+        const float c1 = fmaf(w2, g.RX[0], -w0 * g.RX[2]);
+        const float c2 = fmaf(w0, g.RX[1], -w1 * g.RX[0]);
+        o.j0[k] = fmaf(g.A[0], c0, fmaf(g.A[1], c1, g.A[2] * c2));
+        o.j1[k] = fmaf(g.A[3], c0, fmaf(g.A[4], c1, g.A[5] * c2));
+        o.j0[3 + k] = g.A[k];
+        o.j1[3 + k] = g.A[3 + k];
+    }
+    const float fn2 = cam.f * g.n2;
+    o.j0[6] = g.s * g.p[0]; o.j0[7] = fn2 * g.p[0]; o.j0[8] = fn2 * g.n2 * g.p[0];
+    o.j1[6] = g.s * g.p[1]; o.j1[7] = fn2 * g.p[1]; o.j1[8] = fn2 * g.n2 * g.p[1];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        o.jx0[q] = fmaf(g.A[0], cam.R[q], fmaf(g.A[1], cam.R[3 + q], g.A[2] * cam.R[6 + q]));
+        o.jx1[q] = fmaf(g.A[3], cam.R[q], fmaf(g.A[4], cam.R[3 + q], g.A[5] * cam.R[6 + q]));
+    }
+    return o;
+}
+
+// Everything one observation adds: evaluation outputs (mode 2), the IRLS weight, the cost,
+// the camera sums (registers) and the point sums (shared memory).
+__device__ __forceinline__ void lin_accumulate(const Views<float>& v, LinObs& o, uint32_t j, uint32_t slot, int mode,
+                                               int loss, float lscale, float* res_out, float* jac_out,
+                                               float (&acc)[TL_ACC], float* sG, float* sH, float& cs, float& cc) {
+    if (mode == 2) {   // evaluation output: the unweighted residual and Jacobian
+        const uint32_t u = v.obs_user[j];
+        if (res_out) { res_out[2 * (size_t)u] = o.r0; res_out[2 * (size_t)u + 1] = o.r1; }
+        if (jac_out) {
+            float* Jo = jac_out + 24 * (size_t)u;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) { Jo[k] = o.j0[k]; Jo[12 + k] = o.j1[k]; }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { Jo[9 + q] = o.jx0[q]; Jo[21 + q] = o.jx1[q]; }
+        }
+    }
+    const float s2 = fmaf(o.r0, o.r0, o.r1 * o.r1);
+    if (loss) {   // IRLS weight w = rho'(|r|^2): rows scaled by sqrt(w)
+        const float w = loss_weight(s2, loss, lscale);
+        if (mode != 2) v.obs_w[j] = w;
+        kahan_add(cs, cc, loss_rho(s2, loss, lscale));
+        const float sw = sqrtf(w);
+        o.r0 *= sw;
+        o.r1 *= sw;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { o.j0[k] *= sw; o.j1[k] *= sw; }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { o.jx0[q] *= sw; o.jx1[q] *= sw; }
+    } else {
+        kahan_add(cs, cc, s2);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc[i] = fmaf(o.j0[i], o.r0, fmaf(o.j1[i], o.r1, acc[i]));
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int k = i; k < 9; ++k) {
+            const int t = 9 + tri_index(9, i, k);
+            acc[t] = fmaf(o.j0[i], o.j0[k], fmaf(o.j1[i], o.j1[k], acc[t]));
+        }
+    float* gq = sG + 3 * slot;
+    float* hq = sH + 6 * slot;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) atomicAdd(gq + q, fmaf(o.jx0[q], o.r0, o.jx1[q] * o.r1));
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+        for (int b2 = a2; b2 < 3; ++b2)
+            atomicAdd(hq + tri_index(3, a2, b2), fmaf(o.jx0[a2], o.jx0[b2], o.jx1[a2] * o.jx1[b2]));
+}
+
+__device__ __forceinline__ void load_jl(const float* __restrict__ rec, float (&JL)[9]) {
+    const float4* j4 = reinterpret_cast<const float4*>(rec + CP_JL);
+    const float4 a = __ldg(j4), b = __ldg(j4 + 1), c = __ldg(j4 + 2);
+    JL[0] = a.x; JL[1] = a.y; JL[2] = a.z; JL[3] = a.w;
+    JL[4] = b.x; JL[5] = b.y; JL[6] = b.z; JL[7] = b.w; JL[8] = c.x;
+}
+
+// A thread's camera sums of one run into the global accumulators (g in FP64, the
+// J_c^T J_c triangle as float4 atomics), then cleared.
+__device__ __forceinline__ void flush_lin_global(const Views<float>& v, uint32_t c, float (&a)[TL_ACC]) {
+    double* g = v.cam_lin + (size_t)c * CL_STRIDE;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) atomicAdd(g + k, (double)a[k]);
+    float4* h = reinterpret_cast<float4*>(v.cam_H + (size_t)c * CH_STRIDE);
+#pragma unroll
+    for (int k = 0; k < 11; ++k)
+        atomicAdd(h + k, make_float4(a[9 + 4 * k], a[10 + 4 * k], a[11 + 4 * k], a[12 + 4 * k]));
+    atomicAdd(v.cam_H + (size_t)c * CH_STRIDE + 44, a[53]);
+#pragma unroll
+    for (int k = 0; k < TL_ACC; ++k) a[k] = 0.0f;
+}
+
+template <int TB>
+__global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mode, float* res_out, float* jac_out,
+                                                       CondHandle lm_cond, int use_cond, int key_cap) {
+    if (mode == 1 && v.st->relin == 0) return;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);             // [key_cap]
+    float2* sUV = reinterpret_cast<float2*>(sKey + key_cap);       // [key_cap]
+    uint32_t* sRun = reinterpret_cast<uint32_t*>(sUV + key_cap);   // [3 key_cap / LONG_RUN]
+    __shared__ float4 sX4[TILE_PTS];
+    __shared__ float sG[3 * TILE_PTS], sH[PH_STRIDE * TILE_PTS];   // J_p^T W r, J_p^T W J_p (upper)
+    __shared__ unsigned int s_next;
+    const float eps = (float)v.st->opt.eps;
+    // robust loss (evaluation, mode 2, is always the squared loss)
+    const int loss = mode == 2 ? 0 : v.st->opt.loss;
+    const float lscale = (float)v.st->opt.loss_scale;
+    const int lane = threadIdx.x & 31;
+    float cs = 0.0f, cc = 0.0f;   // compensated cost
+    for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
+        const TileRange T = tile_range(v, tile);
+        for (int i = threadIdx.x; i < T.npt; i += TB)
+            sX4[i] = make_float4(v.x[T.base + 3 * i], v.x[T.base + 3 * i + 1], v.x[T.base + 3 * i + 2], 0.0f);
+        for (int i = threadIdx.x; i < 3 * TILE_PTS; i += TB) sG[i] = 0.0f;
+        for (int i = threadIdx.x; i < PH_STRIDE * TILE_PTS; i += TB) sH[i] = 0.0f;
+        stage_obs<TB, true>(v, T, sKey, sUV, sRun);
+        if (threadIdx.x == 0) s_next = 0u;
+        __syncthreads();
+        // long runs: camera-uniform steps of 32 observations
+        for (;;) {
+            unsigned int r = 0;
+            if (lane == 0) r = atomicAdd(&s_next, 1u);
+            r = __shfl_sync(FULL, r, 0);
+            if (r >= T.nl) break;
+            const uint32_t start = sRun[3 * r] - T.lo, len = sRun[3 * r + 1], c = sRun[3 * r + 2];
+            const float* rec = v.cam_pre + (size_t)c * CP_STRIDE;
+            const Cam cam = load_cam(rec);
+            float JL[9];
+            load_jl(rec, JL);
+            float acc[TL_ACC];
+#pragma unroll
+            for (int k = 0; k < TL_ACC; ++k) acc[k] = 0.0f;
+            for (uint32_t off = lane; off < len; off += 32) {
+                const uint32_t i = start + off, j = T.lo + i;
+                const uint32_t slot = sKey[i] & 0xffu;
+                const float2 uv = sUV[i];
+                LinObs o = lin_obs(cam, JL, sX4[slot], uv.x, uv.y, eps);
+                lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sG, sH, cs, cc);
+            }
+            int idx;
+            const int nv = warp_split_sum<TL_ACC>(acc, lane, idx);
+#pragma unroll
+            for (int k = 0; k < split_sum_slots(TL_ACC); ++k) {
+                const int i = idx + k;
+                if (k < nv) {
+                    if (i < 9) atomicAdd(v.cam_lin + (size_t)c * CL_STRIDE + CL_G + i, (double)acc[k]);
+                    else atomicAdd(v.cam_H + (size_t)c * CH_STRIDE + (i - 9), acc[k]);
+                }
+            }
+        }
+        // short runs: one contiguous chunk per thread
+        {
+            const uint32_t n = T.hi - T.ss;
+            const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
+            const uint32_t a = T.ss + min(threadIdx.x * chunk, n), b = T.ss + min(threadIdx.x * chunk + chunk, n);
+            uint32_t cur = NO_CAM;
+            float acc[TL_ACC];
+#pragma unroll
+            for (int k = 0; k < TL_ACC; ++k) acc[k] = 0.0f;
+            Cam cam;
+            float JL[9];
+            for (uint32_t j = a; j < b; ++j) {
+                const uint32_t key = sKey[j - T.lo];
+                const uint32_t c = key >> 8, slot = key & 0xffu;
+                if (c != cur) {
+                    if (cur != NO_CAM) flush_lin_global(v, cur, acc);
+                    cur = c;
+                    cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+                    load_jl(v.cam_pre + (size_t)c * CP_STRIDE, JL);
+                }
+                const float2 uv = sUV[j - T.lo];
+                LinObs o = lin_obs(cam, JL, sX4[slot], uv.x, uv.y, eps);
+                lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sG, sH, cs, cc);
+            }
+            if (cur != NO_CAM) flush_lin_global(v, cur, acc);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * T.npt; i += TB) v.g[T.base + i] = sG[i];
+        for (int i = threadIdx.x; i < PH_STRIDE * T.npt; i += TB) v.pt_H[(size_t)T.pt0 * PH_STRIDE + i] = sH[i];
+        __syncthreads();   // the next tile's staging overwrites the shared sums
+    }
+    double in[1] = {(double)cs - (double)cc}, out[1];
+    if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_LIN], out) && threadIdx.x == 0) {
+        DevState* st = v.st;
+        const double F = 0.5 * out[0] + (v.n_fac > 0 ? st->fac_cost : 0.0);   // pose factors: k_factor_linearize
+        st->cost_out = F;
+        if (mode == 0) {
+            st->F = F;
+            st->F0 = F;
+            const bool ok = isfinite(F);
+            if (!ok) st->status = 4;
+            st->lm_active = (ok && F > 0.0 && st->opt.max_lm > 0) ? 1 : 0;
+            if (use_cond) cudaGraphSetConditional(lm_cond, st->lm_active ? 1u : 0u);
+        } else if (mode == 1) {
+            st->F = F;
+        }
+    }
+}
+
+// ------------------------------------------------------------ candidate evaluation ---
+// F' = 1/2 sum rho(|r(x')|^2) and |J(x) h|^2 (weighted at x); the last block applies the
+// LM rule of Sec. V (lm_decide).  Never gated: its last block sets the LM loop flag.
+constexpr int TE_TB = 128;
+
+struct EvalCam {
+    Cam cn, co;   // records at x' and at x
+    float dir[9]; // direction record of h (k_candidate)
+};
+
+__device__ __forceinline__ EvalCam load_eval_cam(const Views<float>& v, uint32_t c) {
+    EvalCam e;
+    e.cn = load_cam(v.cam_pre_new + (size_t)c * CP_STRIDE);
+    e.co = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+    const float4* d4 = reinterpret_cast<const float4*>(v.cam_dir + (size_t)c * CD_STRIDE);
+    const float4 a = __ldcg(d4), b = __ldcg(d4 + 1), cc = __ldcg(d4 + 2);
+    e.dir[0] = a.x; e.dir[1] = a.y; e.dir[2] = a.z; e.dir[3] = a.w;
+    e.dir[4] = b.x; e.dir[5] = b.y; e.dir[6] = b.z; e.dir[7] = b.w; e.dir[8] = cc.x;
+    return e;
+}
+
+__device__ __forceinline__ void eval_obs(const Views<float>& v, const EvalCam& e, const float4* sXn,
+                                         const float4* sXo, const float4* sHp, uint32_t j, uint32_t slot, float2 uv,
+                                         float eps, int loss, float lscale, float& fs_, float& fc_, float& js_,
+                                         float& jc_) {
+    const float4 xn = sXn[slot], xo = sXo[slot], hp = sHp[slot];
+    float r0, r1;
+    project_residual(e.cn, xn.x, xn.y, xn.z, eps, uv.x, uv.y, r0, r1);
+    const Geo g = project_geo(e.co, xo.x, xo.y, xo.z, eps);
+    float t0, t1;
+    jdir(g, e.co, e.dir, hp.x, hp.y, hp.z, t0, t1);
+    if (loss) {   // F' = 1/2 sum rho(|r'|^2); |J h|^2 weighted at x
+        kahan_add(fs_, fc_, loss_rho(fmaf(r0, r0, r1 * r1), loss, lscale));
+        kahan_add(js_, jc_, __ldg(v.obs_w + j) * fmaf(t0, t0, t1 * t1));
+    } else {
+        kahan_add(fs_, fc_, fmaf(r0, r0, r1 * r1));
+        kahan_add(js_, jc_, fmaf(t0, t0, t1 * t1));
+    }
+}
+
+// Four CTAs per SM (at most 128 registers per thread).
+template <int TB>
+__global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle lm_cond, int use_cond, int key_cap) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);             // [key_cap]
+    float2* sUV = reinterpret_cast<float2*>(sKey + key_cap);       // [key_cap]
+    uint32_t* sRun = reinterpret_cast<uint32_t*>(sUV + key_cap);   // [3 key_cap / LONG_RUN]
+    __shared__ float4 sXn[TILE_PTS], sXo[TILE_PTS], sHp[TILE_PTS];   // x', x and h of the tile's points
+    __shared__ unsigned int s_next;
+    DevState* st = v.st;
+    const int active = st->lm_active;
+    const float eps = (float)st->opt.eps;
+    const int loss = st->opt.loss;
+    const float lscale = (float)st->opt.loss_scale;
+    const int lane = threadIdx.x & 31;
+    float fs_ = 0.0f, fc_ = 0.0f, js_ = 0.0f, jc_ = 0.0f;   // compensated F' and |J h|^2
+    for (int tile = blockIdx.x; active && tile < v.n_tiles; tile += gridDim.x) {
+        const TileRange T = tile_range(v, tile);
+        for (int i = threadIdx.x; i < T.npt; i += TB) {
+            const size_t e = T.base + 3 * i;
+            sXn[i] = make_float4(v.x_new[e], v.x_new[e + 1], v.x_new[e + 2], 0.0f);
+            sXo[i] = make_float4(v.x[e], v.x[e + 1], v.x[e + 2], 0.0f);
+            sHp[i] = make_float4(v.h[e], v.h[e + 1], v.h[e + 2], 0.0f);
+        }
+        stage_obs<TB, true>(v, T, sKey, sUV, sRun);
+        if (threadIdx.x == 0) s_next = 0u;
+        __syncthreads();
+        for (;;) {
+            unsigned int r = 0;
+            if (lane == 0) r = atomicAdd(&s_next, 1u);
+            r = __shfl_sync(FULL, r, 0);
+            if (r >= T.nl) break;
+            const uint32_t start = sRun[3 * r] - T.lo, len = sRun[3 * r + 1];
+            const EvalCam e = load_eval_cam(v, sRun[3 * r + 2]);
+            for (uint32_t off = lane; off < len; off += 32) {
+                const uint32_t i = start + off;
+                eval_obs(v, e, sXn, sXo, sHp, T.lo + i, sKey[i] & 0xffu, sUV[i], eps, loss, lscale, fs_, fc_, js_,
+                         jc_);
+            }
+        }
+        {
+            const uint32_t n = T.hi - T.ss;
+            const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
+            const uint32_t a = T.ss + min(threadIdx.x * chunk, n), b = T.ss + min(threadIdx.x * chunk + chunk, n);
+            uint32_t cur = NO_CAM;
+            EvalCam e;
+            for (uint32_t j = a; j < b; ++j) {
+                const uint32_t key = sKey[j - T.lo];
+                const uint32_t c = key >> 8;
+                if (c != cur) {
+                    cur = c;
+                    e = load_eval_cam(v, c);
+                }
+                eval_obs(v, e, sXn, sXo, sHp, j, key & 0xffu, sUV[j - T.lo], eps, loss, lscale, fs_, fc_, js_, jc_);
+            }
+        }
+        __syncthreads();   // the next tile's staging overwrites the points
+    }
+    double in[2] = {(double)fs_ - (double)fc_, (double)js_ - (double)jc_}, out[2];
+    if (grid_reduce<2>(in, v.partials, &st->tickets[TK_COST], out) && threadIdx.x == 0) {
+        // pose factors: k_factor_eval ran just before
+        const bool fac = v.n_fac > 0;
+        lm_decide(st, active, 0.5 * out[0] + (fac ? st->fac_cost_new : 0.0), out[1] + (fac ? st->fac_jh2 : 0.0));
+        if (use_cond) cudaGraphSetConditional(lm_cond, st->lm_active ? 1u : 0u);
+    }
+}
+
+// Dynamic shared memory of the staged observations for a key capacity (keys, pixels
+// where `uv`, and the long-run table).
+size_t stage_bytes(int key_cap, bool uv) {
+    return (size_t)key_cap * (uv ? 12 : 4) + 12 * (size_t)(key_cap / LONG_RUN + 1);
+}
+
+template <typename K>
+int prepare(K kernel, int tb, size_t dyn) {
+    if (ensure_dynamic_smem((const void*)kernel, (int)dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, tb, dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+}  // namespace
+
+// The tile kernels stage a whole tile's observations; a problem whose largest tile does
+// not fit in shared memory keeps the per-thread-chunk kernels (all grids 0).
+void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs) {
+    L.tn_grid = L.tl_grid = L.te_grid = 0;
+    const int key_cap = (std::max(1, max_tile_obs) + 31) / 32 * 32;
+    const size_t limit = 160 * 1024;
+    if (stage_bytes(key_cap, true) > limit) return;
+    L.tk_key_cap = key_cap;
+    L.tn_smem = (int)stage_bytes(key_cap, false);
+    L.tl_smem = L.te_smem = (int)stage_bytes(key_cap, true);
+    const int bn = prepare(k_tile_normal<TN_TB>, TN_TB, L.tn_smem);
+    const int bl = prepare(k_tile_linearize<TL_TB>, TL_TB, L.tl_smem);
+    const int be = prepare(k_tile_eval<TE_TB>, TE_TB, L.te_smem);
+    if (bn < 1 || bl < 1 || be < 1) return;
+    const int nt = std::max(1, n_tiles);
+    L.tn_grid = nt;   // one CTA per tile
+    L.tl_grid = std::max(1, std::min({nt, sms * bl, MAX_GRID}));
+    L.te_grid = std::max(1, std::min({nt, sms * be, MAX_GRID}));
+}
+
+void launch_tile_normal(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
+                        const float* zs, int use_beta) {
+    k_tile_normal<TN_TB><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, zs, use_beta, L.tk_key_cap);
+}
+
+void launch_tile_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode, float* res_out,
+                           float* jac_out, CondHandle lm_cond, int use_cond) {
+    k_tile_linearize<TL_TB><<<L.tl_grid, TL_TB, L.tl_smem, s>>>(v, mode, res_out, jac_out, lm_cond, use_cond,
+                                                                 L.tk_key_cap);
+}
+
+void launch_tile_eval(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle lm_cond, int use_cond) {
+    k_tile_eval<TE_TB><<<L.te_grid, TE_TB, L.te_smem, s>>>(v, lm_cond, use_cond, L.tk_key_cap);
+}
+
+}  // namespace gbba

@@ -64,6 +64,9 @@ CONFIGS = {
     "medium": dict(n_cams=1000, n_pts=200_000, views=("poisson", 4.0), visibility="nearest", seed=1001),
     "large": dict(n_cams=13_000, n_pts=4_500_000, views=("geometric", 4.4), visibility="nearest", seed=1002),
     "autograd": dict(n_cams=200, n_pts=50_000, views=("poisson", 4.0), visibility="nearest", seed=1004),
+    # the large workload's shape (points per camera, view counts, visibility) at 1/13 of
+    # its size: a case small enough for full profiler captures of the same tile structure
+    "large_shape": dict(n_cams=1000, n_pts=346_000, views=("geometric", 4.4), visibility="nearest", seed=1002),
 }
 
 

@@ -46,3 +46,33 @@ def test_time_to_cost_takes_the_first_accepted_step_at_the_target():
     assert bench.time_to_cost(hist, 5.0) == 3.0
     assert bench.time_to_cost(hist, 2.0) is None
     assert bench.time_to_cost(hist, None) is None
+
+
+def test_tile_operator_bytes_per_unit():
+    # 4 B per key; 60 B per point (direction, D, X read; p, q written); 364 B per camera
+    assert bench.operator_model(_P(0, 0, 1)) == (4, 120)
+    assert bench.operator_model(_P(0, 1, 0))[0] == 60
+    assert bench.operator_model(_P(1, 0, 0))[0] == 364
+
+
+def test_tile_pcg_iteration_bytes():
+    # per point 72 (operator) + 84 (update) + 24 (M^-1); per camera 364 + 684
+    assert bench.pcg_iter_tile_model(_P(0, 1, 0)) == 180
+    assert bench.pcg_iter_tile_model(_P(1, 0, 0)) == 1048
+    assert bench.pcg_iter_tile_model(_P(0, 0, 1)) == 4
+
+
+def test_oracle_subsample_keeps_every_strided_point_with_all_its_observations():
+    import numpy as np
+    from paper_2605_30583_gb300 import synth
+    prob = synth.make_config("tiny")
+    sub = bench.oracle_subsample(prob, 4)
+    keep = np.arange(prob.n_pts)[::4]
+    assert sub.n_pts == len(keep) and sub.n_cams == prob.n_cams
+    assert sub.n_obs == int(np.isin(prob.pt_idx, keep).sum())
+    # observation by observation the same measurements, points renumbered in order
+    sel = np.isin(prob.pt_idx, keep)
+    assert np.array_equal(sub.pixels, prob.pixels[sel])
+    assert np.array_equal(keep[sub.pt_idx], prob.pt_idx[sel])
+    assert np.array_equal(sub.pts_init, prob.pts_init[keep])
+    assert np.all(np.bincount(sub.pt_idx, minlength=sub.n_pts) >= 2)
