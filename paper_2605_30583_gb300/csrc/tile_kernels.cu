@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_
         float acc[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
-        for (uint32_t off = lane; off < len; off += 32) {
+        uint32_t off = lane;
+        for (; off < len; off += 32) {
             const uint32_t j = T.lo + start + off;
             const uint32_t slot = sKey[start + off] & 0xffu;
             const float4 xp = sX4[slot], pp = sP4[slot];

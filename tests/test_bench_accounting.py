@@ -76,3 +76,11 @@ def test_oracle_subsample_keeps_every_strided_point_with_all_its_observations():
     assert np.array_equal(keep[sub.pt_idx], prob.pt_idx[sel])
     assert np.array_equal(sub.pts_init, prob.pts_init[keep])
     assert np.all(np.bincount(sub.pt_idx, minlength=sub.n_pts) >= 2)
+
+
+def test_fp64_form_iteration_model():
+    # per observation 192 B of stored Jacobian + 8 B of indices, 228 FP64 flops; per point
+    # 3 unknowns x (32 + 56) B + 48 B of block inverse; per camera 9 x 88 + 648 B
+    assert bench.fp64_iter_model(_P(0, 0, 1)) == (200, 228)
+    assert bench.fp64_iter_model(_P(0, 1, 0)) == (312, 60)
+    assert bench.fp64_iter_model(_P(1, 0, 0)) == (1440, 180)
