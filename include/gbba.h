@@ -83,7 +83,12 @@ typedef struct {
                                      2: the persistent kernel with the recurrences
                                      arranged so that one exchange per iteration carries
                                      both inner products (same iterates in exact
-                                     arithmetic; its updated residual drifts sooner)  */
+                                     arithmetic; its updated residual drifts sooner);
+                                     3: separate kernels per PCG iteration with those
+                                     one-reduction recurrences: each iteration's update
+                                     is fused into the next operator application (falls
+                                     back to 1 when a tile's observations exceed the
+                                     tile kernels' shared-memory stage)             */
     int32_t rotation_update;      /* how a step updates each camera's rotation:
                                      0 (default): additive angle-axis, w <- w + dw, the
                                      Jacobian taken w.r.t. w (through the left Jacobian
@@ -266,7 +271,10 @@ ba_status ba_repeat_normal(ba_problem* problem, int32_t launches);
  * PCG kernel (a whole PCG solve capped at 50 iterations with zero tolerance, each
  * launch after a preconditioner launch that resets its state, events around the PCG
  * launch alone) and [9] the PCG iterations that launch ran; -1 and 0 there when the
- * problem does not fit the persistent kernel.  Leaves the solver state undefined
+ * problem does not fit the persistent kernel; [10] one round of the one-reduction
+ * separate-kernel PCG (pcg_kernel 3: camera update and direction records, pose
+ * factors, tiles) past its first round, -1 when the tile kernels are not planned.
+ * Leaves the solver state undefined
  * (the next ba_solve starts afresh).  Synchronises. */
 ba_status ba_profile_kernels(ba_problem* problem, int32_t reps, double* us_out, int32_t n);
 

@@ -269,7 +269,7 @@ class Problem:
         return out, vav.value
 
     KERNELS = ("camera_records", "linearize", "precond", "matvec", "update", "candidate", "eval_candidate",
-               "commit", "pcg_persistent", "pcg_persistent_iters")
+               "commit", "pcg_persistent", "pcg_persistent_iters", "cg_round")
 
     def profile_kernels(self, reps=20) -> dict:
         out = np.zeros(len(self.KERNELS))

@@ -90,7 +90,7 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
     // solver arrays
     Bump s;
     s.off = union_base;
-    for (int i = 0; i < 9; ++i) l.vec[i] = s.take(T * n_vec);
+    for (int i = 0; i < 10; ++i) l.vec[i] = s.take(T * n_vec);
     l.cam_pre = s.take(4 * CP_STRIDE * nc);
     l.cam_pre_new = s.take(4 * CP_STRIDE * nc);
     l.cam_dir = s.take(4 * CD_STRIDE * nc);
@@ -155,8 +155,8 @@ Views<T> make_views(ba_problem* p) {
     v.long_off = (const uint32_t*)(w + l.long_off);
     v.long_run = (const uint32_t*)(w + l.long_run);
     v.short_start = (const uint32_t*)(w + l.short_start);
-    T** vecs[9] = {&v.x, &v.x_new, &v.h, &v.r, &v.z, &v.p, &v.q, &v.g, &v.D};
-    for (int i = 0; i < 9; ++i) *vecs[i] = (T*)(w + l.vec[i]);
+    T** vecs[10] = {&v.x, &v.x_new, &v.h, &v.r, &v.z, &v.p, &v.q, &v.g, &v.D, &v.s};
+    for (int i = 0; i < 10; ++i) *vecs[i] = (T*)(w + l.vec[i]);
     v.cam_pre = (float*)(w + l.cam_pre);
     v.cam_pre_new = (float*)(w + l.cam_pre_new);
     v.cam_dir = (float*)(w + l.cam_dir);
@@ -215,6 +215,9 @@ static void step_pcg_iter(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int u
         const Views<float>& v = p->vf;
         launch_schur(v, s, 1, &v.st->pcg_active);
         launch_update(v, p->L, s, pcg_c, use, 1);
+    } else if (p->precision == BA_PREC_MIXED && p->use_cg) {
+        const Views<float>& v = p->vf;
+        launch_cg_round(v, p->L, s, &v.st->pcg_active, pcg_c, use);
     } else if (p->precision == BA_PREC_MIXED) {
         const Views<float>& v = p->vf;
         launch_matvec(v, p->L, s, &v.st->pcg_active, v.z, 1);
@@ -243,8 +246,9 @@ static void step_lm_head(ba_problem* p, cudaStream_t s, CondHandle pcg_c, int us
     } else {
         launch64_precond(p->vd, p->L, s, pcg_c, use);
     }
+    // the one-reduction rounds take one more launch than updates: round 0 only stages
     if (inline_pcg && inner_pcg(p))
-        for (int k = 0; k < max_pcg; ++k) step_pcg_iter(p, s, pcg_c, use);
+        for (int k = 0; k < max_pcg + (p->use_cg ? 1 : 0); ++k) step_pcg_iter(p, s, pcg_c, use);
 }
 
 static void step_lm_tail(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use) {
@@ -861,7 +865,7 @@ static ba_status check_options(const ba_options* o) {
     }
     if (o->max_lm_iters < 0 || o->max_pcg_iters < 0 || !(o->pcg_rel_tol >= 0) || !(o->initial_trust_region > 0) ||
         !(o->min_diag > 0) || !(o->max_diag >= o->min_diag) || !(o->eps_depth >= 0) || !(o->max_mu > 0) ||
-        (o->pcg_kernel < 0 || o->pcg_kernel > 2) || o->use_graph < 0 || o->use_graph > 2 ||
+        (o->pcg_kernel < 0 || o->pcg_kernel > 3) || o->use_graph < 0 || o->use_graph > 2 ||
         (o->rotation_update != 0 && o->rotation_update != 1) || o->loss < 0 || o->loss > 2 ||
         !(o->loss_scale > 0) || (o->solver != 0 && o->solver != 1) || o->wait_timeout_ms < 0 ||
         o->wait_timeout_ms > 60000) {
@@ -937,13 +941,16 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
     // pcg_kernel 0: the persistent kernel's two-exchange form, 2: its one-exchange
     // form, each when the plan fits in that form; otherwise separate kernels
     const int want_form = o->pcg_kernel == 2 ? PCG_ONE_EXCHANGE : PCG_TWO_EXCHANGE;
-    const bool want_persistent = !want_schur && o->pcg_kernel != 1 &&
+    const bool want_persistent = !want_schur && o->pcg_kernel != 1 && o->pcg_kernel != 3 &&
                                  (want_form == PCG_ONE_EXCHANGE ? p->fits_one : p->fits_two);
-    if (want_persistent != p->use_persistent || want_schur != p->use_schur ||
+    // pcg_kernel 3: separate kernels with the one-reduction recurrences (tile kernels)
+    const bool want_cg = p->precision == BA_PREC_MIXED && !want_schur && o->pcg_kernel == 3 && p->L.tn_grid > 0;
+    if (want_persistent != p->use_persistent || want_schur != p->use_schur || want_cg != p->use_cg ||
         (want_persistent && want_form != p->p_form)) {
         release_graph(p);   // cached graphs were built for the other PCG form
         p->use_persistent = want_persistent;
         p->use_schur = want_schur;
+        p->use_cg = want_cg;
         if (want_persistent) p->p_form = want_form;
     }
     // A cooperative kernel cannot sit inside a conditional node, so with the persistent
@@ -1169,6 +1176,27 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
         }
         out[4] = 1e3 * total / reps;
     }
+    // one round of the one-reduction PCG past its first (so the update is applied),
+    // before the candidate kernels overwrite the direction records it reads
+    double out_cg = -1.0;
+    if (p->L.tn_grid > 0) {
+        const int32_t it1 = 1;
+        const double ab[2] = {1e-6, 0.5};   // alpha, beta (adjacent in the state)
+        double total = 0.0;
+        for (int i = 0; i <= reps; ++i) {
+            open_gates();
+            GBBA_CUDA(cudaMemcpyAsync(&v.st->pcg_iter, &it1, 4, cudaMemcpyHostToDevice, s));
+            GBBA_CUDA(cudaMemcpyAsync(&v.st->alpha, ab, sizeof(ab), cudaMemcpyHostToDevice, s));
+            cudaEventRecord(e0, s);
+            launch_cg_round(v, p->L, s, nullptr, 0, 0);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (i > 0) total += ms;
+        }
+        out_cg = 1e3 * total / reps;
+    }
     out[5] = timeit([&] { launch_candidate(v, p->L, s); });
     out[6] = timeit([&] { launch_eval_candidate(v, p->L, s, 0, 0); });
     out[7] = timeit([&] { launch_commit(v, p->L, s); });
@@ -1177,6 +1205,7 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
     GBBA_CUDA(cudaGetLastError());
     for (int i = 0; i < n && i < 8; ++i) us[i] = out[i];
     for (int i = 8; i < n && i < 10; ++i) us[i] = out_pcg[i - 8];
+    if (n > 10) us[10] = out_cg;
     // restore the default options; the solver state is re-initialised by the next solve
     ba_options d;
     ba_options_default(&d);

@@ -56,6 +56,11 @@ void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs);
 void launch_tile_normal(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                         const float* zs, int use_beta);
 void launch_tile_eval(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle lm_cond, int use_cond);
+// One round of the separate-kernel PCG with the one-reduction recurrences: the cameras'
+// update and direction records, the pose factors' operator, then the tiles (update fused
+// into the staging, operator, reduction and stop decision in the last CTA).
+void launch_cg_round(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate, CondHandle c,
+                     int use);
 void launch_tile_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode, float* res_out,
                            float* jac_out, CondHandle lm_cond, int use_cond);
 // Schur-complement PCG (kernels_mixed.cu): mode 0 right-hand side, 1 operator, 2 back-substitution

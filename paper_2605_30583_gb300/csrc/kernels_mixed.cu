@@ -294,6 +294,7 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
             v.r[e] = ri;
             v.z[e] = z;
             v.p[e] = 0.0f;
+            v.s[e] = 0.0f;
             v.h[e] = 0.0f;
             v.pc[e] = 0.0f;
             v.pc[v.pc_stride + e] = 0.0f;
@@ -338,6 +339,7 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
         v.r[e] = r0; v.r[e + 1] = r1; v.r[e + 2] = r2;
         v.z[e] = z0; v.z[e + 1] = z1; v.z[e + 2] = z2;
         v.p[e] = 0.0f; v.p[e + 1] = 0.0f; v.p[e + 2] = 0.0f;
+        v.s[e] = 0.0f; v.s[e + 1] = 0.0f; v.s[e + 2] = 0.0f;
         v.h[e] = 0.0f; v.h[e + 1] = 0.0f; v.h[e + 2] = 0.0f;
         rz += (double)(r0 * z0 + r1 * z1 + r2 * z2);
         rr += (double)(r0 * r0 + r1 * r1 + r2 * r2);
@@ -348,6 +350,7 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
         st->rr0 = out[1];
         st->rr = out[1];
         st->beta = 0.0;
+        st->alpha = 0.0;
         st->pcg_iter = 0;
         for (int k = 0; k < NSLOT * SLOT_STRIDE; ++k) st->acc_mv[k] = st->acc_up[k] = 0.0;
         st->pcg_active = (out[1] > 0.0 && isfinite(out[0]) && st->opt.max_pcg > 0) ? 1 : 0;
@@ -640,6 +643,9 @@ __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond, int 
 // records of h at x (for |J h|^2).
 __global__ void k_candidate(Views<float> v) {
     DevState* st = v.st;
+    // the one-reduction PCG leaves its last round's camera sums behind
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < v.n_cams * CA_STRIDE; i += gridDim.x * blockDim.x)
+        v.cam_acc[i] = 0.0f;
     if (st->lm_active == 0) return;
     const bool retract = st->opt.retract != 0;
     double gh = 0.0;

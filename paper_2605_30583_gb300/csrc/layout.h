@@ -115,6 +115,7 @@ struct Views {
     const uint32_t* short_start;    // [n_tiles]
     // vectors of length n_vec
     T *x, *x_new, *h, *r, *z, *p, *q, *g, *D;
+    T* s;             // A p of the one-reduction PCG recurrences (separate-kernel form)
     // camera records
     float *cam_pre, *cam_pre_new, *cam_dir, *cam_acc;
     float* pc;        // camera part of the PCG direction, double-buffered [2][pc_stride]

@@ -24,7 +24,7 @@ ba_status cuda_status(cudaError_t e, const char* what);
 // Offsets (bytes) of every array inside the workspace.
 struct Layout {
     size_t state, partials, obs_key, obs_uv, obs_user, tile_off, pt_user, pt_internal, obs_pm, pt_obs_off;
-    size_t vec[9];                       // x, x_new, h, r, z, p, q, g, D
+    size_t vec[10];                      // x, x_new, h, r, z, p, q, g, D, s
     size_t blk_tile, blk_cam_off, blk_cams, pslots;
     size_t long_off, long_run, short_start;
     size_t cam_pre, cam_pre_new, cam_dir, cam_acc, pc, cam_lin, cam_H, cam64, cam64_new, cam_H64, pt_H, Minv_c, Minv_p, jac, res, obs_w,
@@ -72,7 +72,8 @@ struct ba_problem {
     bool persistent = false;        // the plan fits, in at least one form
     bool fits_one = false, fits_two = false;   // ... in the one-exchange / two-exchange form
     bool use_persistent = false;    // the plan is used by the current solve sequences
-    bool use_schur = false;         // the current solve sequences use the Schur-complement PCG
+    bool use_schur = false;
+    bool use_cg = false;            // the current solve sequences use the one-reduction PCG rounds         // the current solve sequences use the Schur-complement PCG
     int p_grid = 0, p_smem_one = 0, p_smem_two = 0;
     int p_form = 0;                 // form of the current solve sequences (gbba::PCG_*)
     uint32_t* blk_tile = nullptr;   // device, [p_grid + 1]

@@ -102,18 +102,35 @@ __global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_
     const TileRange T = tile_range(v, blockIdx.x);
     float jp_s = 0.0f, jp_c = 0.0f, pd_s = 0.0f, pd_c = 0.0f;
     {
+        // every load before the stores of p (which may alias them)
+        static_assert((3 * TILE_PTS) % TB == 0, "whole entry steps");
+        constexpr int EPT = 3 * TILE_PTS / TB;
+        const int ne = 3 * T.npt;
         float* sPf = reinterpret_cast<float*>(sP4);
         float* sXf = reinterpret_cast<float*>(sX4);
-        for (int i = threadIdx.x; i < 3 * T.npt; i += TB) {
-            const float z = zs[T.base + i];
-            const float pn = beta != 0.0f ? fmaf(beta, v.p[T.base + i], z) : z;
-            v.p[T.base + i] = pn;
-            const float d = v.D[T.base + i];
-            const int slot = i / 3, k = i - 3 * slot;
-            sPf[4 * slot + k] = pn;
-            sXf[4 * slot + k] = v.x[T.base + i];
-            sQ[i] = mu * d * pn;
-            kahan_add(pd_s, pd_c, d * pn * pn);
+        float Z[EPT], P[EPT], Dd[EPT], X[EPT];
+#pragma unroll
+        for (int t = 0; t < EPT; ++t) {
+            const int i = threadIdx.x + t * TB;
+            if (i < ne) {
+                Z[t] = zs[T.base + i];
+                P[t] = beta != 0.0f ? v.p[T.base + i] : 0.0f;
+                Dd[t] = v.D[T.base + i];
+                X[t] = v.x[T.base + i];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < EPT; ++t) {
+            const int i = threadIdx.x + t * TB;
+            if (i < ne) {
+                const float pn = beta != 0.0f ? fmaf(beta, P[t], Z[t]) : Z[t];
+                v.p[T.base + i] = pn;
+                const int slot = i / 3, k = i - 3 * slot;
+                sPf[4 * slot + k] = pn;
+                sXf[4 * slot + k] = X[t];
+                sQ[i] = mu * Dd[t] * pn;
+                kahan_add(pd_s, pd_c, Dd[t] * pn * pn);
+            }
         }
     }
     stage_obs<TB, false>(v, T, sKey, nullptr, sRun);
@@ -185,6 +202,301 @@ __global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_
 }
 
 constexpr int TN_TB = 128;
+
+// ------------------------------------------------------- one-reduction PCG rounds ---
+// The separate-kernel PCG with its recurrences arranged as in the CG of Chronopoulos and
+// Gear (J. Comput. Appl. Math. 25, 1989): with u = M^-1 r, w = A u and s = A p carried by
+// s = w + beta s, both inner products gamma = r^T u and delta = u^T A u = |J u|^2 +
+// mu u^T D u of a round come from one reduction, and each round applies the previous
+// round's update before its operator:
+//   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev),
+//   p = u + beta p,  s = w + beta s,  h += alpha p,  r -= alpha s,  u = M^-1 r.
+// Round k (st->pcg_iter = k) runs k_cg_cameras (the cameras' update k - 1 from the camera
+// sums of round k - 1, then their direction records) and k_tile_cg (the points' update
+// k - 1 fused into the tile staging, then w = A u); the last CTA of k_tile_cg takes the
+// reduction, the stop test on |r_k| and alpha, beta.  Same iterates as the textbook
+// recurrences in exact arithmetic; the updated residual drifts from the true one sooner
+// in FP32.  Round 0 only stages u = z = M^-1 r_0 from the preconditioner.
+
+// Slot-sum components of a round: |J u|^2, u^T D u, r^T u, |r|^2.
+enum : int { CG_JU = 0, CG_UDU = 1, CG_RU = 2, CG_RR = 3 };
+
+// Cameras of a k_cg_cameras block: one thread per camera entry (coalesced vectors),
+// the 9x9 preconditioner rows and the direction record through shared memory.
+constexpr int CGC_CAMS = 32;
+constexpr int CGC_TB = 9 * CGC_CAMS;
+
+__global__ void __launch_bounds__(CGC_TB) k_cg_cameras(Views<float> v, const int32_t* gate) {
+    if (gated_off(gate)) return;
+    __shared__ float sr[CGC_TB], su[CGC_TB];
+    __shared__ double red[2 * (CGC_TB / 32)];
+    DevState* st = v.st;
+    const int k = st->pcg_iter;
+    const float alpha = (float)st->alpha, beta = (float)st->beta, mu = (float)st->mu;
+    const int i = threadIdx.x, cl = i / 9, kk = i - 9 * cl;
+    const int c = blockIdx.x * CGC_CAMS + cl;
+    const bool live = c < v.n_cams;
+    const size_t e = 9 * (size_t)blockIdx.x * CGC_CAMS + i;
+    float* ca = v.cam_acc + (size_t)c * CA_STRIDE;
+    const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
+    float ri = 0.0f, d = 0.0f;
+    if (live) {
+        d = v.D[e];
+        if (k > 0) {
+            // w = J^T J u (from the camera sums) + mu D u, then update k - 1
+            const float w = kk < 3 ? fmaf(JL[kk], ca[0], fmaf(JL[3 + kk], ca[1], JL[6 + kk] * ca[2])) : ca[kk];
+            const float uo = v.z[e];
+            const float pi = fmaf(beta, v.p[e], uo);
+            const float si = fmaf(beta, v.s[e], fmaf(mu * d, uo, w));
+            v.p[e] = pi;
+            v.s[e] = si;
+            v.h[e] = fmaf(alpha, pi, v.h[e]);
+            ri = fmaf(-alpha, si, v.r[e]);
+            v.r[e] = ri;
+        } else {
+            ri = v.r[e];
+        }
+    }
+    sr[i] = ri;
+    __syncthreads();   // every camera sum has been read
+    float u = 0.0f;
+    if (live) {
+        if (k > 0) {
+            ca[kk] = 0.0f;
+            const float* M = v.Minv_c + (size_t)c * MC_STRIDE + 9 * kk;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) u = fmaf(M[q], sr[9 * cl + q], u);
+            v.z[e] = u;
+        } else {
+            u = v.z[e];
+        }
+    }
+    su[i] = u;
+    float gs = 0.0f, gc = 0.0f, rs = 0.0f, rc = 0.0f, us = 0.0f, uc = 0.0f;   // Kahan pairs
+    kahan_add(gs, gc, ri * u);
+    kahan_add(rs, rc, ri * ri);
+    kahan_add(us, uc, d * u * u);
+    __syncthreads();
+    if (live) {   // direction record: phi = J_l u_w (3), u_t (3), u_intr (3)
+        const float dv = kk < 3 ? fmaf(JL[3 * kk], su[9 * cl], fmaf(JL[3 * kk + 1], su[9 * cl + 1],
+                                                                  JL[3 * kk + 2] * su[9 * cl + 2]))
+                                : u;
+        v.cam_dir[(size_t)c * CD_STRIDE + kk] = dv;
+    }
+    double bg, br, bu, dummy;
+    block_sum2c(gs, gc, rs, rc, red, bg, br);
+    block_sum2c(us, uc, 0.0f, 0.0f, red, bu, dummy);
+    if (threadIdx.x == 0) {
+        slot_add(st->acc_mv, CG_RU, bg);
+        slot_add(st->acc_mv, CG_RR, br);
+        slot_add(st->acc_mv, CG_UDU, bu);
+    }
+}
+
+template <int TB>
+__global__ void __launch_bounds__(TB) k_tile_cg(Views<float> v, const int32_t* gate, int key_cap, CondHandle pcg_cond,
+                                                int use_cond) {
+    if (gated_off(gate)) return;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);   // [key_cap]
+    uint32_t* sRun = sKey + key_cap;                     // [3 key_cap / LONG_RUN]
+    __shared__ float4 sX4[TILE_PTS], sP4[TILE_PTS];      // X and u of the tile's points
+    __shared__ float sQ[3 * TILE_PTS];
+    __shared__ unsigned int s_next;
+    __shared__ double red[2 * (TB / 32)];
+    __shared__ bool is_last;
+    DevState* st = v.st;
+    const int k = st->pcg_iter;
+    const float alpha = (float)st->alpha, beta = (float)st->beta, mu = (float)st->mu;
+    const float eps = (float)st->opt.eps;
+    const bool weighted = st->opt.loss != 0;
+    const int lane = threadIdx.x & 31;
+    const TileRange T = tile_range(v, blockIdx.x);
+    float jp_s = 0.0f, jp_c = 0.0f, ud_s = 0.0f, ud_c = 0.0f;   // |J u|^2, u^T D u
+    float ru_s = 0.0f, ru_c = 0.0f, rr_s = 0.0f, rr_c = 0.0f;   // r^T u, |r|^2
+    // The points' update k - 1 and their u = M^-1 r, entry-parallel (coalesced): every
+    // load first (the stores that follow may alias them, so loads issued after a store
+    // would wait for it), then the update entry by entry with r into sQ; then u of each
+    // entry from its point's three residual entries and row of M; then u and mu D u
+    // into the staging arrays.
+    static_assert((3 * TILE_PTS) % TB == 0, "whole entry steps");
+    constexpr int EPT = 3 * TILE_PTS / TB;   // entries per thread
+    const int ne = 3 * T.npt;
+    float* sPf = reinterpret_cast<float*>(sP4);
+    float* sXf = reinterpret_cast<float*>(sX4);
+    float R[EPT], X[EPT], Dd[EPT], Z[EPT], Qw[EPT], P[EPT], S[EPT], H[EPT], M0[EPT], M1[EPT], M2[EPT];
+#pragma unroll
+    for (int t = 0; t < EPT; ++t) {
+        const int i = threadIdx.x + t * TB;
+        if (i < ne) {
+            const size_t e = T.base + i;
+            R[t] = v.r[e];
+            X[t] = v.x[e];
+            Dd[t] = v.D[e];
+            Z[t] = v.z[e];
+            if (k > 0) {
+                Qw[t] = v.q[e];   // w = A u of the previous round (mu D u included)
+                P[t] = v.p[e];
+                S[t] = v.s[e];
+                H[t] = v.h[e];
+                // row kk of the point's packed symmetric block (xx, xy, xz, yy, yz, zz)
+                const int slot = i / 3, kk = i - 3 * slot;
+                const float* m = v.Minv_p + (size_t)(T.pt0 + slot) * MP_STRIDE;
+                M0[t] = __ldg(m + (kk == 0 ? 0 : (kk == 1 ? 1 : 2)));
+                M1[t] = __ldg(m + (kk == 0 ? 1 : (kk == 1 ? 3 : 4)));
+                M2[t] = __ldg(m + (kk == 0 ? 2 : (kk == 1 ? 4 : 5)));
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < EPT; ++t) {
+        const int i = threadIdx.x + t * TB;
+        if (i < ne) {
+            const size_t e = T.base + i;
+            if (k > 0) {
+                const float pi = fmaf(beta, P[t], Z[t]);
+                const float si = fmaf(beta, S[t], Qw[t]);
+                v.p[e] = pi;
+                v.s[e] = si;
+                v.h[e] = fmaf(alpha, pi, H[t]);
+                R[t] = fmaf(-alpha, si, R[t]);
+                v.r[e] = R[t];
+            }
+            sQ[i] = R[t];
+            const int slot = i / 3;
+            sXf[4 * slot + (i - 3 * slot)] = X[t];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < EPT; ++t) {
+        const int i = threadIdx.x + t * TB;
+        if (i < ne) {
+            const int slot = i / 3;
+            if (k > 0) {
+                Z[t] = fmaf(M0[t], sQ[3 * slot], fmaf(M1[t], sQ[3 * slot + 1], M2[t] * sQ[3 * slot + 2]));
+                v.z[T.base + i] = Z[t];
+            }
+            kahan_add(ru_s, ru_c, R[t] * Z[t]);
+            kahan_add(rr_s, rr_c, R[t] * R[t]);
+            kahan_add(ud_s, ud_c, Dd[t] * Z[t] * Z[t]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < EPT; ++t) {
+        const int i = threadIdx.x + t * TB;
+        if (i < ne) {
+            const int slot = i / 3;
+            sPf[4 * slot + (i - 3 * slot)] = Z[t];
+            sQ[i] = mu * Dd[t] * Z[t];
+        }
+    }
+    stage_obs<TB, false>(v, T, sKey, nullptr, sRun);
+    if (threadIdx.x == 0) s_next = 0u;
+    __syncthreads();
+    // w = A u: long runs in camera-uniform steps, then the short tail by chunks
+    for (;;) {
+        unsigned int rr = 0;
+        if (lane == 0) rr = atomicAdd(&s_next, 1u);
+        rr = __shfl_sync(FULL, rr, 0);
+        if (rr >= T.nl) break;
+        const uint32_t start = sRun[3 * rr] - T.lo, len = sRun[3 * rr + 1], c = sRun[3 * rr + 2];
+        const Cam cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+        float dir[9];
+        load_dir(v.cam_dir + (size_t)c * CD_STRIDE, dir);
+        float acc[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] = 0.0f;
+        for (uint32_t off = lane; off < len; off += 32) {
+            const uint32_t j = T.lo + start + off;
+            const uint32_t slot = sKey[start + off] & 0xffu;
+            const float4 xp = sX4[slot], pp = sP4[slot];
+            const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
+            const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * slot, __ldg(v.obs_w + j))
+                                      : obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * slot);
+            kahan_add(jp_s, jp_c, tt);
+        }
+        int idx;
+        const int nv = warp_split_sum<9>(acc, lane, idx);
+        if (nv > 0) atomicAdd(v.cam_acc + (size_t)c * CA_STRIDE + idx, acc[0]);
+    }
+    {
+        const uint32_t n = T.hi - T.ss;
+        const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
+        const uint32_t a = T.ss + min(threadIdx.x * chunk, n), b = T.ss + min(threadIdx.x * chunk + chunk, n);
+        uint32_t cur = NO_CAM;
+        float acc[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc[q] = 0.0f;
+        Cam cam;
+        float dir[9];
+        for (uint32_t j = a; j < b; ++j) {
+            const uint32_t key = sKey[j - T.lo];
+            const uint32_t c = key >> 8, slot = key & 0xffu;
+            if (c != cur) {
+                if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
+                cur = c;
+                cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
+                load_dir(v.cam_dir + (size_t)c * CD_STRIDE, dir);
+            }
+            const float4 xp = sX4[slot], pp = sP4[slot];
+            const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
+            const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * slot, __ldg(v.obs_w + j))
+                                      : obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * slot);
+            kahan_add(jp_s, jp_c, tt);
+        }
+        if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * T.npt; i += TB) v.q[T.base + i] = sQ[i];
+    double b_jp, b_ud, b_ru, b_rr;
+    block_sum2c(jp_s, jp_c, ud_s, ud_c, red, b_jp, b_ud);
+    block_sum2c(ru_s, ru_c, rr_s, rr_c, red, b_ru, b_rr);
+    if (threadIdx.x == 0) {
+        slot_add(st->acc_mv, CG_JU, b_jp);
+        slot_add(st->acc_mv, CG_UDU, b_ud);
+        slot_add(st->acc_mv, CG_RU, b_ru);
+        slot_add(st->acc_mv, CG_RR, b_rr);
+        __threadfence();
+        is_last = atomicAdd(&st->tickets[TK_UPD], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last || threadIdx.x >= 32) return;
+    __threadfence();
+    const double ju = slot_sum_warp(st->acc_mv, CG_JU), udu = slot_sum_warp(st->acc_mv, CG_UDU);
+    const double gam = slot_sum_warp(st->acc_mv, CG_RU), rho = slot_sum_warp(st->acc_mv, CG_RR);
+    for (int i = threadIdx.x; i < NSLOT * SLOT_STRIDE; i += 32) st->acc_mv[i] = 0.0;
+    if (threadIdx.x != 0) return;
+    st->tickets[TK_UPD] = 0u;
+    if (k > 0) st->pcg_total += 1;   // this round applied update k - 1
+    const double delta = ju + st->mu * udu;
+    bool stop = false;
+    if (!isfinite(gam) || !isfinite(rho) || !isfinite(delta)) {
+        st->status = 4;
+        stop = true;
+    } else if (k > 0 && (rho <= st->opt.tol * st->opt.tol * st->rr0 || k >= st->opt.max_pcg)) {
+        stop = true;
+    }
+    double a_new = 0.0, b_new = 0.0;
+    if (!stop) {
+        b_new = k > 0 ? gam / st->rz : 0.0;
+        const double den = k > 0 ? delta - b_new * gam / st->alpha : delta;
+        if (!(den > 0.0)) stop = true;
+        else a_new = gam / den;
+    }
+    st->rr = rho;
+    if (stop) {
+        st->pcg_iter = k;
+        st->pcg_active = 0;
+    } else {
+        st->alpha = a_new;
+        st->beta = b_new;
+        st->rz = gam;
+        st->pcg_iter = k + 1;
+    }
+    if (use_cond) cudaGraphSetConditional(pcg_cond, st->pcg_active ? 1u : 0u);
+}
 
 // ---------------------------------------------------------------- linearisation ---
 // Linearisation (fused score + Jacobian products, Sec. V-A): cost F = 1/2 sum rho(|r|^2),
@@ -548,9 +860,10 @@ void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs) {
     L.tn_smem = (int)stage_bytes(key_cap, false);
     L.tl_smem = L.te_smem = (int)stage_bytes(key_cap, true);
     const int bn = prepare(k_tile_normal<TN_TB>, TN_TB, L.tn_smem);
+    const int bc = prepare(k_tile_cg<TN_TB>, TN_TB, L.tn_smem);
     const int bl = prepare(k_tile_linearize<TL_TB>, TL_TB, L.tl_smem);
     const int be = prepare(k_tile_eval<TE_TB>, TE_TB, L.te_smem);
-    if (bn < 1 || bl < 1 || be < 1) return;
+    if (bn < 1 || bl < 1 || be < 1 || bc < 1) return;
     const int nt = std::max(1, n_tiles);
     L.tn_grid = nt;   // one CTA per tile
     L.tl_grid = std::max(1, std::min({nt, sms * bl, MAX_GRID}));
@@ -560,6 +873,13 @@ void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs) {
 void launch_tile_normal(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                         const float* zs, int use_beta) {
     k_tile_normal<TN_TB><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, zs, use_beta, L.tk_key_cap);
+}
+
+void launch_cg_round(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate, CondHandle c,
+                     int use) {
+    k_cg_cameras<<<std::max(1, (v.n_cams + CGC_CAMS - 1) / CGC_CAMS), CGC_TB, 0, s>>>(v, gate);
+    launch_factor_matvec(v, L, s, gate, v.z, 0);   // pose factors: |J_f u|^2 before the round's reduction
+    k_tile_cg<TN_TB><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, L.tk_key_cap, c, use);
 }
 
 void launch_tile_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode, float* res_out,

@@ -96,8 +96,8 @@ def test_normal_operator_matches_oracle(B):
 
 # (use_graph, pcg_kernel): conditional-loop graph / unrolled graph / host-launched
 # sequence, with the persistent PCG kernel (0: two exchanges per iteration, 2: one),
-# or one kernel per PCG step (1)
-MODES = [(1, 0), (1, 1), (1, 2), (2, 0), (2, 1), (2, 2), (0, 0), (0, 1), (0, 2)]
+# or separate kernels per PCG step (1: textbook recurrences, 3: one reduction a step)
+MODES = [(g, k) for g in (1, 2, 0) for k in (0, 1, 2, 3)]
 
 
 @pytest.mark.parametrize("use_graph,pcg_kernel", MODES)
@@ -141,7 +141,7 @@ def test_pcg_step_matches_oracle_at_tight_tolerance(B):
     prob = _ragged(13)
     opts = dict(max_lm_iters=1, pcg_rel_tol=1e-6, max_pcg_iters=200)
     ref = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels, O.LMOptions(**opts))
-    for k in (0, 1, 2):
+    for k in (0, 1, 2, 3):
         r = _problem(B, prob).solve(pcg_kernel=k, **opts)
         h, o = r.history[0], ref.history[0]
         assert abs(h["pcg_iters"] - o["pcg_iters"]) <= 2
