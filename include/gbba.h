@@ -66,7 +66,10 @@ typedef struct {
     double initial_trust_region;  /* mu_0 = 1 / initial_trust_region, default 100       */
     double min_diag;              /* D = clamp(diag(J^T J), min_diag, max_diag)         */
     double max_diag;
-    double max_mu;                /* stop when mu exceeds this, default 1e32            */
+    double max_mu;                /* stop when mu exceeds this, default 1e16 (a step is
+                                     then ~1e-16 of the gradient step: below the
+                                     parameters' resolution).  The mixed form caps it at
+                                     1e16: beyond that its FP32 PCG products underflow */
     double eps_depth;             /* epsilon of d_safe (Sec. VI-A), default 0           */
     int32_t use_graph;            /* 1 (default): one CUDA graph; its LM and PCG loops are
                                      device-driven conditional nodes, except with the

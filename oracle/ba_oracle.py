@@ -617,7 +617,7 @@ class LMOptions:
     min_diag: float = 1e-6
     max_diag: float = 1e32
     eps_depth: float = 0.0
-    max_mu: float = 1e32
+    max_mu: float = 1e16
     rotation_update: str = "additive"   # or "retraction": R <- Exp(d) R, J w.r.t. d
     loss: str = "squared"               # or "huber", "cauchy" (IRLS weights, see LOSSES)
     loss_scale: float = 1.0             # the loss's scale d, in pixels

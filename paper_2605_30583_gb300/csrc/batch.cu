@@ -1000,7 +1000,7 @@ DevOptions dev_options(const ba_options* o) {
     d.mu0 = 1.0 / o->initial_trust_region;
     d.min_diag = o->min_diag;
     d.max_diag = o->max_diag;
-    d.max_mu = o->max_mu;
+    d.max_mu = std::min(o->max_mu, 1e16);   // FP32 PCG vectors ~ g / (mu D): squares underflow past ~1e19
     d.eps = o->eps_depth;
     d.retract = o->rotation_update;
     return d;

@@ -113,8 +113,11 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
         l.cam64 = s.take(8 * CP_STRIDE * nc);
         l.cam64_new = s.take(8 * CP_STRIDE * nc);
         l.cam_H64 = s.take(8 * CH_STRIDE * nc);
+        l.xm = l.xm_new = 0;
     } else {
         l.jac = l.res = l.cam64 = l.cam64_new = l.cam_H64 = 0;
+        l.xm = s.take(8 * n_vec);
+        l.xm_new = s.take(8 * n_vec);
     }
     // ordering scratch (only live during ba_bind_workspace), overlaps the solver arrays
     Bump o;
@@ -170,6 +173,8 @@ Views<T> make_views(ba_problem* p) {
     v.cam64 = l.cam64 ? (double*)(w + l.cam64) : nullptr;
     v.cam64_new = l.cam64_new ? (double*)(w + l.cam64_new) : nullptr;
     v.cam_H64 = l.cam_H64 ? (double*)(w + l.cam_H64) : nullptr;
+    v.xm = l.xm ? (double*)(w + l.xm) : nullptr;
+    v.xm_new = l.xm_new ? (double*)(w + l.xm_new) : nullptr;
     v.jac = l.jac ? (T*)(w + l.jac) : nullptr;
     v.res = l.res ? (T*)(w + l.res) : nullptr;
     v.obs_w = (float*)(w + l.obs_w);
@@ -427,7 +432,7 @@ ba_status ba_options_default(ba_options* o) {
     o->initial_trust_region = 100.0;
     o->min_diag = 1e-6;
     o->max_diag = 1e32;
-    o->max_mu = 1e32;
+    o->max_mu = 1e16;
     o->eps_depth = 0.0;
     o->use_graph = 1;
     o->pcg_kernel = 0;
@@ -819,7 +824,7 @@ ba_status ba_get_params_device(ba_problem* p, void* cams, void* pts, int32_t dty
         set_error("ba_get_params_device: null pointer or bad dtype %d", dtype);
         return BA_ERR_INVALID_ARG;
     }
-    if (p->precision == BA_PREC_MIXED) launch_unpack(p->vf, p->L, p->stream, p->vf.x, cams, pts, dtype);
+    if (p->precision == BA_PREC_MIXED) launch_unpack(p->vf, p->L, p->stream, p->vf.xm, cams, pts, dtype);
     else launch64_unpack(p->vd, p->L, p->stream, cams, pts, dtype);
     GBBA_CUDA(cudaGetLastError());
     return BA_OK;
@@ -884,7 +889,9 @@ static ba_status write_options(ba_problem* p, const ba_options* o) {
     d.mu0 = 1.0 / o->initial_trust_region;
     d.min_diag = o->min_diag;
     d.max_diag = o->max_diag;
-    d.max_mu = o->max_mu;
+    // the mixed form's PCG vectors scale like g / (mu D): past mu ~ 1e19 their FP32
+    // squares underflow, so its LM stops at 1e16 at the latest
+    d.max_mu = p->precision == BA_PREC_MIXED ? std::min(o->max_mu, 1e16) : o->max_mu;
     d.eps = o->eps_depth;
     d.retract = o->rotation_update;
     d.loss = o->loss;

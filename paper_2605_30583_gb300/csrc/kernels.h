@@ -78,7 +78,7 @@ void launch_init_state(DevState* st, cudaStream_t s);
 void launch_finish_state(DevState* st, cudaStream_t s);
 void launch_pack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const void* cams,
                  const void* pts, int dtype);
-void launch_unpack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const float* src, void* cams,
+void launch_unpack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const double* src, void* cams,
                    void* pts, int dtype);
 void launch_set_direction(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const float* src);
 void launch_normal_out(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, float* out);

@@ -27,12 +27,13 @@ namespace gbba {
 
 
 // ------------------------------------------------------------------ K0 --------
-// Camera records from the current parameters; zeroes the linearisation sums.
+// Camera records from the current parameters (their FP64 master copy); zeroes the
+// linearisation sums.
 __global__ void k_camera_precompute(Views<float> v) {
     for (int c = 32 * (int)blockIdx.x + (int)threadIdx.x; threadIdx.x < 32 && c < v.n_cams; c += 32 * (int)gridDim.x) {
         double p[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) p[k] = (double)v.x[9 * (size_t)c + k];
+        for (int k = 0; k < 9; ++k) p[k] = v.xm[9 * (size_t)c + k];
         camera_record(p, v.cam_pre + (size_t)c * CP_STRIDE, v.st->opt.retract != 0);
         double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
 #pragma unroll
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(TB, 8) k_matvec(Views<float> v, const int32_t*
         const bool head = seg_reduce<9>(cur, acc);
         if (head && cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
         __syncthreads();
-        for (int i = threadIdx.x; i < 3 * npt; i += TB) v.q[base + i] = fmaf(mu * v.D[base + i], sd[i], sq[i]);
+        for (int i = threadIdx.x; i < 3 * npt; i += TB) v.q[base + i] = fmaf(mu, v.D[base + i] * sd[i], sq[i]);
         __syncthreads();
     }
     const double bj = block_sum((double)jp2 - (double)jp2c, red);
@@ -526,7 +527,7 @@ __global__ void k_update(Views<float> v, CondHandle pcg_cond, int use_cond, int 
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
                 const float pk = pcur[e + k];
-                const float qk = fmaf(mu * v.D[e + k], pk, q[k]);
+                const float qk = fmaf(mu, v.D[e + k] * pk, q[k]);
                 v.p[e + k] = pk;
                 v.h[e + k] = fmaf(alpha, pk, v.h[e + k]);
                 rn[k] = fmaf(-alpha, qk, v.r[e + k]);
@@ -653,27 +654,24 @@ __global__ void k_candidate(Views<float> v) {
         {
             const size_t e = 9 * (size_t)c;
             const double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
+            // the step applied to the FP64 master copy; the FP32 copy is its rounding
             double xn[9];
             float hc[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
                 hc[k] = v.h[e + k];
-                const float xk = v.x[e + k] + hc[k];
-                v.x_new[e + k] = xk;
-                xn[k] = (double)xk;
+                xn[k] = v.xm[e + k] + (double)hc[k];
                 gh += cl[CL_G + k] * (double)hc[k];
             }
             if (retract) {   // R' = Exp(h_w) R(w)
-                const double w[3] = {v.x[e], v.x[e + 1], v.x[e + 2]};
+                const double w[3] = {v.xm[e], v.xm[e + 1], v.xm[e + 2]};
                 const double hw[3] = {hc[0], hc[1], hc[2]};
-                double wn[3];
-                compose_rotvec(hw, w, wn);
+                compose_rotvec(hw, w, xn);
+            }
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float wk = (float)wn[k];
-                    v.x_new[e + k] = wk;
-                    xn[k] = (double)wk;
-                }
+            for (int k = 0; k < 9; ++k) {
+                v.xm_new[e + k] = xn[k];
+                v.x_new[e + k] = (float)xn[k];
             }
             camera_record(xn, v.cam_pre_new + (size_t)c * CP_STRIDE, retract);
             const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
@@ -692,7 +690,9 @@ __global__ void k_candidate(Views<float> v) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const float hk = v.h[e + k];
-                v.x_new[e + k] = v.x[e + k] + hk;
+                const double xk = v.xm[e + k] + (double)hk;
+                v.xm_new[e + k] = xk;
+                v.x_new[e + k] = (float)xk;
                 s = fmaf(v.g[e + k], hk, s);
             }
             gh += (double)s;
@@ -765,7 +765,8 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
 }
 
 // ------------------------------------------------------------------ K8 --------
-// Commit an accepted step: x = x', camera records = those of x', and clear the
+// Commit an accepted step: x = x' (FP64 master and FP32 copies), camera records =
+// those of x', and clear the
 // camera linearisation sums for the relinearisation that follows.
 __global__ void k_commit(Views<float> v) {
     if (v.st->accepted == 0) return;
@@ -776,6 +777,9 @@ __global__ void k_commit(Views<float> v) {
     const float4* xs = reinterpret_cast<const float4*>(v.x_new);
     float4* xd = reinterpret_cast<float4*>(v.x);
     for (size_t i = tid; i < (size_t)v.n_vec / 4; i += nth) xd[i] = xs[i];
+    const double2* ms = reinterpret_cast<const double2*>(v.xm_new);
+    double2* md = reinterpret_cast<double2*>(v.xm);
+    for (size_t i = tid; i < (size_t)v.n_vec / 2; i += nth) md[i] = ms[i];
     const float4* cs = reinterpret_cast<const float4*>(v.cam_pre_new);
     float4* cd = reinterpret_cast<float4*>(v.cam_pre);
     for (size_t i = tid; i < (size_t)v.n_cams * (CP_STRIDE / 4); i += nth) cd[i] = cs[i];
@@ -1047,23 +1051,32 @@ __global__ void k_init_state(DevState* st) {
 __global__ void k_finish_state(DevState* st) { st->t_end = global_ns(); }
 
 // Parameters between the caller layout (cams [n][9], pts [n][3], float or double)
-// and the internal vector layout.
+// and the internal vector layout: set writes the FP64 master copy and its FP32
+// rounding, get reads the master copy.
 template <typename S>
 __global__ void k_pack(Views<float> v, const S* cams, const S* pts) {
     const int items = v.n_cams + v.n_pts;
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
         if (it < v.n_cams) {
-            for (int k = 0; k < 9; ++k) v.x[9 * (size_t)it + k] = (float)cams[9 * (size_t)it + k];
+            for (int k = 0; k < 9; ++k) {
+                const double a = (double)cams[9 * (size_t)it + k];
+                v.xm[9 * (size_t)it + k] = a;
+                v.x[9 * (size_t)it + k] = (float)a;
+            }
         } else {
             const int u = it - v.n_cams;
             const size_t e = v.pt_off + 3 * (size_t)v.pt_internal[u];
-            for (int k = 0; k < 3; ++k) v.x[e + k] = (float)pts[3 * (size_t)u + k];
+            for (int k = 0; k < 3; ++k) {
+                const double a = (double)pts[3 * (size_t)u + k];
+                v.xm[e + k] = a;
+                v.x[e + k] = (float)a;
+            }
         }
     }
 }
 
 template <typename S>
-__global__ void k_unpack(Views<float> v, const float* src, S* cams, S* pts) {
+__global__ void k_unpack(Views<float> v, const double* src, S* cams, S* pts) {
     const int items = v.n_cams + v.n_pts;
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
         if (it < v.n_cams) {
@@ -1089,7 +1102,7 @@ __global__ void k_normal_out(Views<float> v, S* out) {
             const float* JL = v.cam_pre + (size_t)it * CP_STRIDE + CP_JL;
             for (int k = 0; k < 9; ++k) {
                 float q = k < 3 ? fmaf(JL[k], ca[0], fmaf(JL[3 + k], ca[1], JL[6 + k] * ca[2])) : ca[k];
-                out[e + k] = (S)fmaf(mu * v.D[e + k], v.p[e + k], q);
+                out[e + k] = (S)fmaf(mu, v.D[e + k] * v.p[e + k], q);
             }
             for (int k = 0; k < CA_STRIDE; ++k) ca[k] = 0.0f;
         } else {
@@ -1194,7 +1207,7 @@ void launch_pack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, cons
     if (dtype == 1) k_pack<double><<<g, L.item_block, 0, s>>>(v, (const double*)cams, (const double*)pts);
     else k_pack<float><<<g, L.item_block, 0, s>>>(v, (const float*)cams, (const float*)pts);
 }
-void launch_unpack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const float* src, void* cams,
+void launch_unpack(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const double* src, void* cams,
                    void* pts, int dtype) {
     const int g = grid_items(L, v.n_cams + v.n_pts);
     if (dtype == 1) k_unpack<double><<<g, L.item_block, 0, s>>>(v, src, (double*)cams, (double*)pts);

@@ -116,6 +116,12 @@ struct Views {
     // vectors of length n_vec
     T *x, *x_new, *h, *r, *z, *p, *q, *g, *D;
     T* s;             // A p of the one-reduction PCG recurrences (separate-kernel form)
+    // Mixed form: the parameters' FP64 master copy (x, x_new above are its FP32
+    // roundings, which every FP32 kernel reads).  Steps are applied to the master copy,
+    // so a step smaller than an FP32 ulp of a parameter still accumulates, and each
+    // evaluation rounds afresh: the rounding then enters F and F' alike instead of
+    // adding a one-sided cost to every candidate.  nullptr in the plain form.
+    double *xm, *xm_new;
     // camera records
     float *cam_pre, *cam_pre_new, *cam_dir, *cam_acc;
     float* pc;        // camera part of the PCG direction, double-buffered [2][pc_stride]

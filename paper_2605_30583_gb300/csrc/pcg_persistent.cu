@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                 for (int q = 0; q < 3; ++q) {
                     const float pk = pq[q];
                     sH[e + q] = fmaf(af, pk, sH[e + q]);
-                    r3[q] = fmaf(-af, fmaf(muf * sD[e + q], pk, sQ[e + q]), sR[e + q]);
+                    r3[q] = fmaf(-af, fmaf(muf, sD[e + q] * pk, sQ[e + q]), sR[e + q]);
                     sR[e + q] = r3[q];
                 }
                 const float* m = sM + 6 * i;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
             if (mine) {
                 v.p[e] = pk;
                 v.h[e] = fmaf(af, pk, hk);
-                ri = fmaf(-af, fmaf(muf * dk, pk, qi), rk);
+                ri = fmaf(-af, fmaf(muf, dk * pk, qi), rk);
                 v.r[e] = ri;
                 s_cam_r[tid] = ri;
             }
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent(Views<float> v, const 
                     const float pk = pc_new[e];
                     v.p[e] = pk;
                     v.h[e] = fmaf(af, pk, v.h[e]);
-                    ri = fmaf(-af, fmaf(muf * __ldg(v.D + e), pk, qi), v.r[e]);
+                    ri = fmaf(-af, fmaf(muf, __ldg(v.D + e) * pk, qi), v.r[e]);
                     v.r[e] = ri;
                     s_cam_r[idx] = ri;
                 }
@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
                 q = __ldcg(ca + i);
             }
             const float u = sCu[e];
-            const float w = fmaf(muf * __ldg(v.D + 9 * (size_t)c + i), u, q);
+            const float w = fmaf(muf, __ldg(v.D + 9 * (size_t)c + i) * u, q);
             const float pk = fmaf(beta, sCp[e], u);
             const float sk = fmaf(beta, sCs[e], w);
             sCp[e] = pk;
@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 const int e = 3 * i + q;
-                const float w = fmaf(muf * Dq[q], uq[q], sQ[e]);
+                const float w = fmaf(muf, Dq[q] * uq[q], sQ[e]);
                 const float pk = fmaf(beta, sP[e], uq[q]);
                 const float sk = fmaf(beta, sS[e], w);
                 sP[e] = pk;

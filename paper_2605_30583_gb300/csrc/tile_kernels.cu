@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_
                 const int slot = i / 3, k = i - 3 * slot;
                 sPf[4 * slot + k] = pn;
                 sXf[4 * slot + k] = X[t];
-                sQ[i] = mu * Dd[t] * pn;
+                sQ[i] = mu * (Dd[t] * pn);
                 kahan_add(pd_s, pd_c, Dd[t] * pn * pn);
             }
         }
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(CGC_TB) k_cg_cameras(Views<float> v, const int
             const float w = kk < 3 ? fmaf(JL[kk], ca[0], fmaf(JL[3 + kk], ca[1], JL[6 + kk] * ca[2])) : ca[kk];
             const float uo = v.z[e];
             const float pi = fmaf(beta, v.p[e], uo);
-            const float si = fmaf(beta, v.s[e], fmaf(mu * d, uo, w));
+            const float si = fmaf(beta, v.s[e], fmaf(mu, d * uo, w));
             v.p[e] = pi;
             v.s[e] = si;
             v.h[e] = fmaf(alpha, pi, v.h[e]);
@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(TB) k_tile_cg(Views<float> v, const int32_t* g
         if (i < ne) {
             const int slot = i / 3;
             sPf[4 * slot + (i - 3 * slot)] = Z[t];
-            sQ[i] = mu * Dd[t] * Z[t];
+            sQ[i] = mu * (Dd[t] * Z[t]);
         }
     }
     stage_obs<TB, false>(v, T, sKey, nullptr, sRun);
