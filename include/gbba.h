@@ -124,6 +124,16 @@ typedef struct {
                                      the barrier incomplete.  0..60000.  The separate-
                                      kernel PCG and the batched mode have no grid-wide
                                      waits and ignore it.                              */
+    int32_t residual_precision;   /* arithmetic of the mixed form's residuals r = f s p - u
+                                     (the cost LM minimises and the r of g = J^T r):
+                                     1 (default): double-float (pairs of FP32 values,
+                                     ~48 bits) from FP64 master parameters, then rounded
+                                     to FP32, so r carries ~1e-7 px of error instead of
+                                     FP32's ~1e-4 px, which LM can otherwise exploit
+                                     along poorly constrained directions; 0: FP32.  The
+                                     Jacobian, the normal operator and PCG are FP32
+                                     either way; the FP64 form and the batched mode
+                                     ignore it.                                         */
 } ba_options;
 
 /* One LM iteration (Sec. V): cost before the step, candidate cost, damping used,
@@ -276,7 +286,8 @@ ba_status ba_repeat_normal(ba_problem* problem, int32_t launches);
  * launch alone) and [9] the PCG iterations that launch ran; -1 and 0 there when the
  * problem does not fit the persistent kernel; [10] one round of the one-reduction
  * separate-kernel PCG (pcg_kernel 3: camera update and direction records, pose
- * factors, tiles) past its first round, -1 when the tile kernels are not planned.
+ * factors, tiles) past its first round, -1 when the tile kernels are not planned;
+ * [11] the residual pass (all observations' residuals at the current parameters).
  * Leaves the solver state undefined
  * (the next ba_solve starts afresh).  Synchronises. */
 ba_status ba_profile_kernels(ba_problem* problem, int32_t reps, double* us_out, int32_t n);

@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
                 ("min_diag", ctypes.c_double), ("max_diag", ctypes.c_double), ("max_mu", ctypes.c_double),
                 ("eps_depth", ctypes.c_double), ("use_graph", ctypes.c_int32), ("pcg_kernel", ctypes.c_int32),
                 ("rotation_update", ctypes.c_int32), ("loss", ctypes.c_int32), ("loss_scale", ctypes.c_double),
-                ("solver", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32)]
+                ("solver", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32),
+                ("residual_precision", ctypes.c_int32)]
 
 
 class IterStat(ctypes.Structure):
@@ -269,7 +270,7 @@ class Problem:
         return out, vav.value
 
     KERNELS = ("camera_records", "linearize", "precond", "matvec", "update", "candidate", "eval_candidate",
-               "commit", "pcg_persistent", "pcg_persistent_iters", "cg_round")
+               "commit", "pcg_persistent", "pcg_persistent_iters", "cg_round", "residual")
 
     def profile_kernels(self, reps=20) -> dict:
         out = np.zeros(len(self.KERNELS))

@@ -113,11 +113,14 @@ Layout compute_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, int32_t prec
         l.cam64 = s.take(8 * CP_STRIDE * nc);
         l.cam64_new = s.take(8 * CP_STRIDE * nc);
         l.cam_H64 = s.take(8 * CH_STRIDE * nc);
-        l.xm = l.xm_new = 0;
+        l.xm = l.xm_new = l.cam_lo = l.cam_lo_new = l.rbuf = 0;
     } else {
         l.jac = l.res = l.cam64 = l.cam64_new = l.cam_H64 = 0;
         l.xm = s.take(8 * n_vec);
         l.xm_new = s.take(8 * n_vec);
+        l.cam_lo = s.take(4 * CLO_STRIDE * nc);
+        l.cam_lo_new = s.take(4 * CLO_STRIDE * nc);
+        l.rbuf = s.take(4 * 2 * no);
     }
     // ordering scratch (only live during ba_bind_workspace), overlaps the solver arrays
     Bump o;
@@ -175,6 +178,9 @@ Views<T> make_views(ba_problem* p) {
     v.cam_H64 = l.cam_H64 ? (double*)(w + l.cam_H64) : nullptr;
     v.xm = l.xm ? (double*)(w + l.xm) : nullptr;
     v.xm_new = l.xm_new ? (double*)(w + l.xm_new) : nullptr;
+    v.cam_lo = l.cam_lo ? (float*)(w + l.cam_lo) : nullptr;
+    v.cam_lo_new = l.cam_lo_new ? (float*)(w + l.cam_lo_new) : nullptr;
+    v.rbuf = l.rbuf ? (float*)(w + l.rbuf) : nullptr;
     v.jac = l.jac ? (T*)(w + l.jac) : nullptr;
     v.res = l.res ? (T*)(w + l.res) : nullptr;
     v.obs_w = (float*)(w + l.obs_w);
@@ -207,6 +213,7 @@ static void step_init(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use) {
     if (p->precision == BA_PREC_MIXED) {
         launch_init_state(p->vf.st, s);
         launch_camera_precompute(p->vf, p->L, s);
+        launch_residual(p->vf, p->L, s, 0);
         launch_linearize(p->vf, p->L, s, 0, nullptr, nullptr, lm_c, use);
     } else {
         launch_init_state(p->vd.st, s);
@@ -261,6 +268,7 @@ static void step_lm_tail(ba_problem* p, cudaStream_t s, CondHandle lm_c, int use
         const Views<float>& v = p->vf;
         if (p->use_schur) launch_schur(v, s, 2, &v.st->lm_active);   // points back-substituted
         launch_candidate(v, p->L, s);
+        launch_residual(v, p->L, s, 1);   // r(x') and F'; the relinearisation reuses r
         launch_eval_candidate(v, p->L, s, lm_c, use);
         launch_commit(v, p->L, s);
         launch_linearize(v, p->L, s, 1, nullptr, nullptr, lm_c, 0);
@@ -441,6 +449,7 @@ ba_status ba_options_default(ba_options* o) {
     o->loss_scale = 1.0;
     o->solver = 0;
     o->wait_timeout_ms = 2000;
+    o->residual_precision = 1;
     return BA_OK;
 }
 
@@ -716,6 +725,7 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
         p->L.lin_grid = std::min(MAX_GRID, sms * std::max(1, occupancy_blocks_linearize()));
         p->L.mv_grid = std::min(MAX_GRID, sms * std::max(1, occupancy_blocks_matvec()));
         p->L.ev_grid = std::min(MAX_GRID, sms * std::max(1, occupancy_blocks_eval()));
+        p->L.res_grid = std::min(MAX_GRID, sms * occupancy_blocks_residual());
     }
     const Layout& l = p->lay;
     char* w = p->ws;
@@ -847,6 +857,7 @@ ba_status ba_evaluate(ba_problem* p, double* cost_out, void* residuals, void* ja
     GBBA_CUDA(cudaMemcpyAsync(&dst->opt.retract, plain, sizeof(plain), cudaMemcpyHostToDevice, p->stream));
     if (p->precision == BA_PREC_MIXED) {
         launch_camera_precompute(p->vf, p->L, p->stream);
+        launch_residual(p->vf, p->L, p->stream, 0);
         launch_linearize(p->vf, p->L, p->stream, 2, (float*)residuals, (float*)jacobian, 0, 0);
     } else {
         launch64_camera_precompute(p->vd, p->L, p->stream);
@@ -873,9 +884,9 @@ static ba_status check_options(const ba_options* o) {
         (o->pcg_kernel < 0 || o->pcg_kernel > 3) || o->use_graph < 0 || o->use_graph > 2 ||
         (o->rotation_update != 0 && o->rotation_update != 1) || o->loss < 0 || o->loss > 2 ||
         !(o->loss_scale > 0) || (o->solver != 0 && o->solver != 1) || o->wait_timeout_ms < 0 ||
-        o->wait_timeout_ms > 60000) {
+        o->wait_timeout_ms > 60000 || (o->residual_precision != 0 && o->residual_precision != 1)) {
         set_error("invalid options (iterations must be >= 0, tolerances/diagonal bounds positive, "
-                  "wait_timeout_ms in [0, 60000])");
+                  "wait_timeout_ms in [0, 60000], residual_precision 0 or 1)");
         return BA_ERR_INVALID_ARG;
     }
     return BA_OK;
@@ -897,6 +908,7 @@ static ba_status write_options(ba_problem* p, const ba_options* o) {
     d.loss = o->loss;
     d.loss_scale = o->loss_scale;
     d.wait_ns = 1000000LL * (int64_t)o->wait_timeout_ms;
+    d.res_df = o->residual_precision;
     static_assert(offsetof(DevState, opt) == 0, "options first");
     GBBA_CUDA(cudaMemcpyAsync(p->ws + p->lay.state, &d, sizeof(d), cudaMemcpyHostToDevice, p->stream));
     return BA_OK;
@@ -1099,6 +1111,7 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
     o.max_mu = 1e300;
     o.eps = 0.0;
     o.wait_ns = 2000000000LL;
+    o.res_df = 1;
     GBBA_CUDA(cudaMemcpyAsync(p->ws + p->lay.state, &o, sizeof(o), cudaMemcpyHostToDevice, s));
     const int32_t flags[4] = {1, 1, 1, 1};
     auto open_gates = [&]() -> cudaError_t {
@@ -1138,6 +1151,7 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
         launch_init_state(v.st, s);
         open_gates();
         launch_camera_precompute(v, p->L, s);
+        launch_residual(v, p->L, s, 0);
         launch_linearize(v, p->L, s, 0, nullptr, nullptr, 0, 0);
         double total_ms = 0.0;
         for (int i = 0; i <= reps; ++i) {
@@ -1204,6 +1218,7 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
         }
         out_cg = 1e3 * total / reps;
     }
+    const double out_res = timeit([&] { launch_residual(v, p->L, s, 0); });
     out[5] = timeit([&] { launch_candidate(v, p->L, s); });
     out[6] = timeit([&] { launch_eval_candidate(v, p->L, s, 0, 0); });
     out[7] = timeit([&] { launch_commit(v, p->L, s); });
@@ -1213,6 +1228,7 @@ ba_status ba_profile_kernels(ba_problem* p, int32_t reps, double* us, int32_t n)
     for (int i = 0; i < n && i < 8; ++i) us[i] = out[i];
     for (int i = 8; i < n && i < 10; ++i) us[i] = out_pcg[i - 8];
     if (n > 10) us[10] = out_cg;
+    if (n > 11) us[11] = out_res;
     // restore the default options; the solver state is re-initialised by the next solve
     ba_options d;
     ba_options_default(&d);

@@ -218,7 +218,10 @@ __device__ __forceinline__ void rodrigues_coeffs(double th2, double& A, double& 
 // so d(R(w) X)/dw . d = (J_l d) x (R X).
 // With `retract` the record is for the tangent-space update R <- Exp(d) R(w): the
 // rotation Jacobian is then taken w.r.t. d at d = 0, i.e. J_l is replaced by I.
-__device__ __forceinline__ void camera_record(const double* c, float* out, bool retract = false) {
+// `lo` (optional, CLO_STRIDE floats): the FP32 rounding error of R, t, f, k1, k2 at the
+// same offsets as in `out`, so out + lo carries them to ~2^-48 (double-float values).
+__device__ __forceinline__ void camera_record(const double* c, float* out, bool retract = false,
+                                              float* lo = nullptr) {
     const double w0 = c[0], w1 = c[1], w2 = c[2];
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
     double A, B, C;
@@ -241,6 +244,17 @@ __device__ __forceinline__ void camera_record(const double* c, float* out, bool 
     out[CP_K1] = (float)c[7];
     out[CP_K2] = (float)c[8];
     out[CP_PAD] = 0.0f;
+    if (lo) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double I = (i % 4 == 0) ? 1.0 : 0.0;
+            const double r = I + A * K[i] + B * K2[i];
+            lo[CP_R + i] = (float)(r - (double)(float)r);
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) lo[CP_T + i] = (float)(c[3 + i] - (double)(float)c[3 + i]);
+        lo[CP_PAD] = 0.0f;
+    }
 }
 
 // Unit quaternion (q0; q1 q2 q3) of the rotation vector v: (cos(t/2); sin(t/2) v / t),

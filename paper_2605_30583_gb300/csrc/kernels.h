@@ -32,6 +32,7 @@ struct LaunchCfg {
     int lin_grid = 1024;    // cap on blocks of tile kernels
     int mv_grid = 1024;
     int ev_grid = 1024;
+    int res_grid = 1024;    // residual pass (residual.cu)
     // tile kernels (tile_kernels.cu: long runs in camera-uniform warp steps); a grid of 0
     // selects the per-thread-chunk kernel of kernels_mixed.cu instead
     int tn_grid = 0;   // normal operator, one CTA per tile
@@ -40,6 +41,11 @@ struct LaunchCfg {
     int tk_key_cap = 0;                      // observations of the largest tile, rounded up to 32
     int tn_smem = 0, tl_smem = 0, te_smem = 0;   // their dynamic shared memory (staged observations)
 };
+
+// residual pass of the mixed form (residual.cu): at x (at_candidate 0) or at x' (1,
+// also F' into the state for the LM decision)
+void launch_residual(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int at_candidate);
+int occupancy_blocks_residual();
 
 // mixed precision (kernels_mixed.cu)
 void launch_camera_precompute(const Views<float>& v, const LaunchCfg& L, cudaStream_t s);

@@ -34,7 +34,7 @@ __global__ void k_camera_precompute(Views<float> v) {
         double p[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) p[k] = v.xm[9 * (size_t)c + k];
-        camera_record(p, v.cam_pre + (size_t)c * CP_STRIDE, v.st->opt.retract != 0);
+        camera_record(p, v.cam_pre + (size_t)c * CP_STRIDE, v.st->opt.retract != 0, v.cam_lo + (size_t)c * CLO_STRIDE);
         double* cl = v.cam_lin + (size_t)c * CL_STRIDE;
 #pragma unroll
         for (int k = 0; k < CL_STRIDE; ++k) cl[k] = 0.0;
@@ -119,9 +119,7 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
                 }
                 const float4 X = sx[slot];
                 const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
-                const float fs = cam.f * g.s;
-                float r0 = fmaf(fs, g.p[0], -__ldg(v.obs_uv + 2 * (size_t)j));
-                float r1 = fmaf(fs, g.p[1], -__ldg(v.obs_uv + 2 * (size_t)j + 1));
+                float r0 = __ldg(v.rbuf + 2 * (size_t)j), r1 = __ldg(v.rbuf + 2 * (size_t)j + 1);   // k_residual
                 // camera Jacobian rows: [J_w | J_t | J_intr], J_w[:,k] = A (J_l[:,k] x RX)
                 float j0[9], j1[9];
 #pragma unroll
@@ -673,7 +671,7 @@ __global__ void k_candidate(Views<float> v) {
                 v.xm_new[e + k] = xn[k];
                 v.x_new[e + k] = (float)xn[k];
             }
-            camera_record(xn, v.cam_pre_new + (size_t)c * CP_STRIDE, retract);
+            camera_record(xn, v.cam_pre_new + (size_t)c * CP_STRIDE, retract, v.cam_lo_new + (size_t)c * CLO_STRIDE);
             const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
             float* d = v.cam_dir + (size_t)c * CD_STRIDE;
 #pragma unroll
@@ -714,8 +712,7 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
     const int active = st->lm_active;
     const float eps = (float)st->opt.eps;
     const int loss = st->opt.loss;
-    const float lscale = (float)st->opt.loss_scale;
-    double fnew = 0.0, jh2 = 0.0;
+    double jh2 = 0.0;
     if (active) {
         for (int tile = blockIdx.x; tile < v.n_tiles; tile += gridDim.x) {
             const uint32_t lo = v.tile_off[tile], hi = v.tile_off[tile + 1];
@@ -724,42 +721,32 @@ __global__ void __launch_bounds__(TB) k_eval_candidate(Views<float> v, CondHandl
             const uint32_t chunk = odd_chunk<uint32_t>(n, TB);
             const uint32_t a = min(lo + threadIdx.x * chunk, hi), b = min(a + chunk, hi);
             uint32_t cur = NO_CAM;
-            Cam cn, co;
+            Cam co;
             float dir[9];
-            float fc = 0.0f, jc = 0.0f, fcc = 0.0f, jcc = 0.0f;   // Kahan pairs
+            float jc = 0.0f, jcc = 0.0f;   // Kahan pair
             for (uint32_t j = a; j < b; ++j) {
                 const uint32_t key = __ldg(v.obs_key + j);
                 const uint32_t c = key >> 8, slot = key & 0xffu;
                 if (c != cur) {
                     cur = c;
-                    cn = load_cam(v.cam_pre_new + (size_t)c * CP_STRIDE);
                     co = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
                     load_dir(v.cam_dir + (size_t)c * CD_STRIDE, dir);
                 }
                 const size_t xi = v.pt_off + 3 * (size_t)(pt0 + slot);
-                float r0, r1;
-                project_residual(cn, v.x_new[xi], v.x_new[xi + 1], v.x_new[xi + 2], eps,
-                                 v.obs_uv[2 * (size_t)j], v.obs_uv[2 * (size_t)j + 1], r0, r1);
                 const Geo g = project_geo(co, v.x[xi], v.x[xi + 1], v.x[xi + 2], eps);
                 float t0, t1;
                 jdir(g, co, dir, v.h[xi], v.h[xi + 1], v.h[xi + 2], t0, t1);
-                if (loss) {   // F' = 1/2 sum rho(|r'|^2); |J h|^2 weighted at x
-                    kahan_add(fc, fcc, loss_rho(fmaf(r0, r0, r1 * r1), loss, lscale));
-                    kahan_add(jc, jcc, __ldg(v.obs_w + j) * fmaf(t0, t0, t1 * t1));
-                } else {
-                    kahan_add(fc, fcc, fmaf(r0, r0, r1 * r1));
-                    kahan_add(jc, jcc, fmaf(t0, t0, t1 * t1));
-                }
+                // |J h|^2 weighted at x (F' comes from k_residual)
+                kahan_add(jc, jcc, (loss ? __ldg(v.obs_w + j) : 1.0f) * fmaf(t0, t0, t1 * t1));
             }
-            fnew += (double)fc - (double)fcc;
             jh2 += (double)jc - (double)jcc;
         }
     }
-    double in[2] = {fnew, jh2}, out[2];
-    if (grid_reduce<2>(in, v.partials, &st->tickets[TK_COST], out) && threadIdx.x == 0) {
+    double in[1] = {jh2}, out[1];
+    if (grid_reduce<1>(in, v.partials, &st->tickets[TK_COST], out) && threadIdx.x == 0) {
         // pose factors: k_factor_eval ran just before
         const bool fac = v.n_fac > 0;
-        lm_decide(st, active, 0.5 * out[0] + (fac ? st->fac_cost_new : 0.0), out[1] + (fac ? st->fac_jh2 : 0.0));
+        lm_decide(st, active, st->F_res + (fac ? st->fac_cost_new : 0.0), out[0] + (fac ? st->fac_jh2 : 0.0));
         if (use_cond) cudaGraphSetConditional(lm_cond, st->lm_active ? 1u : 0u);
     }
 }
@@ -783,6 +770,9 @@ __global__ void k_commit(Views<float> v) {
     const float4* cs = reinterpret_cast<const float4*>(v.cam_pre_new);
     float4* cd = reinterpret_cast<float4*>(v.cam_pre);
     for (size_t i = tid; i < (size_t)v.n_cams * (CP_STRIDE / 4); i += nth) cd[i] = cs[i];
+    const float4* ls = reinterpret_cast<const float4*>(v.cam_lo_new);
+    float4* ld = reinterpret_cast<float4*>(v.cam_lo);
+    for (size_t i = tid; i < (size_t)v.n_cams * (CLO_STRIDE / 4); i += nth) ld[i] = ls[i];
     for (size_t i = tid; i < (size_t)v.n_cams * CL_STRIDE; i += nth) v.cam_lin[i] = 0.0;
     float4* ch = reinterpret_cast<float4*>(v.cam_H);
     for (size_t i = tid; i < (size_t)v.n_cams * (CH_STRIDE / 4); i += nth) ch[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);

@@ -34,6 +34,9 @@ constexpr int LONG_RUN = 32;
 // Camera record (floats), written once per parameter change (FP64 math, FP32 store).
 enum : int { CP_R = 0, CP_T = 9, CP_F = 12, CP_K1 = 13, CP_K2 = 14, CP_PAD = 15,
              CP_JL = 16, CP_STRIDE = 32 };
+// Camera low-order record (floats): the rounding errors of R, t, f, k1, k2 at the
+// offsets CP_R .. CP_K2 of the camera record, for double-float residuals.
+enum : int { CLO_STRIDE = 16 };
 // Camera direction record (floats): phi = J_l(w) d_w (3), d_t (3), d_intr (3), pad.
 enum : int { CD_PHI = 0, CD_T = 3, CD_I = 6, CD_STRIDE = 12 };
 // Camera matvec accumulator (floats): sum (R X) x u (3), sum u (3), intrinsic part (3), pad.
@@ -59,6 +62,7 @@ struct DevOptions {
     int32_t loss;      // robust loss: 0 squared, 1 Huber, 2 Cauchy
     double loss_scale;
     int64_t wait_ns;   // limit on each grid-wide wait of the persistent PCG kernels
+    int32_t res_df;    // mixed form: residuals in double-float arithmetic (else FP32)
 };
 
 // Layout-compatible with ba_iter_stat of the public header.
@@ -68,7 +72,8 @@ struct IterRec {
     int64_t t_ns;
 };
 
-enum : int { TK_LIN = 0, TK_COST, TK_PRE, TK_DIR, TK_MV, TK_UPD, TK_CAND, TK_MISC, TK_FAC, TK_FACEV, TK_COUNT = 16 };
+enum : int { TK_LIN = 0, TK_COST, TK_PRE, TK_DIR, TK_MV, TK_UPD, TK_CAND, TK_MISC, TK_FAC, TK_FACEV, TK_RES,
+             TK_COUNT = 16 };
 
 struct DevState {
     DevOptions opt;
@@ -77,6 +82,8 @@ struct DevState {
     // pose factors: 1/2 sum |r_f|^2 at the linearisation point and at the candidate,
     // and |J_f h|^2 (written by the factor kernels, added by the observation kernels)
     double fac_cost, fac_cost_new, fac_jh2;
+    // mixed form: 1/2 sum rho(|r|^2) of the observations at the candidate (k_residual)
+    double F_res;
     // Per-iteration sums, spread over NSLOT slots (block b adds into slot b % NSLOT,
     // one 128-byte line each) so concurrent atomics do not queue on one address.
     double acc_mv[NSLOT * SLOT_STRIDE];   // k = 0: |J p|^2, k = 1: p^T D p
@@ -122,6 +129,11 @@ struct Views {
     // evaluation rounds afresh: the rounding then enters F and F' alike instead of
     // adding a one-sided cost to every candidate.  nullptr in the plain form.
     double *xm, *xm_new;
+    // Mixed form: low-order camera records (CLO_STRIDE floats, at x and at x') and the
+    // observations' residuals in solver order ([n_obs][2], k_residual), which the
+    // linearisation reads.  nullptr in the plain form.
+    float *cam_lo, *cam_lo_new;
+    float* rbuf;
     // camera records
     float *cam_pre, *cam_pre_new, *cam_dir, *cam_acc;
     float* pc;        // camera part of the PCG direction, double-buffered [2][pc_stride]

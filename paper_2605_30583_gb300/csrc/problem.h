@@ -28,6 +28,7 @@ struct Layout {
     size_t blk_tile, blk_cam_off, blk_cams, pslots;
     size_t long_off, long_run, short_start;
     size_t xm, xm_new;                   // mixed form: FP64 master parameters (0 in the plain form)
+    size_t cam_lo, cam_lo_new, rbuf;     // mixed form: low-order camera records, residuals
     size_t cam_pre, cam_pre_new, cam_dir, cam_acc, pc, cam_lin, cam_H, cam64, cam64_new, cam_H64, pt_H, Minv_c, Minv_p, jac, res, obs_w,
         staging;
     size_t fac_cam, fac_meas, fac_sqrt, fac_J;

@@ -54,15 +54,16 @@ __device__ __forceinline__ TileRange tile_range(const Views<float>& v, int tile)
     return r;
 }
 
-// The tile's observation keys (and pixels) and long-run table into shared memory:
-// sKey[i] / sUV[i] of observation lo + i, sRun[3 r + k] of long run l0 + r.
+// The tile's observation keys (and a float pair per observation, e.g. its residual)
+// and long-run table into shared memory: sKey[i] / sUV[i] of observation lo + i,
+// sRun[3 r + k] of long run l0 + r.
 template <int TB, bool UV>
 __device__ __forceinline__ void stage_obs(const Views<float>& v, const TileRange& T, uint32_t* sKey, float2* sUV,
-                                          uint32_t* sRun) {
+                                          uint32_t* sRun, const float* pairs = nullptr) {
     const uint32_t n = T.hi - T.lo;
     for (uint32_t i = threadIdx.x; i < n; i += TB) {
         sKey[i] = __ldg(v.obs_key + T.lo + i);
-        if (UV) sUV[i] = __ldg(reinterpret_cast<const float2*>(v.obs_uv) + T.lo + i);
+        if (UV) sUV[i] = __ldg(reinterpret_cast<const float2*>(pairs) + T.lo + i);
     }
     for (uint32_t i = threadIdx.x; i < 3 * T.nl; i += TB) sRun[i] = __ldg(v.long_run + 3 * (size_t)T.l0 + i);
 }
@@ -510,14 +511,13 @@ struct LinObs {
     float r0, r1, j0[9], j1[9], jx0[3], jx1[3];
 };
 
-// Residual and Jacobian rows of one observation (J_w[:,k] = A (J_l[:,k] x RX)).
-__device__ __forceinline__ LinObs lin_obs(const Cam& cam, const float (&JL)[9], float4 X, float u0, float u1,
-                                          float eps) {
+// Jacobian rows of one observation (J_w[:,k] = A (J_l[:,k] x RX)) and its residual r
+// (from k_residual).
+__device__ __forceinline__ LinObs lin_obs(const Cam& cam, const float (&JL)[9], float4 X, float2 r, float eps) {
     LinObs o;
     const Geo g = project_geo(cam, X.x, X.y, X.z, eps);
-    const float fs = cam.f * g.s;
-    o.r0 = fmaf(fs, g.p[0], -u0);
-    o.r1 = fmaf(fs, g.p[1], -u1);
+    o.r0 = r.x;
+    o.r1 = r.y;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float w0 = JL[k], w1 = JL[3 + k], w2 = JL[6 + k];
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
     if (mode == 1 && v.st->relin == 0) return;
     extern __shared__ __align__(16) unsigned char dsm[];
     uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);             // [key_cap]
-    float2* sUV = reinterpret_cast<float2*>(sKey + key_cap);       // [key_cap]
+    float2* sUV = reinterpret_cast<float2*>(sKey + key_cap);       // [key_cap] residuals (k_residual)
     uint32_t* sRun = reinterpret_cast<uint32_t*>(sUV + key_cap);   // [3 key_cap / LONG_RUN]
     __shared__ float4 sX4[TILE_PTS];
     __shared__ float sG[3 * TILE_PTS], sH[PH_STRIDE * TILE_PTS];   // J_p^T W r, J_p^T W J_p (upper)
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
             sX4[i] = make_float4(v.x[T.base + 3 * i], v.x[T.base + 3 * i + 1], v.x[T.base + 3 * i + 2], 0.0f);
         for (int i = threadIdx.x; i < 3 * TILE_PTS; i += TB) sG[i] = 0.0f;
         for (int i = threadIdx.x; i < PH_STRIDE * TILE_PTS; i += TB) sH[i] = 0.0f;
-        stage_obs<TB, true>(v, T, sKey, sUV, sRun);
+        stage_obs<TB, true>(v, T, sKey, sUV, sRun, v.rbuf);
         if (threadIdx.x == 0) s_next = 0u;
         __syncthreads();
         // long runs: camera-uniform steps of 32 observations
@@ -656,8 +656,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
             for (uint32_t off = lane; off < len; off += 32) {
                 const uint32_t i = start + off, j = T.lo + i;
                 const uint32_t slot = sKey[i] & 0xffu;
-                const float2 uv = sUV[i];
-                LinObs o = lin_obs(cam, JL, sX4[slot], uv.x, uv.y, eps);
+                LinObs o = lin_obs(cam, JL, sX4[slot], sUV[i], eps);
                 lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sG, sH, cs, cc);
             }
             int idx;
@@ -691,8 +690,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
                     cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
                     load_jl(v.cam_pre + (size_t)c * CP_STRIDE, JL);
                 }
-                const float2 uv = sUV[j - T.lo];
-                LinObs o = lin_obs(cam, JL, sX4[slot], uv.x, uv.y, eps);
+                LinObs o = lin_obs(cam, JL, sX4[slot], sUV[j - T.lo], eps);
                 lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sG, sH, cs, cc);
             }
             if (cur != NO_CAM) flush_lin_global(v, cur, acc);
@@ -721,18 +719,18 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
 }
 
 // ------------------------------------------------------------ candidate evaluation ---
-// F' = 1/2 sum rho(|r(x')|^2) and |J(x) h|^2 (weighted at x); the last block applies the
-// LM rule of Sec. V (lm_decide).  Never gated: its last block sets the LM loop flag.
+// |J(x) h|^2 (weighted at x); with F' = 1/2 sum rho(|r(x')|^2) from k_residual, the last
+// block applies the LM rule of Sec. V (lm_decide).  Never gated: its last block sets the
+// LM loop flag.
 constexpr int TE_TB = 128;
 
 struct EvalCam {
-    Cam cn, co;   // records at x' and at x
+    Cam co;       // record at x
     float dir[9]; // direction record of h (k_candidate)
 };
 
 __device__ __forceinline__ EvalCam load_eval_cam(const Views<float>& v, uint32_t c) {
     EvalCam e;
-    e.cn = load_cam(v.cam_pre_new + (size_t)c * CP_STRIDE);
     e.co = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
     const float4* d4 = reinterpret_cast<const float4*>(v.cam_dir + (size_t)c * CD_STRIDE);
     const float4 a = __ldcg(d4), b = __ldcg(d4 + 1), cc = __ldcg(d4 + 2);
@@ -741,23 +739,15 @@ __device__ __forceinline__ EvalCam load_eval_cam(const Views<float>& v, uint32_t
     return e;
 }
 
-__device__ __forceinline__ void eval_obs(const Views<float>& v, const EvalCam& e, const float4* sXn,
-                                         const float4* sXo, const float4* sHp, uint32_t j, uint32_t slot, float2 uv,
-                                         float eps, int loss, float lscale, float& fs_, float& fc_, float& js_,
+__device__ __forceinline__ void eval_obs(const Views<float>& v, const EvalCam& e, const float4* sXo,
+                                         const float4* sHp, uint32_t j, uint32_t slot, float eps, int loss, float& js_,
                                          float& jc_) {
-    const float4 xn = sXn[slot], xo = sXo[slot], hp = sHp[slot];
-    float r0, r1;
-    project_residual(e.cn, xn.x, xn.y, xn.z, eps, uv.x, uv.y, r0, r1);
+    const float4 xo = sXo[slot], hp = sHp[slot];
     const Geo g = project_geo(e.co, xo.x, xo.y, xo.z, eps);
     float t0, t1;
     jdir(g, e.co, e.dir, hp.x, hp.y, hp.z, t0, t1);
-    if (loss) {   // F' = 1/2 sum rho(|r'|^2); |J h|^2 weighted at x
-        kahan_add(fs_, fc_, loss_rho(fmaf(r0, r0, r1 * r1), loss, lscale));
-        kahan_add(js_, jc_, __ldg(v.obs_w + j) * fmaf(t0, t0, t1 * t1));
-    } else {
-        kahan_add(fs_, fc_, fmaf(r0, r0, r1 * r1));
-        kahan_add(js_, jc_, fmaf(t0, t0, t1 * t1));
-    }
+    // |J h|^2 weighted at x
+    kahan_add(js_, jc_, (loss ? __ldg(v.obs_w + j) : 1.0f) * fmaf(t0, t0, t1 * t1));
 }
 
 // Four CTAs per SM (at most 128 registers per thread).
@@ -765,26 +755,23 @@ template <int TB>
 __global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle lm_cond, int use_cond, int key_cap) {
     extern __shared__ __align__(16) unsigned char dsm[];
     uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);             // [key_cap]
-    float2* sUV = reinterpret_cast<float2*>(sKey + key_cap);       // [key_cap]
-    uint32_t* sRun = reinterpret_cast<uint32_t*>(sUV + key_cap);   // [3 key_cap / LONG_RUN]
-    __shared__ float4 sXn[TILE_PTS], sXo[TILE_PTS], sHp[TILE_PTS];   // x', x and h of the tile's points
+    uint32_t* sRun = sKey + key_cap;                               // [3 key_cap / LONG_RUN]
+    __shared__ float4 sXo[TILE_PTS], sHp[TILE_PTS];                // x and h of the tile's points
     __shared__ unsigned int s_next;
     DevState* st = v.st;
     const int active = st->lm_active;
     const float eps = (float)st->opt.eps;
     const int loss = st->opt.loss;
-    const float lscale = (float)st->opt.loss_scale;
     const int lane = threadIdx.x & 31;
-    float fs_ = 0.0f, fc_ = 0.0f, js_ = 0.0f, jc_ = 0.0f;   // compensated F' and |J h|^2
+    float js_ = 0.0f, jc_ = 0.0f;   // compensated |J h|^2
     for (int tile = blockIdx.x; active && tile < v.n_tiles; tile += gridDim.x) {
         const TileRange T = tile_range(v, tile);
         for (int i = threadIdx.x; i < T.npt; i += TB) {
             const size_t e = T.base + 3 * i;
-            sXn[i] = make_float4(v.x_new[e], v.x_new[e + 1], v.x_new[e + 2], 0.0f);
             sXo[i] = make_float4(v.x[e], v.x[e + 1], v.x[e + 2], 0.0f);
             sHp[i] = make_float4(v.h[e], v.h[e + 1], v.h[e + 2], 0.0f);
         }
-        stage_obs<TB, true>(v, T, sKey, sUV, sRun);
+        stage_obs<TB, false>(v, T, sKey, nullptr, sRun);
         if (threadIdx.x == 0) s_next = 0u;
         __syncthreads();
         for (;;) {
@@ -796,8 +783,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle 
             const EvalCam e = load_eval_cam(v, sRun[3 * r + 2]);
             for (uint32_t off = lane; off < len; off += 32) {
                 const uint32_t i = start + off;
-                eval_obs(v, e, sXn, sXo, sHp, T.lo + i, sKey[i] & 0xffu, sUV[i], eps, loss, lscale, fs_, fc_, js_,
-                         jc_);
+                eval_obs(v, e, sXo, sHp, T.lo + i, sKey[i] & 0xffu, eps, loss, js_, jc_);
             }
         }
         {
@@ -813,16 +799,16 @@ __global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle 
                     cur = c;
                     e = load_eval_cam(v, c);
                 }
-                eval_obs(v, e, sXn, sXo, sHp, j, key & 0xffu, sUV[j - T.lo], eps, loss, lscale, fs_, fc_, js_, jc_);
+                eval_obs(v, e, sXo, sHp, j, key & 0xffu, eps, loss, js_, jc_);
             }
         }
         __syncthreads();   // the next tile's staging overwrites the points
     }
-    double in[2] = {(double)fs_ - (double)fc_, (double)js_ - (double)jc_}, out[2];
-    if (grid_reduce<2>(in, v.partials, &st->tickets[TK_COST], out) && threadIdx.x == 0) {
+    double in[1] = {(double)js_ - (double)jc_}, out[1];
+    if (grid_reduce<1>(in, v.partials, &st->tickets[TK_COST], out) && threadIdx.x == 0) {
         // pose factors: k_factor_eval ran just before
         const bool fac = v.n_fac > 0;
-        lm_decide(st, active, 0.5 * out[0] + (fac ? st->fac_cost_new : 0.0), out[1] + (fac ? st->fac_jh2 : 0.0));
+        lm_decide(st, active, st->F_res + (fac ? st->fac_cost_new : 0.0), out[0] + (fac ? st->fac_jh2 : 0.0));
         if (use_cond) cudaGraphSetConditional(lm_cond, st->lm_active ? 1u : 0u);
     }
 }
@@ -858,7 +844,8 @@ void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs) {
     if (stage_bytes(key_cap, true) > limit) return;
     L.tk_key_cap = key_cap;
     L.tn_smem = (int)stage_bytes(key_cap, false);
-    L.tl_smem = L.te_smem = (int)stage_bytes(key_cap, true);
+    L.tl_smem = (int)stage_bytes(key_cap, true);
+    L.te_smem = (int)stage_bytes(key_cap, false);
     const int bn = prepare(k_tile_normal<TN_TB>, TN_TB, L.tn_smem);
     const int bc = prepare(k_tile_cg<TN_TB>, TN_TB, L.tn_smem);
     const int bl = prepare(k_tile_linearize<TL_TB>, TL_TB, L.tl_smem);

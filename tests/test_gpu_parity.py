@@ -55,6 +55,26 @@ def test_residuals_match_oracle(B):
     assert abs(cost - ref_cost) <= 1e-5 * ref_cost
 
 
+def test_double_float_residuals_are_the_oracle_residuals_rounded(B):
+    """Residual arithmetic of the mixed form.  Default (double-float, ~48 bits): each
+    residual is the oracle's FP64 residual rounded to FP32, so it is within half an ulp
+    of itself plus the double-float error (a few 2^-48 of the ~500 px terms): bound
+    1.2e-7 |r| + 1e-8 px.  residual_precision 0 (FP32 arithmetic): the ~500 px terms
+    carry ~1e-4 px of error, so the same bound fails and the FP32 bar of the other tests
+    (2e-4 px + 1e-5 |r|) holds."""
+    prob = _ragged(19)
+    ref = O.residuals(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
+    p = _problem(B, prob)
+    _, r, _ = p.evaluate(residuals=True)
+    err = np.abs(r.double().cpu().numpy() - ref)
+    assert np.all(err <= 1.2e-7 * np.abs(ref) + 1e-8), err.max()
+    p.solve(max_lm_iters=0, residual_precision=0)   # writes the options
+    _, r32, _ = p.evaluate(residuals=True)
+    err32 = np.abs(r32.double().cpu().numpy() - ref)
+    assert np.all(err32 <= 2e-4 + 1e-5 * np.abs(ref))
+    assert err32.max() > 10 * err.max()
+
+
 def test_jacobian_matches_oracle(B):
     prob = _ragged(5)
     p = _problem(B, prob)
