@@ -49,7 +49,9 @@ typedef enum {
 } ba_status;
 
 typedef enum {
-    BA_PREC_MIXED = 0,   /* FP32 residuals, Jacobians, parameters and PCG vectors;
+    BA_PREC_MIXED = 0,   /* FP32 Jacobians, operator and PCG vectors; FP64 master
+                            parameters (the kernels read their FP32 rounding);
+                            double-float residuals (ba_options.residual_precision);
                             FP64 cost sums, PCG dot products and block inversions */
     BA_PREC_FP64 = 1     /* plain all-FP64 form: stored FP64 Jacobian, FP64 vectors,
                             per-observation atomics (the comparison baseline)      */
@@ -162,6 +164,8 @@ typedef struct {
 
 const char* ba_last_error(void);
 const char* ba_status_string(int32_t status);
+/* Version of the structs above: 2 since ba_options gained wait_timeout_ms and
+ * residual_precision (a caller built against version 1 passes a shorter struct). */
 int32_t ba_abi_version(void);
 
 /* Self-test of the bounded grid waits that every cooperative kernel of this library

@@ -393,7 +393,7 @@ const char* ba_status_string(int32_t s) {
     }
 }
 
-int32_t ba_abi_version(void) { return 1; }
+int32_t ba_abi_version(void) { return 2; }
 
 ba_status ba_selftest_wait_timeout(void* scratch, int32_t grid, int32_t timeout_ms, void* stream, int32_t* gave_up,
                                    int32_t* error_word) {

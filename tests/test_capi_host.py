@@ -37,7 +37,9 @@ def test_options_defaults_follow_the_paper(lib):
     o = binding.default_options()
     assert o.initial_trust_region == 100.0 and o.pcg_rel_tol == 1e-3      # Sec. VI settings
     assert o.max_lm_iters == 20 and o.max_pcg_iters == 50 and o.use_graph == 1
-    assert lib.ba_abi_version() == 1
+    # the build's own defaults: double-float residuals, LM stops once mu passes 1e16
+    assert o.residual_precision == 1 and o.max_mu == 1e16 and o.wait_timeout_ms == 2000
+    assert lib.ba_abi_version() == 2
 
 
 def _create(n_cams, n_pts, ci, pi, px, prec=0):
