@@ -773,11 +773,18 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
     if (p->precision == BA_PREC_MIXED) {
         ba_status pst = plan_persistent(p, sms);
         if (pst) return pst;
-        std::vector<uint32_t> toff((size_t)p->n_tiles + 1);
+        const size_t nt = (size_t)p->n_tiles;
+        std::vector<uint32_t> toff(nt + 1), loff(nt + 1), sst(nt);
         GBBA_CUDA(cudaMemcpy(toff.data(), p->vf.tile_off, 4 * toff.size(), cudaMemcpyDeviceToHost));
-        uint32_t most = 1;
-        for (int t = 0; t < p->n_tiles; ++t) most = std::max(most, toff[t + 1] - toff[t]);
-        plan_tile_kernels(p->L, p->n_tiles, sms, (int)most);
+        GBBA_CUDA(cudaMemcpy(loff.data(), p->vf.long_off, 4 * loff.size(), cudaMemcpyDeviceToHost));
+        GBBA_CUDA(cudaMemcpy(sst.data(), p->vf.short_start, 4 * sst.size(), cudaMemcpyDeviceToHost));
+        uint32_t most_long = 1, most_short = 1, most_runs = 1;
+        for (size_t t = 0; t < nt; ++t) {
+            most_long = std::max(most_long, sst[t] - toff[t]);
+            most_short = std::max(most_short, toff[t + 1] - sst[t]);
+            most_runs = std::max(most_runs, loff[t + 1] - loff[t]);
+        }
+        plan_tile_kernels(p->L, p->n_tiles, sms, (int)most_long, (int)most_short, (int)most_runs);
         GBBA_CUDA(cudaGetLastError());
     }
     p->bound = true;

@@ -38,7 +38,9 @@ struct LaunchCfg {
     int tn_grid = 0;   // normal operator, one CTA per tile
     int tl_grid = 0;   // linearisation
     int te_grid = 0;   // candidate evaluation
-    int tk_key_cap = 0;                      // observations of the largest tile, rounded up to 32
+    // the largest tile's long runs, short-run observations and long-run observations
+    // (the compact observation table the tile kernels stage)
+    int tk_run_cap = 0, tk_short_cap = 0, tk_long_cap = 0;
     int tn_smem = 0, tl_smem = 0, te_smem = 0;   // their dynamic shared memory (staged observations)
 };
 
@@ -58,7 +60,7 @@ void launch_matvec(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, co
 void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use,
                    int cameras_only = 0);
 // tile kernels (tile_kernels.cu): launch shapes, then the launches
-void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs);
+void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_long_obs, int max_short_obs, int max_long_runs);
 void launch_tile_normal(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                         const float* zs, int use_beta);
 void launch_tile_eval(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle lm_cond, int use_cond);

@@ -5,7 +5,8 @@
 // their observations.  Inside a tile each camera's observations form one run, and the
 // runs of at least LONG_RUN observations come first (order.cu); on the large workloads
 // they hold over 90 % of the observations.  A CTA stages in shared memory, in one round
-// trip, the tile's points, its observation keys (and pixels where needed) and its table
+// trip, the tile's points, its compact observation table (a one-byte point slot per long-run
+// observation, the key of each short-run observation) and its table
 // of long runs {start, length, camera}; then
 //   * its warps take the long runs in turn and walk each in camera-uniform steps of 32
 //     consecutive observations: the camera sits in registers for the whole run, and the
@@ -54,9 +55,35 @@ __device__ __forceinline__ TileRange tile_range(const Views<float>& v, int tile)
     return r;
 }
 
-// The tile's observation keys (and a float pair per observation, e.g. its residual)
-// and long-run table into shared memory: sKey[i] / sUV[i] of observation lo + i,
-// sRun[3 r + k] of long run l0 + r.
+// Compact staging of a tile's observation table: sRun[3 r + k] of long run l0 + r, the
+// point slot (one byte) of each long-run observation (its camera is in the run's table
+// entry), and the whole key of each short-run observation.  `Caps` sizes the three
+// regions for the largest tile of each kind.
+struct Caps {
+    int run, shrt, lng;   // long runs, short-run observations, long-run observations
+};
+
+__host__ __device__ __forceinline__ size_t compact_bytes(const Caps& c) {
+    return 12 * (size_t)c.run + 4 * (size_t)c.shrt + (size_t)c.lng;
+}
+
+template <int TB>
+__device__ __forceinline__ void stage_compact(const Views<float>& v, const TileRange& T, const Caps& cap,
+                                              unsigned char* dsm, uint32_t*& sRun, uint32_t*& sShort,
+                                              uint8_t*& sSlot) {
+    sRun = reinterpret_cast<uint32_t*>(dsm);
+    sShort = sRun + 3 * cap.run;
+    sSlot = reinterpret_cast<uint8_t*>(sShort + cap.shrt);
+    const uint32_t nlo = T.ss - T.lo, n = T.hi - T.lo;
+    for (uint32_t i = threadIdx.x; i < n; i += TB) {
+        const uint32_t key = __ldg(v.obs_key + T.lo + i);
+        if (i < nlo) sSlot[i] = (uint8_t)(key & 0xffu);
+        else sShort[i - nlo] = key;
+    }
+    for (uint32_t i = threadIdx.x; i < 3 * T.nl; i += TB) sRun[i] = __ldg(v.long_run + 3 * (size_t)T.l0 + i);
+}
+
+
 template <int TB, bool UV>
 __device__ __forceinline__ void stage_obs(const Views<float>& v, const TileRange& T, uint32_t* sKey, float2* sUV,
                                           uint32_t* sRun, const float* pairs = nullptr) {
@@ -83,13 +110,13 @@ __device__ __forceinline__ void block_pair_sums(float sa, float ca, float sb, fl
 // points' direction step p = zs + beta p_prev is fused into the staging.  One CTA per
 // tile.
 
+// Eight CTAs per SM (at most 64 registers per thread; the compact staging keeps the
+// shared memory of a CTA under a sixth of the SM's).
 template <int TB>
-__global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_t* gate, const float* zs,
-                                                    int use_beta, int key_cap) {
+__global__ void __launch_bounds__(TB, 8) k_tile_normal(Views<float> v, const int32_t* gate, const float* zs,
+                                                       int use_beta, Caps cap) {
     if (gated_off(gate)) return;
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);   // [key_cap]
-    uint32_t* sRun = sKey + key_cap;                     // [3 key_cap / LONG_RUN]
     __shared__ float4 sX4[TILE_PTS], sP4[TILE_PTS];
     __shared__ float sQ[3 * TILE_PTS];
     __shared__ unsigned int s_next;
@@ -134,7 +161,9 @@ __global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_
             }
         }
     }
-    stage_obs<TB, false>(v, T, sKey, nullptr, sRun);
+    uint32_t *sRun, *sShort;
+    uint8_t* sSlot;
+    stage_compact<TB>(v, T, cap, dsm, sRun, sShort, sSlot);
     if (threadIdx.x == 0) s_next = 0u;
     __syncthreads();
     // long runs: camera-uniform steps of 32 observations
@@ -153,7 +182,7 @@ __global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_
         uint32_t off = lane;
         for (; off < len; off += 32) {
             const uint32_t j = T.lo + start + off;
-            const uint32_t slot = sKey[start + off] & 0xffu;
+            const uint32_t slot = sSlot[start + off];
             const float4 xp = sX4[slot], pp = sP4[slot];
             const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
             const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * slot, __ldg(v.obs_w + j))
@@ -176,7 +205,7 @@ __global__ void __launch_bounds__(TB) k_tile_normal(Views<float> v, const int32_
         Cam cam;
         float dir[9];
         for (uint32_t j = a; j < b; ++j) {
-            const uint32_t key = sKey[j - T.lo];
+            const uint32_t key = sShort[j - T.ss];
             const uint32_t c = key >> 8, slot = key & 0xffu;
             if (c != cur) {
                 if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
@@ -295,12 +324,10 @@ __global__ void __launch_bounds__(CGC_TB) k_cg_cameras(Views<float> v, const int
 }
 
 template <int TB>
-__global__ void __launch_bounds__(TB) k_tile_cg(Views<float> v, const int32_t* gate, int key_cap, CondHandle pcg_cond,
+__global__ void __launch_bounds__(TB, 6) k_tile_cg(Views<float> v, const int32_t* gate, Caps cap, CondHandle pcg_cond,
                                                 int use_cond) {
     if (gated_off(gate)) return;
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);   // [key_cap]
-    uint32_t* sRun = sKey + key_cap;                     // [3 key_cap / LONG_RUN]
     __shared__ float4 sX4[TILE_PTS], sP4[TILE_PTS];      // X and u of the tile's points
     __shared__ float sQ[3 * TILE_PTS];
     __shared__ unsigned int s_next;
@@ -393,7 +420,9 @@ __global__ void __launch_bounds__(TB) k_tile_cg(Views<float> v, const int32_t* g
             sQ[i] = mu * (Dd[t] * Z[t]);
         }
     }
-    stage_obs<TB, false>(v, T, sKey, nullptr, sRun);
+    uint32_t *sRun, *sShort;
+    uint8_t* sSlot;
+    stage_compact<TB>(v, T, cap, dsm, sRun, sShort, sSlot);
     if (threadIdx.x == 0) s_next = 0u;
     __syncthreads();
     // w = A u: long runs in camera-uniform steps, then the short tail by chunks
@@ -411,7 +440,7 @@ __global__ void __launch_bounds__(TB) k_tile_cg(Views<float> v, const int32_t* g
         for (int q = 0; q < 9; ++q) acc[q] = 0.0f;
         for (uint32_t off = lane; off < len; off += 32) {
             const uint32_t j = T.lo + start + off;
-            const uint32_t slot = sKey[start + off] & 0xffu;
+            const uint32_t slot = sSlot[start + off];
             const float4 xp = sX4[slot], pp = sP4[slot];
             const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
             const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * slot, __ldg(v.obs_w + j))
@@ -433,7 +462,7 @@ __global__ void __launch_bounds__(TB) k_tile_cg(Views<float> v, const int32_t* g
         Cam cam;
         float dir[9];
         for (uint32_t j = a; j < b; ++j) {
-            const uint32_t key = sKey[j - T.lo];
+            const uint32_t key = sShort[j - T.ss];
             const uint32_t c = key >> 8, slot = key & 0xffu;
             if (c != cur) {
                 if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
@@ -615,12 +644,10 @@ __device__ __forceinline__ void flush_lin_global(const Views<float>& v, uint32_t
 
 template <int TB>
 __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mode, float* res_out, float* jac_out,
-                                                       CondHandle lm_cond, int use_cond, int key_cap) {
+                                                       CondHandle lm_cond, int use_cond, Caps cap) {
     if (mode == 1 && v.st->relin == 0) return;
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);             // [key_cap]
-    float2* sUV = reinterpret_cast<float2*>(sKey + key_cap);       // [key_cap] residuals (k_residual)
-    uint32_t* sRun = reinterpret_cast<uint32_t*>(sUV + key_cap);   // [3 key_cap / LONG_RUN]
+    const float2* rbuf = reinterpret_cast<const float2*>(v.rbuf);   // residuals (k_residual)
     __shared__ float4 sX4[TILE_PTS];
     __shared__ float sG[3 * TILE_PTS], sH[PH_STRIDE * TILE_PTS];   // J_p^T W r, J_p^T W J_p (upper)
     __shared__ unsigned int s_next;
@@ -636,7 +663,9 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
             sX4[i] = make_float4(v.x[T.base + 3 * i], v.x[T.base + 3 * i + 1], v.x[T.base + 3 * i + 2], 0.0f);
         for (int i = threadIdx.x; i < 3 * TILE_PTS; i += TB) sG[i] = 0.0f;
         for (int i = threadIdx.x; i < PH_STRIDE * TILE_PTS; i += TB) sH[i] = 0.0f;
-        stage_obs<TB, true>(v, T, sKey, sUV, sRun, v.rbuf);
+        uint32_t *sRun, *sShort;
+        uint8_t* sSlot;
+        stage_compact<TB>(v, T, cap, dsm, sRun, sShort, sSlot);
         if (threadIdx.x == 0) s_next = 0u;
         __syncthreads();
         // long runs: camera-uniform steps of 32 observations
@@ -655,8 +684,8 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
             for (int k = 0; k < TL_ACC; ++k) acc[k] = 0.0f;
             for (uint32_t off = lane; off < len; off += 32) {
                 const uint32_t i = start + off, j = T.lo + i;
-                const uint32_t slot = sKey[i] & 0xffu;
-                LinObs o = lin_obs(cam, JL, sX4[slot], sUV[i], eps);
+                const uint32_t slot = sSlot[i];
+                LinObs o = lin_obs(cam, JL, sX4[slot], __ldg(rbuf + j), eps);
                 lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sG, sH, cs, cc);
             }
             int idx;
@@ -682,7 +711,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
             Cam cam;
             float JL[9];
             for (uint32_t j = a; j < b; ++j) {
-                const uint32_t key = sKey[j - T.lo];
+                const uint32_t key = sShort[j - T.ss];
                 const uint32_t c = key >> 8, slot = key & 0xffu;
                 if (c != cur) {
                     if (cur != NO_CAM) flush_lin_global(v, cur, acc);
@@ -690,7 +719,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
                     cam = load_cam(v.cam_pre + (size_t)c * CP_STRIDE);
                     load_jl(v.cam_pre + (size_t)c * CP_STRIDE, JL);
                 }
-                LinObs o = lin_obs(cam, JL, sX4[slot], sUV[j - T.lo], eps);
+                LinObs o = lin_obs(cam, JL, sX4[slot], __ldg(rbuf + j), eps);
                 lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sG, sH, cs, cc);
             }
             if (cur != NO_CAM) flush_lin_global(v, cur, acc);
@@ -752,10 +781,8 @@ __device__ __forceinline__ void eval_obs(const Views<float>& v, const EvalCam& e
 
 // Four CTAs per SM (at most 128 registers per thread).
 template <int TB>
-__global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle lm_cond, int use_cond, int key_cap) {
+__global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle lm_cond, int use_cond, Caps cap) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint32_t* sKey = reinterpret_cast<uint32_t*>(dsm);             // [key_cap]
-    uint32_t* sRun = sKey + key_cap;                               // [3 key_cap / LONG_RUN]
     __shared__ float4 sXo[TILE_PTS], sHp[TILE_PTS];                // x and h of the tile's points
     __shared__ unsigned int s_next;
     DevState* st = v.st;
@@ -771,7 +798,9 @@ __global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle 
             sXo[i] = make_float4(v.x[e], v.x[e + 1], v.x[e + 2], 0.0f);
             sHp[i] = make_float4(v.h[e], v.h[e + 1], v.h[e + 2], 0.0f);
         }
-        stage_obs<TB, false>(v, T, sKey, nullptr, sRun);
+        uint32_t *sRun, *sShort;
+        uint8_t* sSlot;
+        stage_compact<TB>(v, T, cap, dsm, sRun, sShort, sSlot);
         if (threadIdx.x == 0) s_next = 0u;
         __syncthreads();
         for (;;) {
@@ -783,7 +812,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle 
             const EvalCam e = load_eval_cam(v, sRun[3 * r + 2]);
             for (uint32_t off = lane; off < len; off += 32) {
                 const uint32_t i = start + off;
-                eval_obs(v, e, sXo, sHp, T.lo + i, sKey[i] & 0xffu, eps, loss, js_, jc_);
+                eval_obs(v, e, sXo, sHp, T.lo + i, sSlot[i], eps, loss, js_, jc_);
             }
         }
         {
@@ -793,7 +822,7 @@ __global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle 
             uint32_t cur = NO_CAM;
             EvalCam e;
             for (uint32_t j = a; j < b; ++j) {
-                const uint32_t key = sKey[j - T.lo];
+                const uint32_t key = sShort[j - T.ss];
                 const uint32_t c = key >> 8;
                 if (c != cur) {
                     cur = c;
@@ -813,12 +842,6 @@ __global__ void __launch_bounds__(TB, 4) k_tile_eval(Views<float> v, CondHandle 
     }
 }
 
-// Dynamic shared memory of the staged observations for a key capacity (keys, pixels
-// where `uv`, and the long-run table).
-size_t stage_bytes(int key_cap, bool uv) {
-    return (size_t)key_cap * (uv ? 12 : 4) + 12 * (size_t)(key_cap / LONG_RUN + 1);
-}
-
 template <typename K>
 int prepare(K kernel, int tb, size_t dyn) {
     if (ensure_dynamic_smem((const void*)kernel, (int)dyn) != cudaSuccess) {
@@ -835,17 +858,17 @@ int prepare(K kernel, int tb, size_t dyn) {
 
 }  // namespace
 
-// The tile kernels stage a whole tile's observations; a problem whose largest tile does
-// not fit in shared memory keeps the per-thread-chunk kernels (all grids 0).
-void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs) {
+// The tile kernels stage a whole tile's observation table (compact form); a problem
+// whose largest tile does not fit in shared memory keeps the per-thread-chunk kernels
+// (all grids 0).
+void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_long_obs, int max_short_obs, int max_long_runs) {
     L.tn_grid = L.tl_grid = L.te_grid = 0;
-    const int key_cap = (std::max(1, max_tile_obs) + 31) / 32 * 32;
-    const size_t limit = 160 * 1024;
-    if (stage_bytes(key_cap, true) > limit) return;
-    L.tk_key_cap = key_cap;
-    L.tn_smem = (int)stage_bytes(key_cap, false);
-    L.tl_smem = (int)stage_bytes(key_cap, true);
-    L.te_smem = (int)stage_bytes(key_cap, false);
+    L.tk_run_cap = std::max(1, max_long_runs);
+    L.tk_short_cap = std::max(1, max_short_obs);
+    L.tk_long_cap = (std::max(1, max_long_obs) + 15) / 16 * 16;
+    const Caps cap{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap};
+    if (compact_bytes(cap) > 160 * 1024) return;
+    L.tn_smem = L.tl_smem = L.te_smem = (int)compact_bytes(cap);
     const int bn = prepare(k_tile_normal<TN_TB>, TN_TB, L.tn_smem);
     const int bc = prepare(k_tile_cg<TN_TB>, TN_TB, L.tn_smem);
     const int bl = prepare(k_tile_linearize<TL_TB>, TL_TB, L.tl_smem);
@@ -859,24 +882,27 @@ void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_tile_obs) {
 
 void launch_tile_normal(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                         const float* zs, int use_beta) {
-    k_tile_normal<TN_TB><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, zs, use_beta, L.tk_key_cap);
+    k_tile_normal<TN_TB><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, zs, use_beta,
+                                                             Caps{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap});
 }
 
 void launch_cg_round(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate, CondHandle c,
                      int use) {
     k_cg_cameras<<<std::max(1, (v.n_cams + CGC_CAMS - 1) / CGC_CAMS), CGC_TB, 0, s>>>(v, gate);
     launch_factor_matvec(v, L, s, gate, v.z, 0);   // pose factors: |J_f u|^2 before the round's reduction
-    k_tile_cg<TN_TB><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, L.tk_key_cap, c, use);
+    k_tile_cg<TN_TB><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, Caps{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap},
+                                                         c, use);
 }
 
 void launch_tile_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode, float* res_out,
                            float* jac_out, CondHandle lm_cond, int use_cond) {
     k_tile_linearize<TL_TB><<<L.tl_grid, TL_TB, L.tl_smem, s>>>(v, mode, res_out, jac_out, lm_cond, use_cond,
-                                                                 L.tk_key_cap);
+                                                                 Caps{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap});
 }
 
 void launch_tile_eval(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle lm_cond, int use_cond) {
-    k_tile_eval<TE_TB><<<L.te_grid, TE_TB, L.te_smem, s>>>(v, lm_cond, use_cond, L.tk_key_cap);
+    k_tile_eval<TE_TB><<<L.te_grid, TE_TB, L.te_smem, s>>>(v, lm_cond, use_cond,
+                                                           Caps{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap});
 }
 
 }  // namespace gbba
