@@ -191,6 +191,16 @@ def pcg_iter_tile_model(prob):
     return 4 * prob.n_obs + 180 * prob.n_pts + 1048 * prob.n_cams
 
 
+def lm_iter_model(prob):
+    """Algorithmic bytes of the LM-level work of one LM iteration (besides its PCG
+    iterations): the linearisation (key, pixel and residual per observation; X read, g
+    and J_p^T J_p written per point; camera record, g and the J_c^T J_c triangle per
+    camera), the preconditioner (blocks read, inverses written), the candidate and its
+    evaluation (key per observation, x, h, x' per unknown, records per camera)."""
+    n = 9 * prob.n_cams + 3 * prob.n_pts
+    return (20 + 12) * prob.n_obs + 48 * prob.n_pts + 240 * prob.n_cams + 48 * prob.n_pts + 516 * prob.n_cams + 44 * n
+
+
 def pcg_iter_model(prob):
     """Algorithmic bytes and FP32 flops of one PCG iteration (recomputed Jacobian).
 
@@ -750,6 +760,12 @@ def run_batched(args, binding, synth, torch, dev, stream, flush, rank=0):
         sp.close()
     fin = np.array([r.final_cost for r in res])
     t = sum(ms) / len(ms)
+    # algorithmic bytes of the whole batch solve: every problem's PCG iterations at the
+    # per-iteration model and its LM iterations at lm_iter_model
+    nbytes = sum(r.pcg_iters_total * pcg_iter_model(q)[0] + r.lm_iters * lm_iter_model(q) for r, q in zip(res, probs))
+    peaks = load_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = nbytes / (t / 1e3) / 1e9
     out = {"workload": f"512 problems, {sum(q.n_cams for q in probs)} cameras, {sum(q.n_pts for q in probs)} points, "
                        f"{sum(q.n_obs for q in probs)} observations, 20 LM x <=50 PCG each",
            "ms_per_batch_solve": t, "step_ms": ms, "problems_per_s": 512 / (t / 1e3),
@@ -757,7 +773,12 @@ def run_batched(args, binding, synth, torch, dev, stream, flush, rank=0):
            "schedule": sched, "autotune_trials": trials,
            "sequential_single_solver_ms": seq_ms,
            "final_cost_max_rel_diff_vs_single_solver": float(np.max(np.abs(fin - seq_fin) / seq_fin)),
-           "status_nonzero": int(sum(r.status != 0 for r in res))}
+           "status_nonzero": int(sum(r.status != 0 for r in res)),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "algorithmic_bytes": nbytes, "traffic": None,
+                        "traffic_note": "one ncu capture of a whole batch solve read 16.2 GB and wrote 11.1 GB of DRAM "
+                                        "(profiles/k_batch_solve_batch512.md)",
+                        "kernel": "k_batch_solve (one CTA per problem at a time, whole batch in one launch)"}}
     b.close()
     return out
 

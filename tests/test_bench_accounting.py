@@ -62,6 +62,14 @@ def test_tile_pcg_iteration_bytes():
     assert bench.pcg_iter_tile_model(_P(0, 0, 1)) == 4
 
 
+def test_lm_iteration_bytes():
+    # per observation 32 B (linearisation 20, evaluation 12); per point 48 + 48 + 3 x 44;
+    # per camera 240 + 516 + 9 x 44
+    assert bench.lm_iter_model(_P(0, 0, 1)) == 32
+    assert bench.lm_iter_model(_P(0, 1, 0)) == 48 + 48 + 132
+    assert bench.lm_iter_model(_P(1, 0, 0)) == 240 + 516 + 396
+
+
 def test_oracle_subsample_keeps_every_strided_point_with_all_its_observations():
     import numpy as np
     from paper_2605_30583_gb300 import synth
