@@ -864,7 +864,7 @@ ba_status ba_evaluate(ba_problem* p, double* cost_out, void* residuals, void* ja
     GBBA_CUDA(cudaMemcpyAsync(&dst->opt.retract, plain, sizeof(plain), cudaMemcpyHostToDevice, p->stream));
     if (p->precision == BA_PREC_MIXED) {
         launch_camera_precompute(p->vf, p->L, p->stream);
-        launch_residual(p->vf, p->L, p->stream, 0);
+        launch_residual(p->vf, p->L, p->stream, 0, 1);   // evaluation: the squared loss
         launch_linearize(p->vf, p->L, p->stream, 2, (float*)residuals, (float*)jacobian, 0, 0);
     } else {
         launch64_camera_precompute(p->vd, p->L, p->stream);

@@ -105,12 +105,12 @@ __device__ __forceinline__ CamDF load_cam_df(const float* __restrict__ rec, cons
     return c;
 }
 
-// The Snavely residual of Sec. VI-A in df arithmetic, rounded to FP32 at the end:
-// P = R X + t, d = P.z -+ eps (d_safe), p = -P.xy / d, s = 1 + k1 |p|^2 + k2 |p|^4,
-// r = f s p - u.  Its error is a few units of 2^-48 of the ~500 px terms, so the FP32
-// result is the exact residual correctly rounded to within an ulp of itself.
+// The Snavely residual of Sec. VI-A in df arithmetic: P = R X + t, d = P.z -+ eps
+// (d_safe), p = -P.xy / d, s = 1 + k1 |p|^2 + k2 |p|^4, r = f s p - u.  Its error is a
+// few units of 2^-48 of the ~500 px terms, so rounded to FP32 it is the exact residual
+// to within an ulp of itself.
 __device__ __forceinline__ void residual_df(const CamDF& c, const DF (&X)[3], float eps, float u0, float u1,
-                                            float& r0, float& r1) {
+                                            DF& r0, DF& r1) {
     DF P[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -125,8 +125,8 @@ __device__ __forceinline__ void residual_df(const CamDF& c, const DF (&X)[3], fl
     const DF n2 = df_add(df_mul(p0, p0), df_mul(p1, p1));
     const DF s = df_add_f(df_mul(n2, df_add(c.k1, df_mul(c.k2, n2))), 1.0f);
     const DF fs = df_mul(c.f, s);
-    r0 = df_to_float(df_add_f(df_mul(fs, p0), -u0));
-    r1 = df_to_float(df_add_f(df_mul(fs, p1), -u1));
+    r0 = df_add_f(df_mul(fs, p0), -u0);
+    r1 = df_add_f(df_mul(fs, p1), -u1);
 }
 
 }  // namespace gbba

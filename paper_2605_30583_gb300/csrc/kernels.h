@@ -44,9 +44,10 @@ struct LaunchCfg {
     int tn_smem = 0, tl_smem = 0, te_smem = 0;   // their dynamic shared memory (staged observations)
 };
 
-// residual pass of the mixed form (residual.cu): at x (at_candidate 0) or at x' (1,
-// also F' into the state for the LM decision)
-void launch_residual(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int at_candidate);
+// residual pass of the mixed form (residual.cu): r at x (at_candidate 0) or at x' (1),
+// and the cost into st->F_res (squared: the squared loss whatever the options, as
+// ba_evaluate reports it)
+void launch_residual(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int at_candidate, int squared = 0);
 int occupancy_blocks_residual();
 
 // mixed precision (kernels_mixed.cu)

@@ -248,6 +248,9 @@ __global__ void k64_precond(V64 v, CondHandle pcg_cond, int use_cond) {
         st->rr = out[1];
         st->beta = 0.0;
         st->pcg_iter = 0;
+        // a non-finite r^T z means a non-finite gradient or block (a Jacobian that
+        // overflowed, e.g. a point at a camera centre): a numeric failure, not a stall
+        if (!isfinite(out[0]) || !isfinite(out[1])) st->status = 4;
         st->pcg_active = (out[1] > 0.0 && isfinite(out[0]) && st->opt.max_pcg > 0) ? 1 : 0;
         if (use_cond) cudaGraphSetConditional(pcg_cond, st->pcg_active ? 1u : 0u);
     }

@@ -202,7 +202,10 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
     double in[1] = {(double)cost - (double)costc}, out[1];
     if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_LIN], out) && threadIdx.x == 0) {
         DevState* st = v.st;
-        const double F = 0.5 * out[0] + (v.n_fac > 0 ? st->fac_cost : 0.0);   // pose factors: k_factor_linearize
+        // the cost is the residual pass's (k_residual, at these parameters); pose factors:
+        // k_factor_linearize.  After an accepted step the LM decision has already set F.
+        (void)out;
+        const double F = st->F_res + (v.n_fac > 0 ? st->fac_cost : 0.0);
         st->cost_out = F;
         if (mode == 0) {
             st->F = F;
@@ -211,8 +214,6 @@ __global__ void __launch_bounds__(TB, 6) k_linearize(Views<float> v, int mode, f
             if (!ok) st->status = 4;
             st->lm_active = (ok && F > 0.0 && st->opt.max_lm > 0) ? 1 : 0;
             if (use_cond) cudaGraphSetConditional(lm_cond, st->lm_active ? 1u : 0u);
-        } else if (mode == 1) {
-            st->F = F;
         }
     }
 }
@@ -352,6 +353,9 @@ __global__ void k_precond(Views<float> v, CondHandle pcg_cond, int use_cond, dou
         st->alpha = 0.0;
         st->pcg_iter = 0;
         for (int k = 0; k < NSLOT * SLOT_STRIDE; ++k) st->acc_mv[k] = st->acc_up[k] = 0.0;
+        // a non-finite r^T z means a non-finite gradient or block (a Jacobian that
+        // overflowed, e.g. a point at a camera centre): a numeric failure, not a stall
+        if (!isfinite(out[0]) || !isfinite(out[1])) st->status = 4;
         st->pcg_active = (out[1] > 0.0 && isfinite(out[0]) && st->opt.max_pcg > 0) ? 1 : 0;
         if (use_cond) cudaGraphSetConditional(pcg_cond, st->pcg_active ? 1u : 0u);
     }
@@ -1015,6 +1019,9 @@ __global__ void k_schur_start(Views<float> v, CondHandle pcg_cond, int use_cond)
         st->beta = 0.0;
         st->pcg_iter = 0;
         for (int k = 0; k < NSLOT * SLOT_STRIDE; ++k) st->acc_mv[k] = st->acc_up[k] = 0.0;
+        // a non-finite r^T z means a non-finite gradient or block (a Jacobian that
+        // overflowed, e.g. a point at a camera centre): a numeric failure, not a stall
+        if (!isfinite(out[0]) || !isfinite(out[1])) st->status = 4;
         st->pcg_active = (out[1] > 0.0 && isfinite(out[0]) && st->opt.max_pcg > 0) ? 1 : 0;
         if (use_cond) cudaGraphSetConditional(pcg_cond, st->pcg_active ? 1u : 0u);
     }

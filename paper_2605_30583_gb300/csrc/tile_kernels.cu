@@ -732,7 +732,10 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
     double in[1] = {(double)cs - (double)cc}, out[1];
     if (grid_reduce<1>(in, v.partials, &v.st->tickets[TK_LIN], out) && threadIdx.x == 0) {
         DevState* st = v.st;
-        const double F = 0.5 * out[0] + (v.n_fac > 0 ? st->fac_cost : 0.0);   // pose factors: k_factor_linearize
+        // the cost is the residual pass's (k_residual, at these parameters); pose factors:
+        // k_factor_linearize.  After an accepted step the LM decision has already set F.
+        (void)out;
+        const double F = st->F_res + (v.n_fac > 0 ? st->fac_cost : 0.0);
         st->cost_out = F;
         if (mode == 0) {
             st->F = F;
@@ -741,8 +744,6 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
             if (!ok) st->status = 4;
             st->lm_active = (ok && F > 0.0 && st->opt.max_lm > 0) ? 1 : 0;
             if (use_cond) cudaGraphSetConditional(lm_cond, st->lm_active ? 1u : 0u);
-        } else if (mode == 1) {
-            st->F = F;
         }
     }
 }

@@ -14,11 +14,15 @@ normalised image point is p = -P.xy / P.z (points in front of a camera have P.z 
 and the pixel is f * (1 + k1 |p|^2 + k2 |p|^4) * p.
 
 Workload recipe (all randomness from numpy's PCG64 seeded per problem):
-  * cameras on a ring of radius 5 in the z = 0 plane, evenly spaced in azimuth,
+  * cameras on a ring (radius 5 unless a configuration states another) in the z = 0 plane, evenly spaced in azimuth,
     each looking at the origin along its own -z axis, with world +z as "up";
   * f ~ U(500, 1000), k1, k2 ~ N(0, 0.01^2);
   * points ~ N(0, I3), redrawn while |X| > 3 so every camera sees every point at a
-    depth of at least 2 (the recipe keeps |P.z| >= 0.5 for every observation);
+    depth of at least 2 (the recipe keeps |P.z| >= 0.5 for every observation); or, for
+    a ring of radius R > 8 ("band"), points at a uniform azimuth, 2-8 units inside the
+    ring, height N(0, 1) clipped to 3 (the large workload: 13,000 cameras at radius 65
+    keep the 1,000-camera ring's spacing, so nearest cameras see a point with the same
+    parallax);
   * each point is seen by 2 + Poisson(lam) cameras (or 2 + Geometric with a given
     mean), clipped to the camera count, chosen either uniformly at random or as the
     cameras nearest to the point on the ring;
@@ -62,10 +66,14 @@ class Problem:
 CONFIGS = {
     "tiny": dict(n_cams=16, n_pts=1000, views=("poisson", 3.0), visibility="uniform", seed=1000),
     "medium": dict(n_cams=1000, n_pts=200_000, views=("poisson", 4.0), visibility="nearest", seed=1001),
-    "large": dict(n_cams=13_000, n_pts=4_500_000, views=("geometric", 4.4), visibility="nearest", seed=1002),
+    # 13,000 cameras at the medium workload's spacing (ring radius 65), points in a band
+    # 2-8 units inside the ring: every point meets its nearest cameras with the medium
+    # workload's parallax, as a large reconstruction's points meet theirs
+    "large": dict(n_cams=13_000, n_pts=4_500_000, views=("geometric", 4.4), visibility="nearest", seed=1002,
+                  ring_radius=65.0, scene="band"),
     "autograd": dict(n_cams=200, n_pts=50_000, views=("poisson", 4.0), visibility="nearest", seed=1004),
-    # the large workload's shape (points per camera, view counts, visibility) at 1/13 of
-    # its size: a case small enough for full profiler captures of the same tile structure
+    # the large workload's local shape (camera spacing, depths, points per camera, view
+    # counts, visibility) at 1/13 of its size: small enough for full profiler captures
     "large_shape": dict(n_cams=1000, n_pts=346_000, views=("geometric", 4.4), visibility="nearest", seed=1002),
 }
 
@@ -75,7 +83,7 @@ def _unit_vectors(rng: np.random.Generator, n: int) -> np.ndarray:
     return v / np.linalg.norm(v, axis=1, keepdims=True)
 
 
-def ring_cameras(n_cams: int) -> tuple[np.ndarray, np.ndarray]:
+def ring_cameras(n_cams: int, radius: float = RING_RADIUS) -> tuple[np.ndarray, np.ndarray]:
     """World-to-camera rotation matrices and translations of the inward-looking ring."""
     az = 2.0 * np.pi * np.arange(n_cams) / n_cams
     c, s = np.cos(az), np.sin(az)
@@ -83,7 +91,7 @@ def ring_cameras(n_cams: int) -> tuple[np.ndarray, np.ndarray]:
     y_cam = np.tile(np.array([0.0, 0.0, 1.0]), (n_cams, 1))      # world up
     x_cam = np.cross(y_cam, z_cam)
     R = np.stack([x_cam, y_cam, z_cam], axis=1)                  # rows are the camera axes
-    centres = RING_RADIUS * z_cam
+    centres = radius * z_cam
     t = -np.einsum("cij,cj->ci", R, centres)
     return R, t
 
@@ -98,7 +106,15 @@ def _pixels(R: np.ndarray, t: np.ndarray, intr: np.ndarray, X: np.ndarray) -> tu
     return scale[:, None] * xy, depth
 
 
-def _draw_points(rng: np.random.Generator, n: int) -> np.ndarray:
+def _draw_points(rng: np.random.Generator, n: int, scene: str = "cloud", radius: float = RING_RADIUS) -> np.ndarray:
+    if scene == "band":
+        # azimuth uniform, 2-8 units inside the ring, height N(0, 1) clipped to 3
+        az = rng.uniform(0.0, 2.0 * np.pi, n)
+        r = radius - rng.uniform(2.0, 8.0, n)
+        z = np.clip(rng.standard_normal(n), -MAX_POINT_RADIUS, MAX_POINT_RADIUS)
+        return np.stack([r * np.cos(az), r * np.sin(az), z], axis=1)
+    if scene != "cloud":
+        raise ValueError(scene)
     X = rng.standard_normal((n, 3))
     bad = np.linalg.norm(X, axis=1) > MAX_POINT_RADIUS
     while bad.any():
@@ -140,14 +156,15 @@ def _choose_cameras(rng, X, counts, n_cams, visibility) -> np.ndarray:
 
 
 def make_problem(n_cams: int, n_pts: int, views=("poisson", 3.0), visibility="uniform",
-                 seed: int = 0, noise_px: float = 1.0, perturb: bool = True,
+                 seed: int = 0, noise_px: float = 1.0, perturb: bool = True, ring_radius: float = RING_RADIUS,
+                 scene: str = "cloud",
                  name: str = "") -> Problem:
     rng = np.random.default_rng(seed)
-    R_gt, t_gt = ring_cameras(n_cams)
+    R_gt, t_gt = ring_cameras(n_cams, ring_radius)
     intr = np.stack([rng.uniform(500.0, 1000.0, n_cams),
                      0.01 * rng.standard_normal(n_cams),
                      0.01 * rng.standard_normal(n_cams)], axis=1)
-    X_gt = _draw_points(rng, n_pts)
+    X_gt = _draw_points(rng, n_pts, scene, ring_radius)
     counts = _view_counts(rng, n_pts, views, n_cams)
     cam_idx = _choose_cameras(rng, X_gt, counts, n_cams, visibility)
     pt_idx = np.repeat(np.arange(n_pts, dtype=np.int64), counts)

@@ -1,5 +1,6 @@
-"""The large workload (13,000 cameras, 4.5M points, ~29M observations, 2+Geometric(4.4)
-views, nearest-camera visibility) at full size, checked where the oracle can follow:
+"""The large workload (13,000 cameras on a ring of radius 65, 4.5M points in a band
+inside it, ~29M observations, 2+Geometric(4.4) nearest-camera views) at full size,
+checked where the oracle can follow:
 
 * residuals of a random sample of observations against the oracle's, one by one;
 * the damped normal operator on sampled points and cameras against the oracle's blocks
@@ -7,8 +8,8 @@ views, nearest-camera visibility) at full size, checked where the oracle can fol
 * the full LM solve against the plain all-FP64 GPU form of the same algorithm, which
   stands in for the oracle at this size (it matches the oracle to 1e-8 on the tiny
   workload and to ~1e-14 on the medium one; the oracle itself would need hours here):
-  the workload's own 20-iteration budget at the first step, and a 500-iteration solve
-  whose end point and continuation are held to the 1e-4 bar.
+  the workload's own 20-iteration budget, and both forms run to convergence, held to the
+  1e-4 bar and the chi^2 band of the maximum-likelihood optimum.
 """
 import numpy as np
 import pytest
@@ -109,16 +110,24 @@ def test_large_sampled_normal_operator(B, mixed, large):
     assert err.max() <= 1e-4, err.max()
 
 
+def _chi2(large):
+    # at the maximum-likelihood optimum 2F ~ chi^2 with m - n + 7 degrees of freedom (the
+    # 7-dimensional similarity gauge): F = (m - n + 7) / 2 +- 4 standard deviations
+    dof = 2 * large.n_obs - 9 * large.n_cams - 3 * large.n_pts + 7
+    return 0.5 * dof, 4.0 * np.sqrt(dof / 2.0)
+
+
+def _costs(r):
+    return [h["cost"] for h in r.history] + [r.final_cost]
+
+
 def test_large_solve_against_fp64_form(B, mixed, large):
     """The workload's own budget (20 LM x <= 50 PCG) on both forms.
 
-    At this size 20 LM iterations do not converge: both forms end a few per cent above
-    the noise floor and are still descending.  Their trajectories separate after the
-    first step, because PCG stops at its 50-iteration cap and a truncated Krylov iterate
-    depends on rounding: FP32 and FP64 steps differ by ~1e-4, which changes the next rho
-    and mu.  So the first LM step is compared at the parity bar, and the end of the solve
-    by where each form stands (statuses, monotone costs, both near the noise floor, and
-    within 1 % of each other)."""
+    The first three LM steps take the same decisions with the same PCG iteration counts
+    (within 2) and candidate costs within 1e-4; after 20 iterations both forms sit in
+    the chi^2 band of the maximum-likelihood optimum and within the 1e-4 bar of each
+    other, with monotone accepted costs."""
     opts = dict(max_lm_iters=20, max_pcg_iters=50)
     mixed.set_params(large.cams_init, large.pts_init)
     a = mixed.solve(**opts)
@@ -128,55 +137,40 @@ def test_large_solve_against_fp64_form(B, mixed, large):
     q.close()
     assert a.status == 0 and b.status == 0 and a.lm_iters == 20 and b.lm_iters == 20
     assert abs(a.initial_cost - b.initial_cost) <= 1e-6 * b.initial_cost
-    # first step: same PCG iteration count, same accepted cost
-    ha, hb = a.history[0], b.history[0]
-    assert ha["accepted"] and hb["accepted"] and ha["pcg_iters"] == hb["pcg_iters"]
-    assert abs(ha["cost_new"] - hb["cost_new"]) <= 1e-4 * hb["cost_new"]
+    for ha, hb in zip(a.history[:3], b.history[:3]):
+        assert ha["accepted"] == hb["accepted"] and abs(ha["pcg_iters"] - hb["pcg_iters"]) <= 2, (ha, hb)
+        assert abs(ha["cost_new"] - hb["cost_new"]) <= 1e-4 * hb["cost_new"], (ha, hb)
     for r in (a, b):
-        costs = [h["cost"] for h in r.history] + [r.final_cost]
-        assert all(x >= y for x, y in zip(costs, costs[1:]))
-    floor = 0.5 * (2 * large.n_obs - 9 * large.n_cams - 3 * large.n_pts + 7)   # chi^2 level at the optimum
-    assert floor < a.final_cost < 1.1 * floor and floor < b.final_cost < 1.1 * floor, (a.final_cost, b.final_cost)
+        c = _costs(r)
+        assert all(x >= y for x, y in zip(c, c[1:]))
+    assert abs(a.final_cost - b.final_cost) <= 1e-4 * b.final_cost, (a.final_cost, b.final_cost)
+    centre, band = _chi2(large)
+    assert abs(a.final_cost - centre) <= band and abs(b.final_cost - centre) <= band, (a.final_cost, b.final_cost)
 
 
-def test_large_long_solve_tracks_the_fp64_form_at_the_bar(B, mixed, large):
-    """The mixed form over a long budget, checked by the plain FP64 form.
+def test_large_converged_solve_matches_the_fp64_form_at_the_bar(B, mixed, large):
+    """Both forms run to a stated convergence rule, and compared there.
 
-    This workload does not converge in any budget a test can afford: its points are seen
-    by their 2-6 nearest cameras of a dense ring, along nearly parallel rays (parallax
-    ~1e-3 rad), so their depths are barely constrained and LM with block-Jacobi PCG crawls
-    along those directions (the FP64 form crawls at the same rate).  What is checked:
-
-    * 500 LM iterations (<= 500 PCG each) lower the cost monotonically, status 0;
-    * the mixed form's own cost at its end point is the true cost: the FP64 form
-      evaluates the same parameters within 1e-9 (double-float residuals; with FP32
-      residuals LM exploits their ~1e-4 px errors along the flat directions and the two
-      evaluations part by up to ~3e-4);
-    * from that end point, 20 more LM iterations of each form (fresh solves, same
-      options) reach costs within the 1e-4 bar of each other: the mixed form keeps
-      tracking FP64 in the hard tail, not only at the first step;
-    * 2F / dof, dof = m - n + 7 (the chi^2 statistic of the maximum-likelihood fit, n
-      minus the 7-dimensional similarity gauge), is within 1 % of 1.  (It sits ~0.2 %
-      below: for nearly degenerate two-view points the linear count of degrees of
-      freedom overstates what the fit leaves in the residuals, so the +-4 sigma band of
-      the linear model, 0.04 %, does not apply.)"""
+    Rule: 100 LM iterations (<= 50 PCG each), after which the accepted costs of the last
+    20 iterations differ by less than 1e-6 relative in either form.  Then: final costs
+    within the 1e-4 bar of each other, both in the chi^2 band, and the mixed form's own
+    cost of its end point equal to the FP64 form's evaluation of the same parameters
+    within 1e-9 (its residuals are double-float, its parameters kept in FP64)."""
+    opts = dict(max_lm_iters=100, max_pcg_iters=50)
     mixed.set_params(large.cams_init, large.pts_init)
-    a = mixed.solve(max_lm_iters=500, max_pcg_iters=500)
-    assert a.status == 0 and a.lm_iters == 500
-    costs = [h["cost"] for h in a.history] + [a.final_cost]
-    assert all(x >= y for x, y in zip(costs, costs[1:]))
-    c, q = mixed.get_params()
+    a = mixed.solve(**opts)
     f = B.Problem(large.n_cams, large.n_pts, large.cam_idx, large.pt_idx, large.pixels, precision="fp64")
-    f.set_params(c, q)
-    b = f.solve(max_lm_iters=20, max_pcg_iters=500)
+    f.set_params(large.cams_init, large.pts_init)
+    b = f.solve(**opts)
+    for r in (a, b):
+        assert r.status == 0 and r.lm_iters == 100
+        c = _costs(r)
+        assert c[-21] - c[-1] <= 1e-6 * c[-1], (c[-21], c[-1])
+    assert abs(a.final_cost - b.final_cost) <= 1e-4 * b.final_cost, (a.final_cost, b.final_cost)
+    centre, band = _chi2(large)
+    assert abs(a.final_cost - centre) <= band and abs(b.final_cost - centre) <= band, (a.final_cost, b.final_cost)
+    cams, pts = mixed.get_params()
+    f.set_params(cams, pts)
+    e = f.solve(max_lm_iters=0)
     f.close()
-    assert b.status == 0
-    assert abs(b.initial_cost - a.final_cost) <= 1e-9 * a.final_cost, (b.initial_cost, a.final_cost)
-    mixed.set_params(c, q)
-    a2 = mixed.solve(max_lm_iters=20, max_pcg_iters=500)
-    assert a2.status == 0
-    assert abs(a2.initial_cost - b.initial_cost) <= 1e-9 * b.initial_cost
-    assert abs(a2.final_cost - b.final_cost) <= 1e-4 * b.final_cost, (a2.final_cost, b.final_cost)
-    dof = 2 * large.n_obs - 9 * large.n_cams - 3 * large.n_pts + 7
-    for r in (a, a2, b):
-        assert abs(2.0 * r.final_cost / dof - 1.0) <= 0.01, r.final_cost
+    assert abs(e.initial_cost - a.final_cost) <= 1e-9 * a.final_cost, (e.initial_cost, a.final_cost)
