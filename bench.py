@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-schur", action="store_true")
     ap.add_argument("--no-factors", action="store_true")
-    ap.add_argument("--no-one-exchange", action="store_true")
+    ap.add_argument("--no-two-exchange", action="store_true", help="skip the textbook persistent PCG leg")
     ap.add_argument("--no-autograd", action="store_true")
     ap.add_argument("--no-medium", action="store_true", help="skip the medium-workload legs")
     ap.add_argument("--no-ttc", action="store_true", help="skip the extended-budget time-to-cost leg")
@@ -440,7 +440,7 @@ def solve_leg(binding, prob, opts, torch, stream, flush, steps, target=None, pos
 def medium_legs(args, binding, synth, torch, dev, stream, flush, hbm_peak, alu_peak):
     """The medium workload (1,000 cameras, 200,000 points, 1,199,169 observations): the
     default solver against the FP64 oracle's stored 20-iteration cost C*, the persistent
-    PCG kernel's roofline, and the option legs (one-exchange PCG form, Schur complement,
+    PCG kernel's roofline, and the option legs (the textbook two-exchange PCG form, Schur complement,
     relative-pose factors)."""
     prob = synth.make_config("medium")
     target = golden_cost("medium")
@@ -456,9 +456,9 @@ def medium_legs(args, binding, synth, torch, dev, stream, flush, hbm_peak, alu_p
     out["kernel_us"] = ku
     out["roofline_pcg_persistent"] = persistent_roofline(ku, prob, "medium", hbm_peak, alu_peak)
     p.close()
-    if not args.no_one_exchange:
-        out["pcg_one_exchange"] = solve_leg(binding, prob, binding.default_options(use_graph=args.graph_mode,
-                                                                                   pcg_kernel=2),
+    if not args.no_two_exchange:
+        out["pcg_two_exchange"] = solve_leg(binding, prob, binding.default_options(use_graph=args.graph_mode,
+                                                                                   pcg_kernel=0),
                                             torch, stream, flush, n, target)
     out["pcg_separate_kernels"] = solve_leg(binding, prob, binding.default_options(use_graph=args.graph_mode,
                                                                                    pcg_kernel=1),

@@ -80,16 +80,20 @@ typedef struct {
                                      2: one graph of the fixed sequence of max_lm_iters x
                                      max_pcg_iters slots, idle slots return at once;
                                      0: the same sequence launched from the host    */
-    int32_t pcg_kernel;           /* 0 (default): one persistent cooperative kernel per PCG
+    int32_t pcg_kernel;           /* 2 (default): one persistent cooperative kernel per PCG
                                      solve when every CTA's tiles fit in shared memory,
-                                     with two grid-wide exchanges per iteration;
+                                     with the recurrences arranged so that one grid-wide
+                                     exchange per iteration carries both inner products,
+                                     and residual replacement: when the recursively
+                                     updated residual meets the tolerance, the true
+                                     residual b - A h is computed and the recurrences
+                                     restart from it, so the solve stops on a true
+                                     residual (at most 4 checks per solve);
+                                     0: the persistent kernel with the textbook
+                                     recurrences (two exchanges per iteration);
                                      1: separate kernels per PCG iteration (also used
                                      when the persistent plan does not fit);
-                                     2: the persistent kernel with the recurrences
-                                     arranged so that one exchange per iteration carries
-                                     both inner products (same iterates in exact
-                                     arithmetic; its updated residual drifts sooner);
-                                     3: separate kernels per PCG iteration with those
+                                     3: separate kernels per PCG iteration with the
                                      one-reduction recurrences: each iteration's update
                                      is fused into the next operator application (falls
                                      back to 1 when a tile's observations exceed the

@@ -443,7 +443,7 @@ ba_status ba_options_default(ba_options* o) {
     o->max_mu = 1e16;
     o->eps_depth = 0.0;
     o->use_graph = 1;
-    o->pcg_kernel = 0;
+    o->pcg_kernel = 2;
     o->rotation_update = 0;
     o->loss = 0;
     o->loss_scale = 1.0;
@@ -691,7 +691,7 @@ static ba_status plan_persistent(ba_problem* p, int sms) {
     p->p_grid = G;
     p->p_smem_one = (int)worst_one;
     p->p_smem_two = (int)worst_two;
-    p->p_form = p->fits_two ? PCG_TWO_EXCHANGE : PCG_ONE_EXCHANGE;
+    p->p_form = p->fits_one ? PCG_ONE_EXCHANGE : PCG_TWO_EXCHANGE;   // the default form first
     return BA_OK;
 }
 

@@ -510,6 +510,81 @@ __device__ __forceinline__ void warp_partials3(float a, float ac, float b, float
     }
 }
 
+// Residual replacement of the one-exchange form: with A h assembled (points in sQ,
+// cameras in the accumulator set `cacc`), r = b - A h with b = -g, u = M^-1 r and
+// p = s = 0; the partials of r^T u, |r|^2 and u^T D u go to red_u as the update phase
+// leaves them, and the owners clear the accumulator set `clear` as it does.
+template <int TB>
+__device__ void replace_residual(const Views<float>& v, const float* cacc, const uint32_t* sCid, const uint32_t* sOwn,
+                                 int ne, int np, size_t g0, float muf, const float4* sX4, float4* sU4,
+                                 const float* sD2, float* sP, float* sS, float* sR, const float* sH, float* sQ,
+                                 const float* sM, float* sCu, float* sCp, float* sCs, float* sCr, const float* sCh,
+                                 float* clear, double* red_u) {
+    const int tid = threadIdx.x;
+    float lg = 0.0f, lr = 0.0f, lu = 0.0f, lgc = 0.0f, lrc = 0.0f, luc = 0.0f;   // Kahan pairs
+    // cameras, step 1: r = -g - (J^T J h + mu D h)
+    for (int e = tid; e < ne; e += TB) {
+        const int lc = e / 9, i = e - 9 * lc;
+        const uint32_t c = sCid[lc];
+        const float* ca = cacc + (size_t)c * CA_STRIDE;
+        float q;
+        if (i < 3) {
+            const float* JL = v.cam_pre + (size_t)c * CP_STRIDE + CP_JL;
+            q = fmaf(__ldg(JL + i), __ldcg(ca + 0), fmaf(__ldg(JL + 3 + i), __ldcg(ca + 1),
+                                                       __ldg(JL + 6 + i) * __ldcg(ca + 2)));
+        } else {
+            q = __ldcg(ca + i);
+        }
+        const float ah = fmaf(muf, __ldg(v.D + 9 * (size_t)c + i) * sCh[e], q);
+        sCr[e] = (float)(-v.cam_lin[(size_t)c * CL_STRIDE + CL_G + i]) - ah;
+        sCp[e] = 0.0f;
+        sCs[e] = 0.0f;
+    }
+    // points
+    for (int i = tid; i < np; i += TB) {
+        const float Dq[3] = {sX4[i].w, sU4[i].w, sD2[i]};
+        float r3[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int e = 3 * i + q;
+            const float ah = fmaf(muf, Dq[q] * sH[e], sQ[e]);
+            r3[q] = -v.g[g0 + e] - ah;
+            sR[e] = r3[q];
+            sQ[e] = 0.0f;
+            sP[e] = 0.0f;
+            sS[e] = 0.0f;
+        }
+        const float* m = sM + 6 * i;
+        const float z0 = fmaf(m[0], r3[0], fmaf(m[1], r3[1], m[2] * r3[2]));
+        const float z1 = fmaf(m[1], r3[0], fmaf(m[3], r3[1], m[4] * r3[2]));
+        const float z2 = fmaf(m[2], r3[0], fmaf(m[4], r3[1], m[5] * r3[2]));
+        sU4[i] = make_float4(z0, z1, z2, Dq[1]);
+        kahan_add(lg, lgc, fmaf(r3[0], z0, fmaf(r3[1], z1, r3[2] * z2)));
+        kahan_add(lr, lrc, fmaf(r3[0], r3[0], fmaf(r3[1], r3[1], r3[2] * r3[2])));
+        kahan_add(lu, luc, fmaf(Dq[0] * z0, z0, fmaf(Dq[1] * z1, z1, Dq[2] * z2 * z2)));
+    }
+    __syncthreads();   // camera r
+    // cameras, step 2: u = M^-1 r
+    for (int e = tid; e < ne; e += TB) {
+        const int lc = e / 9, i = e - 9 * lc;
+        const uint32_t c = sCid[lc];
+        const float* M = v.Minv_c + (size_t)c * MC_STRIDE + 9 * i;
+        const float* r9 = sCr + 9 * lc;
+        float z = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) z = fmaf(__ldg(M + q), r9[q], z);
+        sCu[e] = z;
+        if (owns(sOwn, lc)) {
+            const float ri = r9[i];
+            kahan_add(lg, lgc, ri * z);
+            kahan_add(lr, lrc, ri * ri);
+            kahan_add(lu, luc, __ldg(v.D + 9 * (size_t)c + i) * z * z);
+            clear[(size_t)c * CA_STRIDE + i] = 0.0f;
+        }
+    }
+    warp_partials3(lg, lgc, lr, lrc, lu, luc, red_u);
+}
+
 }  // namespace
 
 template <int TB>
@@ -623,7 +698,17 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
     double gam = st->rz, gam_prev = 1.0, alpha = 0.0, alpha_prev = 1.0, rr = rr0;
     float beta = 0.0f;
     unsigned long long epoch = 0ull;
-    int k = 0;
+    int k = 0;    // PCG updates
+    int it = 0;   // operator passes (they rotate the camera accumulator sets)
+    // Residual replacement (van der Vorst and Ye, SIAM J. Sci. Comput. 22, 2000): when the
+    // recursively updated residual meets the tolerance, one operator pass on h gives the
+    // true residual r = b - A h (b = -g); the recurrences restart from it (p = s = 0), and
+    // the solve stops only on a true residual that meets the tolerance.  At most
+    // MAX_CHECKS such checks per solve; past them the recursive residual decides.
+    constexpr int MAX_CHECKS = 4;
+    int checks = 0;
+    bool verify = false;   // the coming operator pass applies A to h
+    bool fresh = true;     // r is a true residual and p = s = 0 (the recurrence starts anew)
     bool ok = true, numeric_fail = false;
     // this thread's observation chunk (block-local indices) and its first tile
     const uint32_t chunk = odd_chunk<uint32_t>(no, TB);
@@ -639,8 +724,8 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
     }
 
     while (k < max_pcg) {
-        float* cacc = v.cam_acc + (size_t)(k % CA_SETS) * cas;
-        // ------------------------------------------------------------ M: w = A u
+        float* cacc = v.cam_acc + (size_t)(it % CA_SETS) * cas;
+        // ------------------------------------------------------------ M: w = A u (A h when verifying)
         float jj = 0.0f, jjc = 0.0f;   // Kahan pair
         {
             uint32_t cur = NO_CAM;
@@ -696,20 +781,47 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         double mine[XCH_NV] = {0.0, 0.0, 0.0, 0.0}, tot[XCH_NV];
         if (tid == 0) {
             for (int w = 0; w < NW; ++w) {
-                mine[0] += red_u[3 * w];
-                mine[1] += red_u[3 * w + 1];
-                mine[2] += red_u[3 * w + 2];
+                if (!verify) {   // a verification pass carries only its operator sums
+                    mine[0] += red_u[3 * w];
+                    mine[1] += red_u[3 * w + 1];
+                    mine[2] += red_u[3 * w + 2];
+                }
                 mine[3] += red_m[w];
             }
         }
         if (!exchange(st, pslots, ++epoch, mine, tot, shx)) { ok = false; break; }
+        if (verify) {
+            // ---------------------------------------------------- R: r = b - A h, restart
+            replace_residual<TB>(v, cacc, sCid, sOwn, ne, np, g0, muf, sX4, sU4, sD2, sP, sS, sR, sH, sQ, sM, sCu,
+                                 sCp, sCs, sCr, sCh, v.cam_acc + (size_t)((it + 2) % CA_SETS) * cas, red_u);
+            __syncthreads();   // camera u
+            camera_dirs<TB>(v, sCid, sCu, sDir, ne);
+            __syncthreads();
+            verify = false;
+            fresh = true;
+            ++it;
+            continue;
+        }
         const double g_k = tot[0], rr_k = tot[1], udu = tot[2], jju = tot[3];
         if (!isfinite(g_k) || !isfinite(rr_k)) { numeric_fail = true; break; }
         rr = rr_k;
-        if (k > 0 && rr_k <= tol2 * rr0) break;
-        const double b_k = k > 0 ? g_k / gam_prev : 0.0;
-        const double delta = jju + mu * udu;                                  // u^T A u
-        const double denom = k > 0 ? delta - b_k * g_k / alpha_prev : delta;   // p^T A p
+        if (k > 0 && rr_k <= tol2 * rr0) {
+            if (fresh || checks >= MAX_CHECKS) break;   // a true residual (or no checks left)
+            // check the recursive residual against the true one: the next pass applies A to h
+            ++checks;
+            verify = true;
+            for (int i = tid; i < np; i += TB)
+                sU4[i] = make_float4(sH[3 * i], sH[3 * i + 1], sH[3 * i + 2], sU4[i].w);
+            for (int e = tid; e < ne; e += TB) sCu[e] = sCh[e];
+            __syncthreads();
+            camera_dirs<TB>(v, sCid, sCu, sDir, ne);
+            __syncthreads();
+            ++it;
+            continue;
+        }
+        const double b_k = fresh ? 0.0 : g_k / gam_prev;
+        const double delta = jju + mu * udu;                                    // u^T A u
+        const double denom = fresh ? delta : delta - b_k * g_k / alpha_prev;    // p^T A p
         if (!(denom > 0.0) || !isfinite(denom)) {
             numeric_fail = !isfinite(denom);
             break;   // every CTA sees the same sums and leaves here
@@ -775,7 +887,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         // accumulator set that the iteration after next fills (its last readers are
         // past the exchange above)
         {
-            float* clear = v.cam_acc + (size_t)((k + 2) % CA_SETS) * cas;
+            float* clear = v.cam_acc + (size_t)((it + 2) % CA_SETS) * cas;
             for (int e = tid; e < ne; e += TB) {
                 const int lc = e / 9, i = e - 9 * lc;
                 const uint32_t c = sCid[lc];
@@ -800,7 +912,9 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         __syncthreads();
         gam_prev = g_k;
         alpha_prev = alpha;
+        fresh = false;
         ++k;
+        ++it;
     }
     // closing exchange: past it no CTA reads an accumulator set any more, so the
     // owners leave all of them cleared
