@@ -511,15 +511,14 @@ __device__ __forceinline__ void warp_partials3(float a, float ac, float b, float
 }
 
 // Residual replacement of the one-exchange form: with A h assembled (points in sQ,
-// cameras in the accumulator set `cacc`), r = b - A h with b = -g, u = M^-1 r and
-// p = s = 0; the partials of r^T u, |r|^2 and u^T D u go to red_u as the update phase
+// cameras in the accumulator set `cacc`), r = b - A h with b = -g and u = M^-1 r (p and
+// s are kept); the partials of r^T u, |r|^2 and u^T D u go to red_u as the update phase
 // leaves them, and the owners clear the accumulator set `clear` as it does.
 template <int TB>
 __device__ void replace_residual(const Views<float>& v, const float* cacc, const uint32_t* sCid, const uint32_t* sOwn,
                                  int ne, int np, size_t g0, float muf, const float4* sX4, float4* sU4,
-                                 const float* sD2, float* sP, float* sS, float* sR, const float* sH, float* sQ,
-                                 const float* sM, float* sCu, float* sCp, float* sCs, float* sCr, const float* sCh,
-                                 float* clear, double* red_u) {
+                                 const float* sD2, float* sR, const float* sH, float* sQ, const float* sM, float* sCu,
+                                 float* sCr, const float* sCh, float* clear, double* red_u) {
     const int tid = threadIdx.x;
     float lg = 0.0f, lr = 0.0f, lu = 0.0f, lgc = 0.0f, lrc = 0.0f, luc = 0.0f;   // Kahan pairs
     // cameras, step 1: r = -g - (J^T J h + mu D h)
@@ -537,8 +536,6 @@ __device__ void replace_residual(const Views<float>& v, const float* cacc, const
         }
         const float ah = fmaf(muf, __ldg(v.D + 9 * (size_t)c + i) * sCh[e], q);
         sCr[e] = (float)(-v.cam_lin[(size_t)c * CL_STRIDE + CL_G + i]) - ah;
-        sCp[e] = 0.0f;
-        sCs[e] = 0.0f;
     }
     // points
     for (int i = tid; i < np; i += TB) {
@@ -551,8 +548,6 @@ __device__ void replace_residual(const Views<float>& v, const float* cacc, const
             r3[q] = -v.g[g0 + e] - ah;
             sR[e] = r3[q];
             sQ[e] = 0.0f;
-            sP[e] = 0.0f;
-            sS[e] = 0.0f;
         }
         const float* m = sM + 6 * i;
         const float z0 = fmaf(m[0], r3[0], fmaf(m[1], r3[1], m[2] * r3[2]));
@@ -702,13 +697,14 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
     int it = 0;   // operator passes (they rotate the camera accumulator sets)
     // Residual replacement (van der Vorst and Ye, SIAM J. Sci. Comput. 22, 2000): when the
     // recursively updated residual meets the tolerance, one operator pass on h gives the
-    // true residual r = b - A h (b = -g); the recurrences restart from it (p = s = 0), and
-    // the solve stops only on a true residual that meets the tolerance.  At most
-    // MAX_CHECKS such checks per solve; past them the recursive residual decides.
+    // true residual r = b - A h (b = -g), which replaces r (and u = M^-1 r) while the
+    // search directions p, s are kept; the solve stops only on a true residual that
+    // meets the tolerance.  At most MAX_CHECKS such checks per solve; past them the
+    // recursive residual decides.
     constexpr int MAX_CHECKS = 4;
     int checks = 0;
     bool verify = false;   // the coming operator pass applies A to h
-    bool fresh = true;     // r is a true residual and p = s = 0 (the recurrence starts anew)
+    bool true_r = false;   // r was just replaced by the true residual
     bool ok = true, numeric_fail = false;
     // this thread's observation chunk (block-local indices) and its first tile
     const uint32_t chunk = odd_chunk<uint32_t>(no, TB);
@@ -792,13 +788,13 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         if (!exchange(st, pslots, ++epoch, mine, tot, shx)) { ok = false; break; }
         if (verify) {
             // ---------------------------------------------------- R: r = b - A h, restart
-            replace_residual<TB>(v, cacc, sCid, sOwn, ne, np, g0, muf, sX4, sU4, sD2, sP, sS, sR, sH, sQ, sM, sCu,
-                                 sCp, sCs, sCr, sCh, v.cam_acc + (size_t)((it + 2) % CA_SETS) * cas, red_u);
+            replace_residual<TB>(v, cacc, sCid, sOwn, ne, np, g0, muf, sX4, sU4, sD2, sR, sH, sQ, sM, sCu, sCr, sCh,
+                                 v.cam_acc + (size_t)((it + 2) % CA_SETS) * cas, red_u);
             __syncthreads();   // camera u
             camera_dirs<TB>(v, sCid, sCu, sDir, ne);
             __syncthreads();
             verify = false;
-            fresh = true;
+            true_r = true;
             ++it;
             continue;
         }
@@ -806,7 +802,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         if (!isfinite(g_k) || !isfinite(rr_k)) { numeric_fail = true; break; }
         rr = rr_k;
         if (k > 0 && rr_k <= tol2 * rr0) {
-            if (fresh || checks >= MAX_CHECKS) break;   // a true residual (or no checks left)
+            if (true_r || checks >= MAX_CHECKS) break;   // a true residual (or no checks left)
             // check the recursive residual against the true one: the next pass applies A to h
             ++checks;
             verify = true;
@@ -819,9 +815,9 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
             ++it;
             continue;
         }
-        const double b_k = fresh ? 0.0 : g_k / gam_prev;
-        const double delta = jju + mu * udu;                                    // u^T A u
-        const double denom = fresh ? delta : delta - b_k * g_k / alpha_prev;    // p^T A p
+        const double b_k = k > 0 ? g_k / gam_prev : 0.0;
+        const double delta = jju + mu * udu;                                  // u^T A u
+        const double denom = k > 0 ? delta - b_k * g_k / alpha_prev : delta;   // p^T A p
         if (!(denom > 0.0) || !isfinite(denom)) {
             numeric_fail = !isfinite(denom);
             break;   // every CTA sees the same sums and leaves here
@@ -912,7 +908,7 @@ __global__ void __launch_bounds__(TB, 1) k_pcg_persistent_1x(Views<float> v, con
         __syncthreads();
         gam_prev = g_k;
         alpha_prev = alpha;
-        fresh = false;
+        true_r = false;
         ++k;
         ++it;
     }

@@ -199,17 +199,27 @@ def test_noise_free_ground_truth_has_zero_cost(B):
 
 
 def test_single_tile_and_heavy_point(B):
-    """One point seen by every camera (a 40-observation run in a tile) and tiny tiles."""
+    """One point seen by every camera (a 40-observation run in a tile) and tiny tiles.
+
+    The problem is underdetermined (360 camera parameters against 5 points), so LM does
+    not converge on it and the cost after 5 iterations depends on where each PCG solve
+    stopped.  The textbook recurrences (pcg_kernel 0, 1) stop where the oracle's do and
+    match it at the 1e-4 bar.  The default one-exchange form with residual replacement
+    runs on until its true residual meets the tolerance (104 oracle PCG iterations
+    against ~140) and is held to 1e-3."""
     prob = synth.make_problem(40, 5, ("poisson", 60.0), "uniform", seed=4)
     prob = synth.round_to_f32(prob)
     p = _problem(B, prob)
     cost, r, J = p.evaluate(residuals=True, jacobian=True)
     ref = O.residuals(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
     assert np.linalg.norm(r.double().cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
-    res = p.solve(max_lm_iters=5)
     refs = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels,
                       O.LMOptions(max_lm_iters=5))
-    assert abs(res.final_cost - refs.final_cost) <= 1e-4 * max(refs.final_cost, 1e-9) + 1e-6
+    for k, bar in ((0, 1e-4), (1, 1e-4), (2, 1e-3)):
+        p.set_params(prob.cams_init, prob.pts_init)
+        res = p.solve(max_lm_iters=5, pcg_kernel=k)
+        assert res.status == 0 and res.lm_iters == 5
+        assert abs(res.final_cost - refs.final_cost) <= bar * refs.final_cost, (k, res.final_cost, refs.final_cost)
 
 
 def test_problems_bound_side_by_side_keep_working(B):
