@@ -88,7 +88,9 @@ typedef struct {
                                      updated residual meets the tolerance, the true
                                      residual b - A h is computed and the recurrences
                                      restart from it, so the solve stops on a true
-                                     residual (at most 4 checks per solve);
+                                     residual (at most 4 checks per solve); where its
+                                     plan does not fit but the two-exchange one does
+                                     (it holds private camera copies), the latter;
                                      0: the persistent kernel with the textbook
                                      recurrences (two exchanges per iteration);
                                      1: separate kernels per PCG iteration (also used

@@ -964,9 +964,10 @@ ba_status ba_solve(ba_problem* p, const ba_options* o, ba_stats* stats, ba_iter_
     }
     if ((st = write_options(p, o))) return st;
     const bool want_schur = o->solver == 1;
-    // pcg_kernel 0: the persistent kernel's two-exchange form, 2: its one-exchange
-    // form, each when the plan fits in that form; otherwise separate kernels
-    const int want_form = o->pcg_kernel == 2 ? PCG_ONE_EXCHANGE : PCG_TWO_EXCHANGE;
+    // pcg_kernel 2: the persistent kernel's one-exchange form when its plan fits, else its
+    // two-exchange form; 0: the two-exchange form; otherwise (or when neither plan fits)
+    // separate kernels
+    const int want_form = (o->pcg_kernel == 2 && p->fits_one) ? PCG_ONE_EXCHANGE : PCG_TWO_EXCHANGE;
     const bool want_persistent = !want_schur && o->pcg_kernel != 1 && o->pcg_kernel != 3 &&
                                  (want_form == PCG_ONE_EXCHANGE ? p->fits_one : p->fits_two);
     // pcg_kernel 3: separate kernels with the one-reduction recurrences (tile kernels)
