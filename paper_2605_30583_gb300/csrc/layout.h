@@ -29,7 +29,7 @@ static_assert(XCH_NV <= SLOT_STRIDE, "a slot holds every sum of one exchange");
 // Camera accumulator sets of the one-exchange kernel (rotating over iterations).
 constexpr int CA_SETS = 3;
 // A camera run of a tile this long or longer is walked in camera-uniform warp steps.
-constexpr int LONG_RUN = 32;
+constexpr int LONG_RUN = 16;
 
 // Camera record (floats), written once per parameter change (FP64 math, FP32 store).
 enum : int { CP_R = 0, CP_T = 9, CP_F = 12, CP_K1 = 13, CP_K2 = 14, CP_PAD = 15,

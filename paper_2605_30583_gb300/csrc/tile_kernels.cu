@@ -4,7 +4,7 @@
 // Work decomposition.  A tile is TILE_PTS consecutive points (locality order) and all
 // their observations.  Inside a tile each camera's observations form one run, and the
 // runs of at least LONG_RUN observations come first (order.cu); on the large workloads
-// they hold over 90 % of the observations.  A CTA stages in shared memory, in one round
+// they hold most of the observations.  A CTA stages in shared memory, in one round
 // trip, the tile's points, its compact observation table (a one-byte point slot per long-run
 // observation, the key of each short-run observation) and its table
 // of long runs {start, length, camera}; then
