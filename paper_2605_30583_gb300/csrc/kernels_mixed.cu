@@ -685,20 +685,41 @@ __global__ void k_candidate(Views<float> v) {
             for (int k = 0; k < 6; ++k) d[CD_T + k] = hc[3 + k];
         }
     }
-    FOR_POINTS(i, v) {
-        {
-            const size_t e = v.pt_off + 3 * (size_t)i;
-            float s = 0.0f;
+    // points four at a time (a quad's twelve entries as 16-byte accesses; the padding
+    // entries of the last quad are zero and stay zero)
+    for (int qd = blockIdx.x * blockDim.x + threadIdx.x; qd < v.n_quads; qd += gridDim.x * blockDim.x) {
+        const size_t e = v.pt_off + 12 * (size_t)qd;
+        const float4* h4 = reinterpret_cast<const float4*>(v.h + e);
+        const float4* g4 = reinterpret_cast<const float4*>(v.g + e);
+        const double2* m2 = reinterpret_cast<const double2*>(v.xm + e);
+        float H[12], G[12];
+        double X[12];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float hk = v.h[e + k];
-                const double xk = v.xm[e + k] + (double)hk;
-                v.xm_new[e + k] = xk;
-                v.x_new[e + k] = (float)xk;
-                s = fmaf(v.g[e + k], hk, s);
-            }
-            gh += (double)s;
+        for (int k = 0; k < 3; ++k) {
+            const float4 a = h4[k], b = g4[k];
+            H[4 * k] = a.x; H[4 * k + 1] = a.y; H[4 * k + 2] = a.z; H[4 * k + 3] = a.w;
+            G[4 * k] = b.x; G[4 * k + 1] = b.y; G[4 * k + 2] = b.z; G[4 * k + 3] = b.w;
         }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const double2 a = m2[k];
+            X[2 * k] = a.x;
+            X[2 * k + 1] = a.y;
+        }
+        float sgh = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            X[k] += (double)H[k];
+            sgh = fmaf(G[k], H[k], sgh);
+        }
+        double2* n2 = reinterpret_cast<double2*>(v.xm_new + e);
+        float4* x4 = reinterpret_cast<float4*>(v.x_new + e);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) n2[k] = make_double2(X[2 * k], X[2 * k + 1]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            x4[k] = make_float4((float)X[4 * k], (float)X[4 * k + 1], (float)X[4 * k + 2], (float)X[4 * k + 3]);
+        gh += (double)sgh;
     }
     double in[1] = {gh}, out[1];
     if (grid_reduce<1>(in, v.partials, &st->tickets[TK_CAND], out) && threadIdx.x == 0) st->gh = out[0];
@@ -1183,7 +1204,7 @@ void launch_update(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, Co
                L.item_block, 0, s>>>(v, c, use, cameras_only);
 }
 void launch_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s) {
-    k_candidate<<<std::max(grid_items(L, v.n_pts), grid_cams(L, v.n_cams)), L.item_block, 0, s>>>(v);
+    k_candidate<<<std::max(grid_items(L, v.n_quads), grid_cams(L, v.n_cams)), L.item_block, 0, s>>>(v);
 }
 void launch_eval_candidate(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle c, int use) {
     launch_factor_eval(v, L, s);
