@@ -84,17 +84,6 @@ __device__ __forceinline__ void stage_compact(const Views<float>& v, const TileR
 }
 
 
-template <int TB, bool UV>
-__device__ __forceinline__ void stage_obs(const Views<float>& v, const TileRange& T, uint32_t* sKey, float2* sUV,
-                                          uint32_t* sRun, const float* pairs = nullptr) {
-    const uint32_t n = T.hi - T.lo;
-    for (uint32_t i = threadIdx.x; i < n; i += TB) {
-        sKey[i] = __ldg(v.obs_key + T.lo + i);
-        if (UV) sUV[i] = __ldg(reinterpret_cast<const float2*>(pairs) + T.lo + i);
-    }
-    for (uint32_t i = threadIdx.x; i < 3 * T.nl; i += TB) sRun[i] = __ldg(v.long_run + 3 * (size_t)T.l0 + i);
-}
-
 // Block sums of compensated per-thread partials (Kahan pairs s - c): FP32 pairs inside
 // each warp, FP64 across the warps; valid in thread 0.  `sh` holds 2 * (TB / 32) doubles.
 template <int TB>
