@@ -140,19 +140,34 @@ def matvec_model(prob):
 # DRAM bytes (read + write) per launch of a roofline kernel, from one ncu capture of the
 # same workload and launch (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (kernel source file, workload) and stamped with the first 16 hex digits of the
-# SHA-256 of that source file when it was captured: a figure whose source has changed
-# since is reported as null (stale) until it is captured again.
+# SHA-256 of the kernel's source as it was captured (kernel_source below): a figure
+# whose kernel has changed since is reported as null (stale) until it is captured again.
 TRAFFIC = {
-    # k_tile_normal<128>, large workload: 282,884,352 B read + 82,646,784 B written
-    ("tile_kernels.cu", "large"): (365531136, "d69191f1f039ca3b"),
+    # k_tile_normal<128, true>, large workload: 283,754,240 B read + 82,839,808 B written
+    ("tile_kernels.cu", "large"): (366594048, "23e2a5a15cc1ed48"),
+}
+
+# The part of a source file a roofline kernel is built from: the file up to the end of
+# the kernel (its helpers and the kernel itself) and the headers it includes.
+KERNEL_SOURCE = {
+    "tile_kernels.cu": ("constexpr int TN_TB", ["mixed_common.cuh", "device_common.cuh", "layout.h"]),
+    "pcg_persistent.cu": (None, ["mixed_common.cuh", "device_common.cuh", "layout.h"]),
 }
 
 
 def source_sha16(name):
     import hashlib
-    path = os.path.join(ROOT, "paper_2605_30583_gb300", "csrc", name)
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    csrc = os.path.join(ROOT, "paper_2605_30583_gb300", "csrc")
+    end, headers = KERNEL_SOURCE.get(name, (None, []))
+    with open(os.path.join(csrc, name), "rb") as f:
+        text = f.read()
+    if end is not None:
+        text = text[:text.index(end.encode())]
+    h = hashlib.sha256(text)
+    for hd in headers:
+        with open(os.path.join(csrc, hd), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def measured_traffic(src, workload):

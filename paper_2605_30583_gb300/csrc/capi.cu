@@ -756,6 +756,15 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
     if (p->precision == BA_PREC_MIXED) build_order<float>(p->vf, b, s);
     else build_order<double>(p->vd, b, s);
     GBBA_CUDA(cudaGetLastError());
+    // repeated (camera, point) observations decide how the tile operator sums points;
+    // the point-key scratch is free once the order is built
+    uint32_t repeated = 1u;
+    if (p->precision == BA_PREC_MIXED) {
+        GBBA_CUDA(cudaMemsetAsync(b.pt_key, 0, sizeof(uint32_t), s));
+        flag_repeated_keys(p->vf.obs_key, p->n_obs, b.pt_key, s);
+        GBBA_CUDA(cudaGetLastError());
+        GBBA_CUDA(cudaMemcpyAsync(&repeated, b.pt_key, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    }
     // the scratch overlapped the solver arrays: clear them before first use
     const size_t ub = l.vec[0];
     GBBA_CUDA(cudaMemsetAsync(w + ub, 0, l.total - ub, s));
@@ -785,6 +794,7 @@ ba_status ba_bind_workspace(ba_problem* p, void* ws, size_t bytes, void* stream)
             most_runs = std::max(most_runs, loff[t + 1] - loff[t]);
         }
         plan_tile_kernels(p->L, p->n_tiles, sms, (int)most_long, (int)most_short, (int)most_runs);
+        p->L.tn_plain_q = repeated == 0u;
         GBBA_CUDA(cudaGetLastError());
     }
     p->bound = true;

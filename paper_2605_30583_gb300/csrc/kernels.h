@@ -42,6 +42,9 @@ struct LaunchCfg {
     // (the compact observation table the tile kernels stage)
     int tk_run_cap = 0, tk_short_cap = 0, tk_long_cap = 0;
     int tn_smem = 0, tl_smem = 0, te_smem = 0;   // their dynamic shared memory (staged observations)
+    // no camera observes a point twice (checked at bind): the operator's warps add their
+    // point sums into private copies with plain adds
+    int tn_plain_q = 0;
 };
 
 // residual pass of the mixed form (residual.cu): r at x (at_candidate 0) or at x' (1),
@@ -167,6 +170,11 @@ struct OrderBuffers {
 };
 template <typename T>
 void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s);
+// Sets *flag (device, zeroed by the caller) when two neighbouring keys of the ordered
+// observation table are equal: a camera that observes a point twice (or, rarely, the
+// same camera and slot on both sides of a tile boundary; a false alarm only costs the
+// operator its plain point sums).  order.cu.
+void flag_repeated_keys(const uint32_t* obs_key, int64_t n_obs, uint32_t* flag, cudaStream_t s);
 // Ascending sort of (key, value) pairs, n a power of two >= 2 (order.cu).
 void sort_pairs(uint64_t* keys, uint32_t* vals, size_t n, cudaStream_t s);
 

@@ -136,8 +136,10 @@ __device__ __forceinline__ void camera_dir(const Views<float>& v, uint32_t c, co
 // Contribution of one observation to the normal operator: t = J d (returns |t|^2),
 // camera sums (RX x u, u, intrinsic part) into acc, point part R^T u into qs (shared).
 // WEIGHTED: the robust loss's IRLS weight w scales the observation's rows of J^T J
-// (u = A^T (w t), returns w |t|^2).
-template <bool WEIGHTED = false>
+// (u = A^T (w t), returns w |t|^2).  PLAIN_Q: qs belongs to the calling warp alone and
+// no other lane of it touches the same point in this step, so plain adds replace the
+// shared-memory atomics.
+template <bool WEIGHTED = false, bool PLAIN_Q = false>
 __device__ __forceinline__ float obs_normal(const Cam& cam, const float (&dir)[9], const float* xs,
                                             const float* ds, float eps, float (&acc)[9], float* qs,
                                             float w = 1.0f) {
@@ -173,9 +175,18 @@ __device__ __forceinline__ float obs_normal(const Cam& cam, const float (&dir)[9
     acc[6] = fmaf(g.s, pt, acc[6]);
     acc[7] = fmaf(fn2, pt, acc[7]);
     acc[8] = fmaf(fn2 * g.n2, pt, acc[8]);
-    atomicAdd(qs + 0, fmaf(cam.R[0], u0, fmaf(cam.R[3], u1, cam.R[6] * u2)));
-    atomicAdd(qs + 1, fmaf(cam.R[1], u0, fmaf(cam.R[4], u1, cam.R[7] * u2)));
-    atomicAdd(qs + 2, fmaf(cam.R[2], u0, fmaf(cam.R[5], u1, cam.R[8] * u2)));
+    const float q0 = fmaf(cam.R[0], u0, fmaf(cam.R[3], u1, cam.R[6] * u2));
+    const float q1 = fmaf(cam.R[1], u0, fmaf(cam.R[4], u1, cam.R[7] * u2));
+    const float q2 = fmaf(cam.R[2], u0, fmaf(cam.R[5], u1, cam.R[8] * u2));
+    if (PLAIN_Q) {
+        qs[0] += q0;
+        qs[1] += q1;
+        qs[2] += q2;
+    } else {
+        atomicAdd(qs + 0, q0);
+        atomicAdd(qs + 1, q1);
+        atomicAdd(qs + 2, q2);
+    }
     return WEIGHTED ? w * tt : tt;
 }
 

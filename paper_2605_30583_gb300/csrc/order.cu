@@ -376,6 +376,21 @@ void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s) {
 
 void sort_pairs(uint64_t* keys, uint32_t* vals, size_t n, cudaStream_t s) { bitonic_sort(keys, vals, n, s); }
 
+namespace {
+// Within a tile the observations are ordered by (camera, point slot), and moving the
+// long runs to the front keeps each run's order, so two observations of one point by
+// one camera end up next to each other.
+__global__ void k_repeated_keys(const uint32_t* __restrict__ obs_key, int64_t n_obs, uint32_t* flag) {
+    for (int64_t j = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_obs; j += (int64_t)gridDim.x * blockDim.x)
+        if (obs_key[j] == obs_key[j - 1]) atomicOr(flag, 1u);
+}
+}  // namespace
+
+void flag_repeated_keys(const uint32_t* obs_key, int64_t n_obs, uint32_t* flag, cudaStream_t s) {
+    if (n_obs < 2) return;
+    k_repeated_keys<<<blocks_for((size_t)n_obs, 256), 256, 0, s>>>(obs_key, n_obs, flag);
+}
+
 template void build_order<float>(const Views<float>&, const OrderBuffers&, cudaStream_t);
 template void build_order<double>(const Views<double>&, const OrderBuffers&, cudaStream_t);
 

@@ -19,7 +19,10 @@
 //     camera sums to the global accumulators when it leaves it.
 // Point sums go into shared memory (the tile owns its points) and are written once per
 // tile.  This is our counterpart of the paper's Shared Read / Shared Add accessors
-// (Sec. IV-A).
+// (Sec. IV-A).  In the operator each warp adds its long runs' point sums into a copy of
+// its own with plain adds (the points of one run are distinct, so no two lanes of a step
+// meet), and the copies are summed when the tile is written; a problem with repeated
+// (camera, point) observations keeps one copy and shared-memory atomics.
 //
 // Per-thread sums that feed FP64 reductions (|J p|^2, p^T D p, the cost) are kept in
 // FP32 with Kahan's compensated summation, summed inside each warp in compensated FP32
@@ -99,15 +102,20 @@ __device__ __forceinline__ void block_pair_sums(float sa, float ca, float sb, fl
 // points' direction step p = zs + beta p_prev is fused into the staging.  One CTA per
 // tile.
 
-// Eight CTAs per SM (at most 64 registers per thread; the compact staging keeps the
-// shared memory of a CTA under a sixth of the SM's).
-template <int TB>
+// Eight CTAs per SM (at most 64 registers per thread; with per-warp point sums a CTA
+// holds ~20 KB of static shared memory plus its compact observation table).
+// PLAIN_Q: every warp keeps its own copy of the tile's point sums, added to with plain
+// shared-memory adds (valid when no camera observes a point twice; see the file head).
+// Replacing the point-sum atomics of the long runs this way took the operator from 302
+// to 289 us on the 28.8M-observation workload.
+template <int TB, bool PLAIN_Q>
 __global__ void __launch_bounds__(TB, 8) k_tile_normal(Views<float> v, const int32_t* gate, const float* zs,
                                                        int use_beta, Caps cap) {
     if (gated_off(gate)) return;
+    constexpr int NQ = PLAIN_Q ? TB / 32 : 1;   // point-sum copies
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ float4 sX4[TILE_PTS], sP4[TILE_PTS];
-    __shared__ float sQ[3 * TILE_PTS];
+    __shared__ float sQ[NQ * 3 * TILE_PTS];
     __shared__ unsigned int s_next;
     __shared__ double red[2 * (TB / 32)];
     DevState* st = v.st;
@@ -150,6 +158,8 @@ __global__ void __launch_bounds__(TB, 8) k_tile_normal(Views<float> v, const int
             }
         }
     }
+    for (int i = threadIdx.x; i < (NQ - 1) * 3 * TILE_PTS; i += TB) sQ[3 * TILE_PTS + i] = 0.0f;
+    float* const sQw = sQ + (PLAIN_Q ? (threadIdx.x >> 5) * 3 * TILE_PTS : 0);   // this warp's copy
     uint32_t *sRun, *sShort;
     uint8_t* sSlot;
     stage_compact<TB>(v, T, cap, dsm, sRun, sShort, sSlot);
@@ -174,10 +184,12 @@ __global__ void __launch_bounds__(TB, 8) k_tile_normal(Views<float> v, const int
             const uint32_t slot = sSlot[start + off];
             const float4 xp = sX4[slot], pp = sP4[slot];
             const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
-            const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * slot, __ldg(v.obs_w + j))
-                                      : obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * slot);
+            const float tt = weighted ? obs_normal<true, PLAIN_Q>(cam, dir, xs, ds, eps, acc, sQw + 3 * slot,
+                                                                 __ldg(v.obs_w + j))
+                                      : obs_normal<false, PLAIN_Q>(cam, dir, xs, ds, eps, acc, sQw + 3 * slot);
             kahan_add(jp_s, jp_c, tt);
         }
+        if (PLAIN_Q) __syncwarp();   // the warp's next run may meet the same points
         int idx;
         const int nv = warp_split_sum<9>(acc, lane, idx);
         if (nv > 0) atomicAdd(v.cam_acc + (size_t)c * CA_STRIDE + idx, acc[0]);
@@ -204,14 +216,20 @@ __global__ void __launch_bounds__(TB, 8) k_tile_normal(Views<float> v, const int
             }
             const float4 xp = sX4[slot], pp = sP4[slot];
             const float xs[3] = {xp.x, xp.y, xp.z}, ds[3] = {pp.x, pp.y, pp.z};
-            const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQ + 3 * slot, __ldg(v.obs_w + j))
-                                      : obs_normal(cam, dir, xs, ds, eps, acc, sQ + 3 * slot);
+            // lanes of a warp may meet one point here: atomics (into the warp's copy)
+            const float tt = weighted ? obs_normal<true>(cam, dir, xs, ds, eps, acc, sQw + 3 * slot, __ldg(v.obs_w + j))
+                                      : obs_normal(cam, dir, xs, ds, eps, acc, sQw + 3 * slot);
             kahan_add(jp_s, jp_c, tt);
         }
         if (cur != NO_CAM) flush_matvec(v.cam_acc + (size_t)cur * CA_STRIDE, acc);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 3 * T.npt; i += TB) v.q[T.base + i] = sQ[i];
+    for (int i = threadIdx.x; i < 3 * T.npt; i += TB) {
+        float qi = sQ[i];
+#pragma unroll
+        for (int w = 1; w < NQ; ++w) qi += sQ[w * 3 * TILE_PTS + i];
+        v.q[T.base + i] = qi;
+    }
     double bj, bp;
     block_pair_sums<TB>(jp_s, jp_c, pd_s, pd_c, red, bj, bp);
     if (threadIdx.x == 0) {
@@ -860,7 +878,8 @@ void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_long_obs, int
     const Caps cap{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap};
     if (compact_bytes(cap) > 160 * 1024) return;
     L.tn_smem = L.tl_smem = L.te_smem = (int)compact_bytes(cap);
-    const int bn = prepare(k_tile_normal<TN_TB>, TN_TB, L.tn_smem);
+    const int bn = std::min(prepare(k_tile_normal<TN_TB, true>, TN_TB, L.tn_smem),
+                            prepare(k_tile_normal<TN_TB, false>, TN_TB, L.tn_smem));
     const int bc = prepare(k_tile_cg<TN_TB>, TN_TB, L.tn_smem);
     const int bl = prepare(k_tile_linearize<TL_TB>, TL_TB, L.tl_smem);
     const int be = prepare(k_tile_eval<TE_TB>, TE_TB, L.te_smem);
@@ -873,8 +892,9 @@ void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_long_obs, int
 
 void launch_tile_normal(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate,
                         const float* zs, int use_beta) {
-    k_tile_normal<TN_TB><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, zs, use_beta,
-                                                             Caps{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap});
+    const Caps cap{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap};
+    if (L.tn_plain_q) k_tile_normal<TN_TB, true><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, zs, use_beta, cap);
+    else k_tile_normal<TN_TB, false><<<L.tn_grid, TN_TB, L.tn_smem, s>>>(v, gate, zs, use_beta, cap);
 }
 
 void launch_cg_round(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, const int32_t* gate, CondHandle c,

@@ -153,21 +153,32 @@ def test_large_solve_against_fp64_form(B, mixed, large):
 def test_large_converged_solve_matches_the_fp64_form_at_the_bar(B, mixed, large):
     """Both forms run to a stated convergence rule, and compared there.
 
-    Rule: 100 LM iterations (<= 50 PCG each), after which the accepted costs of the last
-    20 iterations differ by less than 1e-6 relative in either form.  Then: final costs
-    within the 1e-4 bar of each other, both in the chi^2 band, and the mixed form's own
-    cost of its end point equal to the FP64 form's evaluation of the same parameters
-    within 1e-9 (its residuals are double-float, its parameters kept in FP64)."""
-    opts = dict(max_lm_iters=100, max_pcg_iters=50)
-    mixed.set_params(large.cams_init, large.pts_init)
-    a = mixed.solve(**opts)
+    Rules: the FP64 form runs 100 LM iterations (<= 50 PCG each), after which its accepted
+    costs of the last 20 iterations differ by less than 1e-6 relative.  The mixed form
+    (about 20 ms per LM iteration) continues from its own end point in solves of 50 LM
+    iterations, at most six, until one whole solve lowers its cost by less than 1e-6
+    relative; where it stops along the way depends on the order of its FP32 sums, so a
+    fixed budget is not a convergence rule for it.  Then: final costs within the 1e-4
+    bar of each other, both in the chi^2 band, and the mixed form's own cost of its end
+    point equal to the FP64 form's evaluation of the same parameters within 1e-9 (its
+    residuals are double-float, its parameters kept in FP64)."""
     f = B.Problem(large.n_cams, large.n_pts, large.cam_idx, large.pt_idx, large.pixels, precision="fp64")
     f.set_params(large.cams_init, large.pts_init)
-    b = f.solve(**opts)
-    for r in (a, b):
-        assert r.status == 0 and r.lm_iters == 100
-        c = _costs(r)
-        assert c[-21] - c[-1] <= 1e-6 * c[-1], (c[-21], c[-1])
+    b = f.solve(max_lm_iters=100, max_pcg_iters=50)
+    assert b.status == 0 and b.lm_iters == 100
+    c = _costs(b)
+    assert c[-21] - c[-1] <= 1e-6 * c[-1], (c[-21], c[-1])
+    mixed.set_params(large.cams_init, large.pts_init)
+    a = mixed.solve(max_lm_iters=50, max_pcg_iters=50)
+    converged = False
+    for _ in range(5):
+        assert a.status == 0
+        prev = a.final_cost
+        a = mixed.solve(max_lm_iters=50, max_pcg_iters=50)
+        if prev - a.final_cost < 1e-6 * a.final_cost:
+            converged = True
+            break
+    assert converged and a.status == 0, a.final_cost
     assert abs(a.final_cost - b.final_cost) <= 1e-4 * b.final_cost, (a.final_cost, b.final_cost)
     centre, band = _chi2(large)
     assert abs(a.final_cost - centre) <= band and abs(b.final_cost - centre) <= band, (a.final_cost, b.final_cost)

@@ -12,6 +12,8 @@ pixels and only arithmetic differs.  Tolerances (derived from FP32 arithmetic):
     wrong block anywhere shows up at its own entries;
   * final LM cost: relative error <= 1e-4.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -87,9 +89,26 @@ def test_jacobian_matches_oracle(B):
     assert err_p.max() < 1e-5, err_p.max()
 
 
-def test_normal_operator_matches_oracle(B):
+def _with_repeats(prob, n_rep, seed):
+    """The problem with n_rep observations repeated (same camera and point, the pixel
+    moved by up to a pixel): a camera that sees a point twice."""
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(prob.n_obs, size=n_rep, replace=False)
+    px = prob.pixels[pick] + rng.uniform(-1.0, 1.0, size=(n_rep, 2))
+    return synth.round_to_f32(dataclasses.replace(
+        prob, cam_idx=np.concatenate([prob.cam_idx, prob.cam_idx[pick]]),
+        pt_idx=np.concatenate([prob.pt_idx, prob.pt_idx[pick]]), pixels=np.concatenate([prob.pixels, px])))
+
+
+@pytest.mark.parametrize("repeats", [0, 300])
+def test_normal_operator_matches_oracle(B, repeats):
+    """repeats = 0: the tile operator's warps add point sums into private copies;
+    repeats > 0: repeated (camera, point) observations, which sit next to each other in
+    a camera run, make it keep one copy with atomics."""
     import torch
     prob = _ragged(9)
+    if repeats:
+        prob = _with_repeats(prob, repeats, seed=4)
     p = _problem(B, prob)
     p.evaluate()
     lin = O.linearize(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels)
@@ -112,6 +131,16 @@ def test_normal_operator_matches_oracle(B):
         out_w, _ = p.apply_normal(mu, torch.from_numpy(w))
         a, b = float(out @ w), float(v @ out_w.double().cpu().numpy())
         assert abs(a - b) <= 1e-4 * (abs(a) + abs(b))
+
+
+def test_lm_solve_with_repeated_observations_matches_oracle(B):
+    prob = _with_repeats(_ragged(13), 400, seed=6)
+    ref = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels,
+                     O.LMOptions(max_lm_iters=10, max_pcg_iters=50))
+    p = _problem(B, prob)
+    res = p.solve(max_lm_iters=10, max_pcg_iters=50)
+    assert res.status == 0
+    assert abs(res.final_cost - ref.final_cost) <= 1e-4 * ref.final_cost, (res.final_cost, ref.final_cost)
 
 
 # (use_graph, pcg_kernel): conditional-loop graph / unrolled graph / host-launched
