@@ -580,24 +580,34 @@ def run_ours(args, rank, world, local_rank):
         q1 = np.empty_like(q0)
         e2e_s = []
         e2e_pcg = 0
+        phases = {"create": [], "bind": [], "set_params": [], "solve": [], "get_params": []}
         for _ in range(max(1, min(3, args.steps))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = ctypes.c_void_p()
             binding.check(L.ba_problem_create(prob.n_cams, prob.n_pts, prob.n_obs, ci.ctypes.data, pi.ctypes.data,
                                               px.ctypes.data, 0, ctypes.byref(h)))
+            t1 = time.perf_counter()
             binding.check(L.ba_bind_workspace(h, ws.data_ptr(), p.workspace_bytes, stream.cuda_stream))
+            t2 = time.perf_counter()
             binding.check(L.ba_set_params(h, c0.ctypes.data, q0.ctypes.data))
+            t3 = time.perf_counter()
             st = binding.Stats()
             binding.check(L.ba_solve(h, ctypes.byref(opts), ctypes.byref(st), None, 0))
+            t4 = time.perf_counter()
             binding.check(L.ba_get_params(h, c1.ctypes.data, q1.ctypes.data))
-            e2e_s.append(time.perf_counter() - t0)
+            t5 = time.perf_counter()
+            e2e_s.append(t5 - t0)
+            for k, a, b in (("create", t0, t1), ("bind", t1, t2), ("set_params", t2, t3), ("solve", t3, t4),
+                            ("get_params", t4, t5)):
+                phases[k].append(b - a)
             e2e_pcg += st.pcg_iters_total
             L.ba_problem_destroy(h)
         h2d = prob.n_obs * (4 + 4 + 16) + 8 * (9 * prob.n_cams + 3 * prob.n_pts)
         d2h = 8 * (9 * prob.n_cams + 3 * prob.n_pts) + 64
         e2e = {"value": e2e_pcg / sum(e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "s_per_step": sum(e2e_s) / len(e2e_s),
+               "phases_s": {k: round(sum(x) / len(x), 4) for k, x in phases.items()},
                "path": "ba_problem_create + ba_bind_workspace (upload + ordering) + ba_set_params + ba_solve "
                        "+ ba_get_params, host FP64 arrays"}
 

@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gbba.h"
@@ -43,12 +45,35 @@ struct GraphCache {
 
 }  // namespace gbba
 
+namespace gbba {
+// Allocator whose resize leaves new elements uninitialised (the observation copies are
+// filled by parallel copies right after).
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+    template <typename U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <typename U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <typename U>
+    void construct(U* ptr) noexcept {
+        ::new (static_cast<void*>(ptr)) U;
+    }
+    template <typename U, typename... A>
+    void construct(U* ptr, A&&... a) {
+        ::new (static_cast<void*>(ptr)) U(std::forward<A>(a)...);
+    }
+};
+}  // namespace gbba
+
 struct ba_problem {
     int32_t n_cams = 0, n_pts = 0, n_tiles = 0;
     int64_t n_obs = 0;
     int32_t precision = BA_PREC_MIXED;
-    std::vector<uint32_t> cam_idx, pt_idx;
-    std::vector<double> pixels;
+    std::vector<uint32_t, gbba::NoInitAlloc<uint32_t>> cam_idx, pt_idx;
+    std::vector<double, gbba::NoInitAlloc<double>> pixels;
     // pose factors (set before the workspace is bound)
     int32_t n_fac = 0;
     std::vector<uint32_t> fac_cam;   // [n_fac][2]

@@ -175,3 +175,38 @@ def test_bind_rejects_a_workspace_one_byte_short(lib):
 def test_wait_timeout_default(lib):
     o = binding.default_options()
     assert o.wait_timeout_ms == 2000
+
+
+def test_create_reports_the_first_bad_observation_of_a_large_problem(lib):
+    """ba_problem_create checks and copies the observations on several host threads for
+    large problems; the error it reports is still the first one in observation order:
+    the lowest bad observation, else the lowest point observed fewer than twice (with
+    its count)."""
+    n_pts, n_cams = 300_000, 50
+    n_obs = 4 * 2 ** 20   # several threads' worth of observations
+    rng = np.random.default_rng(3)
+    pi = np.concatenate([np.repeat(np.arange(n_pts), 2), rng.integers(0, n_pts, n_obs - 2 * n_pts)])
+    ci = rng.integers(0, n_cams, n_obs)
+    px = rng.standard_normal((n_obs, 2))
+    st, h = _create(n_cams, n_pts, ci, pi, px)
+    assert st == 0 and h.value
+    lib.ba_problem_destroy(h)
+    for o_bad in (n_obs - 3, 2_500_000, 1_300_000):      # the lowest of them is reported
+        ci[o_bad] = n_cams
+    px[3_000_000, 0] = np.nan
+    st, h = _create(n_cams, n_pts, ci, pi, px)
+    assert st == 1 and not h.value
+    assert b"observation 1300000 has camera" in lib.ba_last_error(), lib.ba_last_error()
+    ci[[n_obs - 3, 2_500_000, 1_300_000]] = 0
+    st, h = _create(n_cams, n_pts, ci, pi, px)
+    assert st == 1 and b"observation 3000000 has a non-finite pixel" in lib.ba_last_error()
+    px[3_000_000, 0] = 0.0
+    # points 7 and 123,457 lose all but one / all of their observations
+    for q, keep in ((123_457, 0), (7, 1)):
+        idx = np.flatnonzero(pi == q)
+        pi[idx[keep:]] = (q + 1) % n_pts
+    st, h = _create(n_cams, n_pts, ci, pi, px)
+    assert st == 1 and b"point 7 is observed 1 time(s)" in lib.ba_last_error(), lib.ba_last_error()
+    pi[pi == 8] = 7    # point 7 seen again; point 8 now unobserved
+    st, h = _create(n_cams, n_pts, ci, pi, px)
+    assert st == 1 and b"point 8 is observed 0 time(s)" in lib.ba_last_error(), lib.ba_last_error()
