@@ -578,6 +578,7 @@ __device__ __forceinline__ LinObs lin_obs(const Cam& cam, const float (&JL)[9], 
 
 // Everything one observation adds: evaluation outputs (mode 2), the IRLS weight, the cost,
 // the camera sums (registers) and the point sums (shared memory).
+template <bool PLAIN = false>
 __device__ __forceinline__ void lin_accumulate(const Views<float>& v, LinObs& o, uint32_t j, uint32_t slot, int mode,
                                                int loss, float lscale, float* res_out, float* jac_out,
                                                float (&acc)[TL_ACC], float* sG, float* sH, float& cs, float& cc) {
@@ -619,12 +620,19 @@ __device__ __forceinline__ void lin_accumulate(const Views<float>& v, LinObs& o,
     float* gq = sG + 3 * slot;
     float* hq = sH + 6 * slot;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) atomicAdd(gq + q, fmaf(o.jx0[q], o.r0, o.jx1[q] * o.r1));
+    for (int q = 0; q < 3; ++q) {
+        const float x = fmaf(o.jx0[q], o.r0, o.jx1[q] * o.r1);
+        if (PLAIN) gq[q] += x;
+        else atomicAdd(gq + q, x);
+    }
 #pragma unroll
     for (int a2 = 0; a2 < 3; ++a2)
 #pragma unroll
-        for (int b2 = a2; b2 < 3; ++b2)
-            atomicAdd(hq + tri_index(3, a2, b2), fmaf(o.jx0[a2], o.jx0[b2], o.jx1[a2] * o.jx1[b2]));
+        for (int b2 = a2; b2 < 3; ++b2) {
+            const float x = fmaf(o.jx0[a2], o.jx0[b2], o.jx1[a2] * o.jx1[b2]);
+            if (PLAIN) hq[tri_index(3, a2, b2)] += x;
+            else atomicAdd(hq + tri_index(3, a2, b2), x);
+        }
 }
 
 __device__ __forceinline__ void load_jl(const float* __restrict__ rec, float (&JL)[9]) {
@@ -649,14 +657,19 @@ __device__ __forceinline__ void flush_lin_global(const Views<float>& v, uint32_t
     for (int k = 0; k < TL_ACC; ++k) a[k] = 0.0f;
 }
 
-template <int TB>
+// PLAIN: every warp keeps its own copy of the tile's point sums, added to with plain
+// shared-memory adds in its long runs (as in k_tile_normal).
+template <int TB, bool PLAIN>
 __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mode, float* res_out, float* jac_out,
                                                        CondHandle lm_cond, int use_cond, Caps cap) {
     if (mode == 1 && v.st->relin == 0) return;
+    constexpr int NQ = PLAIN ? TB / 32 : 1;   // point-sum copies
     extern __shared__ __align__(16) unsigned char dsm[];
     const float2* rbuf = reinterpret_cast<const float2*>(v.rbuf);   // residuals (k_residual)
     __shared__ float4 sX4[TILE_PTS];
-    __shared__ float sG[3 * TILE_PTS], sH[PH_STRIDE * TILE_PTS];   // J_p^T W r, J_p^T W J_p (upper)
+    __shared__ float sG[NQ * 3 * TILE_PTS], sH[NQ * PH_STRIDE * TILE_PTS];   // J_p^T W r, J_p^T W J_p (upper)
+    float* const sGw = sG + (PLAIN ? (threadIdx.x >> 5) * 3 * TILE_PTS : 0);
+    float* const sHw = sH + (PLAIN ? (threadIdx.x >> 5) * PH_STRIDE * TILE_PTS : 0);
     __shared__ unsigned int s_next;
     const float eps = (float)v.st->opt.eps;
     // robust loss (evaluation, mode 2, is always the squared loss)
@@ -668,8 +681,8 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
         const TileRange T = tile_range(v, tile);
         for (int i = threadIdx.x; i < T.npt; i += TB)
             sX4[i] = make_float4(v.x[T.base + 3 * i], v.x[T.base + 3 * i + 1], v.x[T.base + 3 * i + 2], 0.0f);
-        for (int i = threadIdx.x; i < 3 * TILE_PTS; i += TB) sG[i] = 0.0f;
-        for (int i = threadIdx.x; i < PH_STRIDE * TILE_PTS; i += TB) sH[i] = 0.0f;
+        for (int i = threadIdx.x; i < NQ * 3 * TILE_PTS; i += TB) sG[i] = 0.0f;
+        for (int i = threadIdx.x; i < NQ * PH_STRIDE * TILE_PTS; i += TB) sH[i] = 0.0f;
         uint32_t *sRun, *sShort;
         uint8_t* sSlot;
         stage_compact<TB>(v, T, cap, dsm, sRun, sShort, sSlot);
@@ -693,8 +706,9 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
                 const uint32_t i = start + off, j = T.lo + i;
                 const uint32_t slot = sSlot[i];
                 LinObs o = lin_obs(cam, JL, sX4[slot], __ldg(rbuf + j), eps);
-                lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sG, sH, cs, cc);
+                lin_accumulate<PLAIN>(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sGw, sHw, cs, cc);
             }
+            if (PLAIN) __syncwarp();   // the warp's next run may meet the same points
             int idx;
             const int nv = warp_split_sum<TL_ACC>(acc, lane, idx);
 #pragma unroll
@@ -727,13 +741,23 @@ __global__ void __launch_bounds__(TB, 4) k_tile_linearize(Views<float> v, int mo
                     load_jl(v.cam_pre + (size_t)c * CP_STRIDE, JL);
                 }
                 LinObs o = lin_obs(cam, JL, sX4[slot], __ldg(rbuf + j), eps);
-                lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sG, sH, cs, cc);
+                lin_accumulate(v, o, j, slot, mode, loss, lscale, res_out, jac_out, acc, sGw, sHw, cs, cc);
             }
             if (cur != NO_CAM) flush_lin_global(v, cur, acc);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < 3 * T.npt; i += TB) v.g[T.base + i] = sG[i];
-        for (int i = threadIdx.x; i < PH_STRIDE * T.npt; i += TB) v.pt_H[(size_t)T.pt0 * PH_STRIDE + i] = sH[i];
+        for (int i = threadIdx.x; i < 3 * T.npt; i += TB) {
+            float gi = sG[i];
+#pragma unroll
+            for (int w = 1; w < NQ; ++w) gi += sG[w * 3 * TILE_PTS + i];
+            v.g[T.base + i] = gi;
+        }
+        for (int i = threadIdx.x; i < PH_STRIDE * T.npt; i += TB) {
+            float hi = sH[i];
+#pragma unroll
+            for (int w = 1; w < NQ; ++w) hi += sH[w * PH_STRIDE * TILE_PTS + i];
+            v.pt_H[(size_t)T.pt0 * PH_STRIDE + i] = hi;
+        }
         __syncthreads();   // the next tile's staging overwrites the shared sums
     }
     double in[1] = {(double)cs - (double)cc}, out[1];
@@ -881,7 +905,8 @@ void plan_tile_kernels(LaunchCfg& L, int n_tiles, int sms, int max_long_obs, int
     const int bn = std::min(prepare(k_tile_normal<TN_TB, true>, TN_TB, L.tn_smem),
                             prepare(k_tile_normal<TN_TB, false>, TN_TB, L.tn_smem));
     const int bc = prepare(k_tile_cg<TN_TB>, TN_TB, L.tn_smem);
-    const int bl = prepare(k_tile_linearize<TL_TB>, TL_TB, L.tl_smem);
+    const int bl = std::min(prepare(k_tile_linearize<TL_TB, true>, TL_TB, L.tl_smem),
+                            prepare(k_tile_linearize<TL_TB, false>, TL_TB, L.tl_smem));
     const int be = prepare(k_tile_eval<TE_TB>, TE_TB, L.te_smem);
     if (bn < 1 || bl < 1 || be < 1 || bc < 1) return;
     const int nt = std::max(1, n_tiles);
@@ -907,8 +932,13 @@ void launch_cg_round(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, 
 
 void launch_tile_linearize(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, int mode, float* res_out,
                            float* jac_out, CondHandle lm_cond, int use_cond) {
-    k_tile_linearize<TL_TB><<<L.tl_grid, TL_TB, L.tl_smem, s>>>(v, mode, res_out, jac_out, lm_cond, use_cond,
-                                                                 Caps{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap});
+    const Caps cap{L.tk_run_cap, L.tk_short_cap, L.tk_long_cap};
+    if (L.tn_plain_q)
+        k_tile_linearize<TL_TB, true><<<L.tl_grid, TL_TB, L.tl_smem, s>>>(v, mode, res_out, jac_out, lm_cond, use_cond,
+                                                                        cap);
+    else
+        k_tile_linearize<TL_TB, false><<<L.tl_grid, TL_TB, L.tl_smem, s>>>(v, mode, res_out, jac_out, lm_cond,
+                                                                         use_cond, cap);
 }
 
 void launch_tile_eval(const Views<float>& v, const LaunchCfg& L, cudaStream_t s, CondHandle lm_cond, int use_cond) {
