@@ -13,6 +13,9 @@
 // (ties broken by the value), so the same input always gives the same order.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "kernels.h"
 
 namespace gbba {
@@ -23,6 +26,8 @@ namespace {
 constexpr uint64_t SLOT_ROTATION = 89;
 
 constexpr int LOCAL_ELEMS = 2048;
+// Largest tile (observations) sorted in shared memory: 16,384 64-bit keys, 128 KB.
+constexpr int TILE_SORT_MAX = 16384;
 constexpr int LOCAL_THREADS = LOCAL_ELEMS / 2;
 
 __device__ __forceinline__ bool pair_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb) {
@@ -112,6 +117,51 @@ __global__ void k_obs_sort_keys(const uint32_t* cam_idx, const uint32_t* pt_idx,
     }
 }
 
+// Tile-bucketed observation sort: each observation goes to a free place in its tile's
+// range (any order: the sort below orders it fully), keyed (camera, rotated slot, caller
+// index); then one CTA per tile sorts the bucket in shared memory (bitonic network on the
+// bucket padded to a power of two) and writes the keys and values k_obs_gather reads.
+__global__ void k_obs_bucket(const uint32_t* cam_idx, const uint32_t* pt_idx, const uint32_t* pt_internal,
+                             int64_t n_obs, const uint32_t* tile_off, uint32_t* cursor, uint64_t* keys) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_obs; o += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ip = pt_internal[pt_idx[o]];
+        const uint32_t tile = ip / TILE_PTS, slot = ip % TILE_PTS, cam = cam_idx[o];
+        const uint64_t rslot = (slot + SLOT_ROTATION * (uint64_t)cam) % TILE_PTS;
+        const uint32_t at = tile_off[tile] + atomicAdd(&cursor[tile], 1u);
+        keys[at] = ((uint64_t)cam << 40) | (rslot << 32) | (uint64_t)o;
+    }
+}
+
+__global__ void k_tile_sort(const uint32_t* tile_off, int n_tiles, uint64_t* keys, uint32_t* vals) {
+    extern __shared__ uint64_t sk[];
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const uint32_t lo = tile_off[t], n = tile_off[t + 1] - lo;
+        uint32_t pn = 2;
+        while (pn < n) pn <<= 1;
+        for (uint32_t i = threadIdx.x; i < pn; i += blockDim.x) sk[i] = i < n ? keys[lo + i] : ~0ull;
+        __syncthreads();
+        for (uint32_t k = 2; k <= pn; k <<= 1)
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t q = threadIdx.x; q < pn / 2; q += blockDim.x) {
+                    const uint32_t i = 2 * j * (q / j) + (q % j), l = i + j;
+                    const uint64_t a = sk[i], b = sk[l];
+                    if ((b < a) == ((i & k) == 0)) {
+                        sk[i] = b;
+                        sk[l] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t key = sk[i];
+            const uint64_t cam = key >> 40, rslot = (key >> 32) & 0xffu;
+            keys[lo + i] = ((uint64_t)t << 40) | (cam << 16) | (rslot << 8);
+            vals[lo + i] = (uint32_t)(key & 0xffffffffu);
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void k_obs_gather(const uint64_t* keys, const uint32_t* vals, const double* pixels, int64_t n_obs,
                              uint32_t* obs_key, T* obs_uv, uint32_t* obs_user) {
@@ -126,13 +176,6 @@ __global__ void k_obs_gather(const uint64_t* keys, const uint32_t* vals, const d
         obs_uv[2 * j + 1] = (T)pixels[2 * (size_t)o + 1];
         obs_user[j] = o;
     }
-}
-
-// Point-major index: key = (internal point, position in the tile-major order).
-__global__ void k_pm_keys(const uint32_t* obs_user, const uint32_t* pt_idx, const uint32_t* pt_internal,
-                          int64_t n_obs, size_t sort_n, uint64_t* keys) {
-    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < sort_n; j += (size_t)gridDim.x * blockDim.x)
-        keys[j] = j < (size_t)n_obs ? (((uint64_t)pt_internal[pt_idx[obs_user[j]]] << 32) | (uint64_t)j) : ~0ull;
 }
 
 // --- long runs first ------------------------------------------------------------------
@@ -226,12 +269,67 @@ __global__ void k_copy_back(const uint32_t* tmp_key, const T* tmp_uv, const uint
     }
 }
 
-__global__ void k_pm_finish(const uint64_t* keys, int64_t n_obs, int n_pts, uint32_t* obs_pm, uint32_t* pt_obs_off) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n_obs; k += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t key = keys[k];
-        obs_pm[k] = (uint32_t)(key & 0xffffffffu);
-        const uint32_t ip = (uint32_t)(key >> 32);
-        if (k == 0 || (uint32_t)(keys[k - 1] >> 32) != ip) pt_obs_off[ip] = (uint32_t)k;
+// Point-major index by a counting sort inside each tile: a tile's observation range
+// holds exactly the observations of its TILE_PTS points, so the point offsets are the
+// tile's first observation plus an exclusive scan of per-slot counts, and each point's
+// observations are placed in increasing position j (lanes of a 32-observation step
+// ranked among equal slots, steps in order): the same index as sorting (point, j).
+// One warp per tile; `cnt` holds the warp's 256 slot counters in shared memory.
+constexpr int PM_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * PM_WARPS) k_pm_tiles(const uint32_t* __restrict__ obs_key,
+                                                            const uint32_t* __restrict__ tile_off, int n_tiles,
+                                                            int n_pts, int64_t n_obs, uint32_t* obs_pm,
+                                                            uint32_t* pt_obs_off) {
+    static_assert(TILE_PTS == 256, "one-byte point slots");
+    __shared__ uint32_t cnt_all[PM_WARPS][TILE_PTS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t* cnt = cnt_all[wid];
+    const uint32_t lower = (1u << lane) - 1u;
+    for (int t = blockIdx.x * PM_WARPS + wid; t < n_tiles; t += gridDim.x * PM_WARPS) {
+        const uint32_t lo = tile_off[t], hi = tile_off[t + 1];
+        for (int s = lane; s < TILE_PTS; s += 32) cnt[s] = 0u;
+        __syncwarp();
+        for (uint32_t j = lo + lane; j < hi; j += 32) atomicAdd(&cnt[obs_key[j] & 0xffu], 1u);
+        __syncwarp();
+        // exclusive scan of the 256 counters: 8 per lane, then across lanes
+        uint32_t c[TILE_PTS / 32], run = 0u;
+#pragma unroll
+        for (int k = 0; k < TILE_PTS / 32; ++k) {
+            c[k] = cnt[lane * (TILE_PTS / 32) + k];
+            run += c[k];
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        uint32_t base = incl - run;
+        const int pt0 = t * TILE_PTS;
+#pragma unroll
+        for (int k = 0; k < TILE_PTS / 32; ++k) {
+            const int s2 = lane * (TILE_PTS / 32) + k;
+            cnt[s2] = base;
+            if (pt0 + s2 < n_pts) pt_obs_off[pt0 + s2] = lo + base;
+            base += c[k];
+        }
+        __syncwarp();
+        // stable placement, 32 observations a step
+        for (uint32_t j0 = lo; j0 < hi; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            const bool ok = j < hi;
+            const unsigned act = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const uint32_t slot = obs_key[j] & 0xffu;
+                const unsigned same = __match_any_sync(act, slot);
+                const uint32_t at = cnt[slot] + (uint32_t)__popc(same & lower);
+                obs_pm[lo + at] = j;
+                __syncwarp(act);
+                if ((same >> lane) >> 1 == 0u) cnt[slot] += (uint32_t)__popc(same);   // highest lane of the group
+            }
+            __syncwarp();
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) pt_obs_off[n_pts] = (uint32_t)n_obs;
 }
@@ -341,10 +439,33 @@ void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s) {
     k_fill_u32<<<blocks_for(v.n_tiles, TB), TB, 0, s>>>(b.tile_cnt, (size_t)v.n_tiles, 0u);
     k_tile_count<<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.pt_idx, pt_internal, v.n_obs, b.tile_cnt);
     k_scan_single<<<1, 1024, 0, s>>>(b.tile_cnt, v.n_tiles, tile_off);
-    // 3. observation order
-    const size_t no2 = pow2_at_least((size_t)v.n_obs);
-    k_obs_sort_keys<<<blocks_for(no2, TB), TB, 0, s>>>(b.cam_idx, b.pt_idx, pt_internal, v.n_obs, no2, b.keys, b.vals);
-    bitonic_sort(b.keys, b.vals, no2, s);
+    // 3. observation order: sorted inside each tile's bucket in shared memory when the
+    //    largest tile fits TILE_SORT_MAX observations, else one global sort
+    uint32_t most = 0;
+    {
+        std::vector<uint32_t> toff((size_t)v.n_tiles + 1);
+        if (cudaMemcpyAsync(toff.data(), tile_off, 4 * toff.size(), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+            cudaStreamSynchronize(s) == cudaSuccess) {
+            for (int t = 0; t < v.n_tiles; ++t) most = std::max(most, toff[t + 1] - toff[t]);
+        } else {
+            most = ~0u;   // the error surfaces at the caller's next check; take the general path
+        }
+    }
+    if (most <= (uint32_t)TILE_SORT_MAX) {
+        uint32_t pn = 2;
+        while (pn < most) pn <<= 1;
+        k_fill_u32<<<blocks_for(v.n_tiles, TB), TB, 0, s>>>(b.tile_cnt, (size_t)v.n_tiles, 0u);
+        k_obs_bucket<<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.cam_idx, b.pt_idx, pt_internal, v.n_obs, tile_off,
+                                                             b.tile_cnt, b.keys);
+        const size_t smem = 8 * (size_t)pn;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_tile_sort<<<std::max(1, std::min(v.n_tiles, 65535)), 512, smem, s>>>(tile_off, v.n_tiles, b.keys, b.vals);
+    } else {
+        const size_t no2 = pow2_at_least((size_t)v.n_obs);
+        k_obs_sort_keys<<<blocks_for(no2, TB), TB, 0, s>>>(b.cam_idx, b.pt_idx, pt_internal, v.n_obs, no2, b.keys,
+                                                           b.vals);
+        bitonic_sort(b.keys, b.vals, no2, s);
+    }
     k_obs_gather<T><<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.keys, b.vals, b.pixels, v.n_obs,
                                                            const_cast<uint32_t*>(v.obs_key),
                                                            const_cast<T*>(v.obs_uv),
@@ -367,11 +488,13 @@ void build_order(const Views<T>& v, const OrderBuffers& b, cudaStream_t s) {
                                                               const_cast<uint32_t*>(v.obs_user));
     }
     // 5. point-major index over the tile-major order (every point has >= 2 observations,
-    //    so every internal point owns a non-empty run)
-    k_pm_keys<<<blocks_for(no2, TB), TB, 0, s>>>(v.obs_user, b.pt_idx, pt_internal, v.n_obs, no2, b.keys);
-    bitonic_sort(b.keys, b.vals, no2, s);
-    k_pm_finish<<<blocks_for(v.n_obs, TB), TB, 0, s>>>(b.keys, v.n_obs, v.n_pts, const_cast<uint32_t*>(v.obs_pm),
-                                                        const_cast<uint32_t*>(v.pt_obs_off));
+    //    so every internal point owns a non-empty run), one counting sort per tile
+    {
+        const int grid = (int)std::min<int64_t>(8192, ((int64_t)v.n_tiles + PM_WARPS - 1) / PM_WARPS);
+        k_pm_tiles<<<std::max(1, grid), 32 * PM_WARPS, 0, s>>>(v.obs_key, tile_off, v.n_tiles, v.n_pts, v.n_obs,
+                                                               const_cast<uint32_t*>(v.obs_pm),
+                                                               const_cast<uint32_t*>(v.pt_obs_off));
+    }
 }
 
 void sort_pairs(uint64_t* keys, uint32_t* vals, size_t n, cudaStream_t s) { bitonic_sort(keys, vals, n, s); }

@@ -143,6 +143,23 @@ def test_lm_solve_with_repeated_observations_matches_oracle(B):
     assert abs(res.final_cost - ref.final_cost) <= 1e-4 * ref.final_cost, (res.final_cost, ref.final_cost)
 
 
+def test_lm_solve_with_a_tile_beyond_the_shared_memory_sort(B):
+    """90 cameras that all see the same 256 points: one tile of 23,040 observations, more
+    than the 16,384 the bind sorts per tile in shared memory, so the observation order
+    comes from the global sort; the solve (both PCG forms' inputs, the tile operator)
+    still follows the oracle."""
+    prob = synth.round_to_f32(synth.make_problem(90, 256, ("poisson", 1000.0), "uniform", seed=51))
+    assert prob.n_obs > 16384
+    ref = O.ba_solve(prob.cams_init, prob.pts_init, prob.cam_idx, prob.pt_idx, prob.pixels,
+                     O.LMOptions(max_lm_iters=8, max_pcg_iters=50))
+    for precision, tol in (("mixed", 1e-4), ("fp64", 1e-8)):
+        p = _problem(B, prob, precision)
+        res = p.solve(max_lm_iters=8, max_pcg_iters=50)
+        assert res.status == 0
+        assert abs(res.final_cost - ref.final_cost) <= tol * ref.final_cost, (precision, res.final_cost, ref.final_cost)
+        p.close()
+
+
 # (use_graph, pcg_kernel): conditional-loop graph / unrolled graph / host-launched
 # sequence, with the persistent PCG kernel (0: two exchanges per iteration, 2: one),
 # or separate kernels per PCG step (1: textbook recurrences, 3: one reduction a step)
