@@ -801,8 +801,8 @@ def run_batched(args, binding, synth, torch, dev, stream, flush, rank=0):
            "status_nonzero": int(sum(r.status != 0 for r in res)),
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                         "algorithmic_bytes": nbytes, "traffic": None,
-                        "traffic_note": "one ncu capture of a whole batch solve read 16.2 GB and wrote 11.1 GB of DRAM "
-                                        "(profiles/k_batch_solve_batch512.md)",
+                        "traffic_note": "one ncu capture of a whole batch solve of this workload read 16.2 GB and "
+                                        "wrote 11.1 GB of DRAM",
                         "kernel": "k_batch_solve (one CTA per problem at a time, whole batch in one launch)"}}
     b.close()
     return out
